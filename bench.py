@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""TASER detections/s on MU-MIMO QPSK 128x16 (N = 33), t_max = 20: BF16 tensor-core
+path vs FP32 path at equal BER, on one or more GPUs (one process per GPU).
+
+A step is one pass of the whole detector over one batch of synthetic instances that
+are already resident in HBM: taser_build_T (T~, D, tau from H, y) followed by
+taser_detect (Algorithm 1 and the decisions).  The batch is 65,536 instances per GPU
+with the SNR cycling over 0, 2, ..., 20 dB (the SNR sweep of the workload); its inputs
+(1.14 GB) are larger than the 129 MB L2, so no flush is needed between steps.
+
+Prints one JSON line on rank 0.  `--impl reference` times the FP64 CPU oracle instead.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+B, U, T_MAX, ALPHA = 128, 16, 20, 0.5
+N = 2 * U + 1
+SNR_GRID = np.arange(0.0, 21.0, 2.0)
+METRIC = "TASER detections/s, QPSK 128x16, t_max=20: BF16-TC vs FP32 path at equal BER"
+WORKLOAD = "mimo_qpsk_B128_U16_N33_tmax20_snr0-20dB"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["taser", "reference"], default="taser")
+    ap.add_argument("--instances", type=int, default=65536, help="instances per GPU per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample", type=int, default=8192, help="instances timed on the CPU oracle")
+    return ap.parse_args()
+
+
+def flops_per_detection(n, t_max):
+    """Algorithmic work of Algorithm 1 (Sec. III-D) with the triangular skip (Sec. IV-A):
+    per iteration P(N) = N(N+1)(2N+1)/6 MACs for V, then N(N+1)/2 squares, N(N+1)/2 adds
+    and N(N+1)/2 scalings for the prox, plus N scale factors."""
+    P = n * (n + 1) * (2 * n + 1) // 6
+    return t_max * (2 * P + 3 * n * (n + 1) // 2 + n)
+
+
+def build_bytes_per_instance(b, u, n):
+    """Algorithmic HBM bytes of taser_build_T per instance: read H (B x U complex64) and y
+    (B complex64), write T~ (N x N fp32), D (N) and tau; the step-size kernel reads T~."""
+    return 8 * b * u + 8 * b + 4 * n * n + 4 * n + 4 + 4 * n * n
+
+
+def make_workload(n, seed):
+    from synth import make_mimo
+    snr = np.tile(SNR_GRID, n // len(SNR_GRID) + 1)[:n]
+    return make_mimo(n, B, U, snr, "qpsk", seed=seed)
+
+
+def truth_bits(w):
+    return np.concatenate([w["bits_re"], w["bits_im"]], axis=1)
+
+
+def clopper_pearson(k, n, conf=0.95):
+    from scipy.stats import beta
+    a = (1 - conf) / 2
+    lo = 0.0 if k == 0 else float(beta.ppf(a, k, n - k + 1))
+    hi = 1.0 if k == n else float(beta.ppf(1 - a, k + 1, n - k))
+    return lo, hi
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while the GPU is busy."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [x.strip() for x in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax.append(float(p[2]))
+                    power.append(float(p[3]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        busy = [s for s in sm if smax and s > 0.5 * max(smax)] or sm
+        return {"sm_mhz": statistics.median(busy) if busy else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_median": statistics.median(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+def _peak(d, *keys):
+    for k in keys:
+        if k in d and isinstance(d[k], (int, float)):
+            return float(d[k])
+    return None
+
+
+def cpu_baseline(w, sample):
+    """The FP64 oracle as it stands, single process, on the first `sample` instances."""
+    from oracle import taser_oracle as O
+    H, y = w["H"][:sample], w["y"][:sample]
+    t0 = time.perf_counter()
+    O.detect("mimo_qpsk", H, y, ALPHA, T_MAX)
+    dt = time.perf_counter() - t0
+    return {"value": sample / dt, "unit": "detections/s", "cores": 1, "kind": "oracle",
+            "sample": "%d QPSK 128x16 instances of the workload (SNR 0..20 dB), FP64 numpy oracle "
+                      "(T, Jacobi preconditioning, eigvalsh, Algorithm 1), %.1f s" % (sample, dt)}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sample = 512
+    w = make_workload(sample * (args.warmup + args.steps), seed=1)
+    from oracle import taser_oracle as O
+    times = []
+    for i in range(args.warmup + args.steps):
+        sl = slice(i * sample, (i + 1) * sample)
+        t0 = time.perf_counter()
+        O.detect("mimo_qpsk", w["H"][sl], w["y"][sl], ALPHA, T_MAX)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    value = sample * len(times) / sum(times)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "detections/s", "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic", "config": {"workload": WORKLOAD, "instances_per_step": sample,
+                                           "t_max": T_MAX, "alpha": ALPHA},
+           "cpu_baseline": {"value": value, "unit": "detections/s", "cores": 1, "kind": "oracle",
+                            "sample": "%d instances per step, FP64 numpy oracle, one process" % sample},
+           "e2e": {"value": value, "unit": "detections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import paper_1609_01797_gb300 as taser
+    from paper_1609_01797_gb300.replicas import max_over_ranks, sum_over_ranks
+
+    n = args.instances
+    w = make_workload(n, seed=1 + 1000 * rank)
+    bits = truth_bits(w)
+    H = torch.from_numpy(w["H"]).to(dev)
+    y = torch.from_numpy(w["y"]).to(dev)
+    bufs = {"T_tilde": torch.empty((n, N, N), device=dev), "D": torch.empty((n, N), device=dev),
+            "tau": torch.empty((n,), device=dev), "flags": torch.zeros((n,), device=dev, dtype=torch.int32)}
+    s_hat = torch.empty((n, N - 1), device=dev, dtype=torch.int8)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def run_path(precision, steps, warmup):
+        for _ in range(warmup):
+            taser.build_T("mimo_qpsk", H, y, ALPHA, out=bufs)
+            taser.detect(bufs["T_tilde"], bufs["D"], bufs["tau"], T_MAX, precision, want_L=False,
+                         flags=bufs["flags"], out_s=s_hat)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+        start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        start.record(stream)
+        for i in range(steps):
+            ev[i][0].record(stream)
+            taser.build_T("mimo_qpsk", H, y, ALPHA, out=bufs)
+            ev[i][1].record(stream)
+            taser.detect(bufs["T_tilde"], bufs["D"], bufs["tau"], T_MAX, precision, want_L=False,
+                         flags=bufs["flags"], out_s=s_hat)
+            ev[i][2].record(stream)
+        end.record(stream)
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = start.elapsed_time(end) / steps
+        build_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
+        detect_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        errs = int((s_hat.cpu().numpy() != bits).sum())
+        return {"ms_per_step": ms, "build_ms": build_ms, "detect_ms": detect_ms, "bit_errors": errs}
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    paths = {}
+    for precision in ("bf16_tc", "fp32", "fp16_tc"):
+        paths[precision] = run_path(precision, args.steps, args.warmup)
+    clocks = sampler.stop()
+
+    # e2e through the C ABI with host buffers: H2D of H and y, the full path, D2H of s_hat.
+    H_host = torch.from_numpy(w["H"]).pin_memory()
+    y_host = torch.from_numpy(w["y"]).pin_memory()
+    s_host = torch.empty((n, N - 1), dtype=torch.int8).pin_memory()
+    ws = torch.empty(taser.host_workspace_bytes("mimo_qpsk", n, B, U), device=dev, dtype=torch.uint8)
+    for _ in range(args.warmup):
+        taser.run_host("mimo_qpsk", H_host, y_host, ALPHA, T_MAX, "bf16_tc", ws, s_host)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        taser.run_host("mimo_qpsk", H_host, y_host, ALPHA, T_MAX, "bf16_tc", ws, s_host)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    e2e_errs = int((s_host.numpy() != bits).sum())
+
+    # Whole-job numbers: max step time over ranks, instances summed over ranks.
+    total = n * world
+    for p in paths.values():
+        p["ms_per_step"] = max_over_ranks(p["ms_per_step"], world)
+        p["build_ms"] = max_over_ranks(p["build_ms"], world)
+        p["detect_ms"] = max_over_ranks(p["detect_ms"], world)
+        p["bit_errors"] = sum_over_ranks(p["bit_errors"], world)
+        p["det_per_s"] = total / (p["ms_per_step"] * 1e-3)
+        p["detect_only_det_per_s"] = total / (p["detect_ms"] * 1e-3)
+        nbits = total * (N - 1)
+        p["ber"] = p["bit_errors"] / nbits
+        p["ber_ci95"] = clopper_pearson(p["bit_errors"], nbits)
+    lo, hi = paths["fp32"]["ber_ci95"]
+    equal_ber = lo <= paths["bf16_tc"]["ber"] <= hi
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return 0
+
+    peaks, peak_src = load_peaks()
+    head = paths["bf16_tc"]
+    smax = clocks.get("sm_max_mhz") or 2070.0
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * smax * 1e6 / 1e12   # TFLOP/s, FMA = 2 flops
+    bf16_peak = _peak(peaks, "bf16_tflops", "bf16_dense_tflops") or 1900.0
+    hbm_peak = _peak(peaks, "hbm_gbs", "hbm_GBps", "copy_gbs") or 6800.0
+    fl = flops_per_detection(N, T_MAX)
+    det_tc = n / (head["detect_ms"] * 1e-3) / 1e12 * fl                      # TFLOP/s per GPU
+    build_gbs = n * build_bytes_per_instance(B, U, N) / (head["build_ms"] * 1e-3) / 1e9
+    roof_detect = {"kernel": "detect_tc_kernel<32,bf16> (mma.sync m16n8k16)", "bound": "tensor",
+                   "achieved": det_tc, "peak": bf16_peak, "unit": "TFLOP/s", "frac": det_tc / bf16_peak,
+                   "traffic": None, "peak_source": peak_src,
+                   "algorithmic_flops_per_launch": fl * n,
+                   "fp32_pipe_frac": det_tc / fp32_peak}
+    roof_build = {"kernel": "build_T_kernel<17> + spectral_kernel<32>", "bound": "hbm", "achieved": build_gbs,
+                  "peak": hbm_peak, "unit": "GB/s", "frac": build_gbs / hbm_peak, "traffic": None,
+                  "peak_source": peak_src,
+                  "algorithmic_bytes_per_launch": n * build_bytes_per_instance(B, U, N)}
+    dominant, other = (roof_detect, roof_build) if head["detect_ms"] >= head["build_ms"] else (roof_build, roof_detect)
+    fp32 = paths["fp32"]
+    det_fp32 = n / (fp32["detect_ms"] * 1e-3) / 1e12 * fl
+    out = {
+        "metric": METRIC,
+        "value": head["det_per_s"],
+        "unit": "detections/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "bf16",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "instances_per_gpu": n, "B": B, "U": U, "N": N, "t_max": T_MAX,
+                   "alpha": ALPHA, "snr_db": "0..20 step 2, cycled over instances",
+                   "l2": "inputs (%.2f GB per GPU) larger than L2; no flush" % (n * (8 * B * U + 8 * B) / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "paths": {k: {"det_per_s": v["det_per_s"], "detect_only_det_per_s": v["detect_only_det_per_s"],
+                      "ms_per_step": v["ms_per_step"], "build_ms": v["build_ms"], "detect_ms": v["detect_ms"],
+                      "ber": v["ber"], "ber_ci95": v["ber_ci95"]} for k, v in paths.items()},
+        "equal_ber": equal_ber,
+        "speedup_bf16_vs_fp32": fp32["ms_per_step"] / head["ms_per_step"],
+        "roofline": dominant,
+        "roofline_other": other,
+        "roofline_fp32_path": {"kernel": "detect_fp32_kernel<32>", "bound": "alu", "achieved": det_fp32,
+                               "peak": fp32_peak, "unit": "TFLOP/s", "frac": det_fp32 / fp32_peak,
+                               "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
+                                              % (props.multi_processor_count, smax)},
+        "clocks": clocks,
+        "e2e": {"value": total / (e2e_ms * 1e-3), "unit": "detections/s",
+                "h2d_bytes_per_step": int(H_host.numel() * 8 + y_host.numel() * 8),
+                "d2h_bytes_per_step": int(s_host.numel()), "ms_per_step": e2e_ms,
+                "path": "taser_run_host (bf16_tc)", "bit_errors": e2e_errs},
+        "gpu_launches": 3 * args.steps,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, min(args.cpu_sample, n))
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

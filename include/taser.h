@@ -1,0 +1,174 @@
+/*
+ * taser.h -- C ABI of the GB300 (sm_103a) TASER detector library (libtaser.so).
+ *
+ * TASER (Triangular Approximate SEmidefinite Relaxation; Castaneda, Goldstein, Studer,
+ * arXiv:1609.01797) detects BPSK/QPSK symbols of many independent problems at once:
+ * coherent MU-MIMO (Sec. II-A) and SIMO joint channel estimation and detection (JED,
+ * Sec. II-B).  Every entry point works on a batch of independent instances.
+ *
+ * Conventions shared by all entry points
+ *   - Array arguments are DEVICE pointers owned by the caller unless stated otherwise.
+ *     The library never allocates, frees or keeps them.
+ *   - Calls are asynchronous and ordered on `stream` (a cudaStream_t passed as void*;
+ *     NULL means the legacy default stream).  A returned TASER_OK means the work was
+ *     enqueued; kernel-side numeric trouble is reported through the per-instance flag
+ *     bits below, never as a global failure.
+ *   - Invalid arguments return TASER_ERR_INVALID_ARG before anything is launched.
+ *     Array pointers must be 16-byte aligned.  batch == 0 is a valid no-op.
+ *   - TASER_ERR_CUDA carries the CUDA error seen at launch; taser_last_error() returns
+ *     its text (thread-local).
+ *   - Matrices are row-major per instance and instances are contiguous:
+ *     element (i, j) of instance b of an [batch][N][N] array is at b*N*N + i*N + j.
+ *   - The last index N-1 of every real-valued problem is the augmented "1" coordinate
+ *     (MIMO) or the pilot slot (JED); decisions are returned for indices 0..N-2.
+ */
+#ifndef TASER_H
+#define TASER_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    TASER_OK = 0,
+    TASER_ERR_INVALID_ARG = 1,
+    TASER_ERR_UNSUPPORTED = 2,
+    TASER_ERR_CUDA = 3,
+    TASER_ERR_TIMEOUT = 4,
+    TASER_ERR_NUMERIC = 5
+} taser_status;
+
+/* Problem kinds (Sec. II).  N is the size of the real-valued matrix T. */
+typedef enum {
+    TASER_MIMO_BPSK = 0,     /* N = U + 1,  H complex64 [batch][B][U], y [batch][B]      */
+    TASER_MIMO_QPSK = 1,     /* N = 2U + 1, same inputs                                  */
+    TASER_SIMO_JED_BPSK = 2  /* N = K,      Y complex64 [batch][B][K], slot 0 = +1 pilot */
+} taser_problem;
+
+/* Arithmetic of the triangular product L~ T^ inside the iterations.  The prox
+ * (column norms and rescaling) and the master copy of L~ are always FP32. */
+typedef enum {
+    TASER_FP32 = 0,      /* FP32 FMA pipe                                              */
+    TASER_BF16_TC = 1,   /* tensor cores, BF16 operands, FP32 accumulation             */
+    TASER_FP16_TC = 2    /* tensor cores, FP16 operands, FP32 accumulation             */
+} taser_precision;
+
+/* Handling of L~_NN (the prox of Sec. III-C applied to the last column). */
+typedef enum {
+    TASER_LNN_FIXED = 0,   /* default: L~_NN stays +D_NN (last column is constant)       */
+    TASER_LNN_LITERAL = 1  /* L~_NN = D_NN sign(V_NN); decisions multiplied by its sign */
+} taser_lnn_mode;
+
+/* Per-instance flag bits (uint32). */
+#define TASER_FLAG_ZERO_DIAG   (1u << 0) /* some T_kk == 0; D_kk was replaced by 1       */
+#define TASER_FLAG_NONFINITE   (1u << 1) /* a non-finite value reached T or its norm     */
+#define TASER_FLAG_ZERO_COLUMN (1u << 2) /* a column of V had zero norm in the prox      */
+#define TASER_FLAG_LNN_SIGN    (1u << 3) /* V_NN <= 0 was seen in some iteration         */
+
+/* Largest N supported by the detection kernels. */
+#define TASER_MAX_N 65
+
+/* Size N of the real-valued problem, or -1 for an unknown kind / non-positive size. */
+int taser_problem_size(int kind, int U_or_K);
+
+/* Static text of a status code. */
+const char* taser_status_string(int status);
+
+/* Thread-local text of the last error reported by this library ("" if none). */
+const char* taser_last_error(void);
+
+/*
+ * taser_build_T -- per instance, the real-valued matrix T of Sec. II-A (Eq. 2) or
+ * Sec. II-B (Eq. 5), its Jacobi preconditioning D = diag(sqrt|T_kk|),
+ * T~ = D^-1 T D^-1 (Sec. III-C), and the step size tau = alpha / ||T~||_2
+ * (Sec. III-B, inputs of Algorithm 1).
+ *
+ *   kind      taser_problem.
+ *   batch     number of instances (>= 0).
+ *   B         receive antennas (>= 1).
+ *   U_or_K    users U (MIMO, 1..32) or slots K including the pilot (JED, 2..33).
+ *   H_or_Y    complex64 (interleaved re, im float pairs):
+ *               MIMO: H [batch][B][U]; JED: Y [batch][B][K] with column 0 the pilot slot.
+ *   y         complex64 [batch][B] (MIMO), must be NULL for JED.
+ *   alpha     step-size factor, 0 < alpha < 1 (the paper leaves its value open).
+ *   T_tilde   out, float [batch][N][N], full symmetric matrix.
+ *   D         out, float [batch][N], D_kk = sqrt(|T_kk|) (1 where T_kk == 0).
+ *   tau       out, float [batch].
+ *   spec_norm out, float [batch] = ||T~||_2, or NULL.
+ *   flags     out, uint32 [batch] (overwritten with ZERO_DIAG / NONFINITE bits), or NULL.
+ *
+ * QPSK symbols are taken as (+-1 +-j)/sqrt2: T is built from the effective channel
+ * H/sqrt2 so that the relaxed vector lies in {+-1}^N.  For JED the pilot column is
+ * moved to the last index, so decisions 0..N-2 are slots 1..K-1.
+ * ||T~||_2 is the largest |eigenvalue|, from an FP32 Householder tridiagonalisation
+ * and Sturm-count multisection (not a power iteration, which converges too slowly on
+ * MU-MIMO matrices with nearly equal top eigenvalues).
+ */
+taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K,
+                           const void* H_or_Y, const void* y, float alpha,
+                           float* T_tilde, float* D, float* tau, float* spec_norm,
+                           uint32_t* flags, void* stream);
+
+/*
+ * taser_step_size -- tau = alpha / ||T~||_2 for caller-provided symmetric T~
+ * (Sec. III-B; Algorithm 1 inputs).  T_tilde float [batch][N][N] (full), N in [2, 65];
+ * tau out float [batch]; spec_norm out float [batch] or NULL.
+ */
+taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, float alpha,
+                             float* tau, float* spec_norm, void* stream);
+
+/*
+ * taser_detect -- Algorithm 1 (TASER) for every instance:
+ *   L~(0) = D;  for t = 1..t_max:  V = L~ - tril(2 tau L~ T~),  L~ = prox(V)
+ * where prox rescales every column k < N-1 to norm D_kk (Sec. III-C) and the last
+ * column follows lnn_mode; outputs s_k = sign(L~_{N,k}), k = 0..N-2, sign(0) = +1.
+ *
+ *   batch     number of instances (>= 0).
+ *   N         problem size, 2..65.
+ *   T_tilde   float [batch][N][N], full symmetric preconditioned matrix.
+ *   D         float [batch][N], positive scaling (D_kk of Sec. III-C).
+ *   tau       float [batch], step size.
+ *   t_max     iterations, >= 1.
+ *   precision taser_precision.  Tensor-core precisions run for 10 <= N <= 33; outside
+ *             that range the FP32 kernel runs (below it the product has no dense tile
+ *             worth a tensor core; above it no tensor-core kernel is built yet).
+ *   lnn_mode  taser_lnn_mode.
+ *   L         out, float [batch][N][N] = L~(t_max) with zeros above the diagonal, or NULL.
+ *   s_hat     out, int8 [batch][N-1], values +1 / -1.
+ *   flags     in/out, uint32 [batch]; ZERO_COLUMN / LNN_SIGN bits are OR-ed in; or NULL.
+ */
+taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const float* D,
+                          const float* tau, int t_max, int precision, int lnn_mode,
+                          float* L, int8_t* s_hat, uint32_t* flags, void* stream);
+
+/*
+ * taser_host_workspace_bytes -- bytes of device workspace taser_run_host needs for
+ * `batch` instances of the given problem (0 for invalid arguments).
+ */
+size_t taser_host_workspace_bytes(int kind, int64_t batch, int B, int U_or_K);
+
+/*
+ * taser_run_host -- the whole path from HOST inputs to HOST decisions, ordered on
+ * `stream`: copy H and y (or Y) to the device, taser_build_T, taser_detect (no L
+ * output), copy s_hat and flags back.  Arguments as in taser_build_T / taser_detect,
+ * except:
+ *   H_or_Y, y     HOST complex64 buffers (pinned memory gives full copy bandwidth).
+ *   workspace     DEVICE buffer of at least taser_host_workspace_bytes(...) bytes,
+ *                 256-byte aligned, owned by the caller; its contents are scratch.
+ *   s_hat, flags  HOST outputs, int8 [batch][N-1] and uint32 [batch] (flags may be NULL).
+ * The call returns once the work is enqueued; synchronize `stream` before reading the
+ * host outputs.
+ */
+taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y,
+                            const void* y, float alpha, int t_max, int precision, int lnn_mode,
+                            void* workspace, size_t workspace_bytes, int8_t* s_hat,
+                            uint32_t* flags, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TASER_H */

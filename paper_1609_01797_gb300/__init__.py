@@ -1,0 +1,7 @@
+"""GB300 (sm_103a) TASER detector: C ABI libtaser.so + thin torch binding.
+
+The Python layer only marshals device pointers and the current CUDA stream into the
+C ABI declared in include/taser.h; every step of the detector runs in CUDA kernels.
+"""
+from .api import (BPSK, JED_BPSK, QPSK, PRECISIONS, build_T, detect, problem_size,  # noqa: F401
+                  step_size, host_workspace_bytes, run_host)

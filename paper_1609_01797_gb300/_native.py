@@ -1,0 +1,53 @@
+"""ctypes loader of libtaser.so.  There is no fallback: if the library is missing the
+import fails loudly, because every step of the detector runs in its CUDA kernels."""
+import ctypes
+import os
+
+LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libtaser.so")
+
+_c_i32, _c_i64, _c_f32, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
+
+# name -> (restype, argtypes); must match include/taser.h
+SIGNATURES = {
+    "taser_problem_size": (_c_i32, [_c_i32, _c_i32]),
+    "taser_status_string": (ctypes.c_char_p, [_c_i32]),
+    "taser_last_error": (ctypes.c_char_p, []),
+    "taser_build_T": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "taser_step_size": (_c_i32, [_c_i64, _c_i32, _vp, _c_f32, _vp, _vp, _vp]),
+    "taser_detect": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _c_i32, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
+    "taser_host_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i64, _c_i32, _c_i32]),
+    "taser_run_host": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32, _vp,
+                                ctypes.c_size_t, _vp, _vp, _vp]),
+}
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(
+                "libtaser.so not found at %s; build it with paper_1609_01797_gb300.build.build() "
+                "(the detector has no CPU fallback)" % LIB_PATH)
+        handle = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = handle
+    return _lib
+
+
+class TaserError(RuntimeError):
+    def __init__(self, status, where):
+        l = lib()
+        msg = "%s failed: %s (%s)" % (where, l.taser_status_string(status).decode(),
+                                      l.taser_last_error().decode())
+        super().__init__(msg)
+        self.status = status
+
+
+def check(status, where):
+    if status != 0:
+        raise TaserError(status, where)

@@ -1,0 +1,108 @@
+"""Torch-facing binding of the TASER C ABI (argument marshalling only)."""
+import ctypes
+
+import torch
+
+from ._native import check, lib
+
+BPSK, QPSK, JED_BPSK = 0, 1, 2
+KINDS = {"mimo_bpsk": BPSK, "mimo_qpsk": QPSK, "jed_bpsk": JED_BPSK, BPSK: BPSK, QPSK: QPSK,
+         JED_BPSK: JED_BPSK}
+PRECISIONS = {"fp32": 0, "bf16_tc": 1, "fp16_tc": 2}
+LNN_MODES = {"fixed": 0, "literal": 1}
+
+
+def _ptr(t):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _stream(stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _dev(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda):
+        raise TypeError("%s must be a CUDA tensor" % name)
+    if t.dtype != dtype:
+        raise TypeError("%s must be %s (got %s)" % (name, dtype, t.dtype))
+    if not t.is_contiguous():
+        raise ValueError("%s must be contiguous" % name)
+    return t
+
+
+def problem_size(kind, U_or_K):
+    return lib().taser_problem_size(KINDS[kind], int(U_or_K))
+
+
+def build_T(kind, H_or_Y, y=None, alpha=0.5, out=None, stream=None):
+    """T~, D, tau (and ||T~||_2, flags) per instance from complex64 H [n,B,U] and
+    y [n,B] (MIMO) or Y [n,B,K] (JED).  Returns a dict of device tensors."""
+    k = KINDS[kind]
+    X = _dev(H_or_Y, torch.complex64, "H_or_Y")
+    n, B, M = X.shape
+    if k != JED_BPSK:
+        _dev(y, torch.complex64, "y")
+        if tuple(y.shape) != (n, B):
+            raise ValueError("y must have shape [n, B]")
+    N = problem_size(k, M)
+    dev = X.device
+    if out is None:
+        out = {"T_tilde": torch.empty((n, N, N), device=dev, dtype=torch.float32),
+               "D": torch.empty((n, N), device=dev, dtype=torch.float32),
+               "tau": torch.empty((n,), device=dev, dtype=torch.float32),
+               "spec_norm": torch.empty((n,), device=dev, dtype=torch.float32),
+               "flags": torch.zeros((n,), device=dev, dtype=torch.int32)}
+    st = lib().taser_build_T(k, n, B, M, _ptr(X), _ptr(y if k != JED_BPSK else None), float(alpha),
+                             _ptr(out["T_tilde"]), _ptr(out["D"]), _ptr(out["tau"]),
+                             _ptr(out.get("spec_norm")), _ptr(out.get("flags")), _stream(stream))
+    check(st, "taser_build_T")
+    return out
+
+
+def step_size(T_tilde, alpha=0.5, stream=None):
+    T = _dev(T_tilde, torch.float32, "T_tilde")
+    n, N, _ = T.shape
+    tau = torch.empty((n,), device=T.device, dtype=torch.float32)
+    nrm = torch.empty((n,), device=T.device, dtype=torch.float32)
+    check(lib().taser_step_size(n, N, _ptr(T), float(alpha), _ptr(tau), _ptr(nrm), _stream(stream)),
+          "taser_step_size")
+    return tau, nrm
+
+
+def detect(T_tilde, D, tau, t_max, precision="fp32", lnn_mode="fixed", want_L=True, flags=None,
+           out_s=None, out_L=None, stream=None):
+    """Algorithm 1 on every instance.  Returns (s_hat int8 [n,N-1], L or None, flags)."""
+    T = _dev(T_tilde, torch.float32, "T_tilde")
+    n, N, _ = T.shape
+    _dev(D, torch.float32, "D")
+    _dev(tau, torch.float32, "tau")
+    s = out_s if out_s is not None else torch.empty((n, N - 1), device=T.device, dtype=torch.int8)
+    L = out_L if out_L is not None else (
+        torch.empty((n, N, N), device=T.device, dtype=torch.float32) if want_L else None)
+    if flags is None:
+        flags = torch.zeros((n,), device=T.device, dtype=torch.int32)
+    st = lib().taser_detect(n, N, _ptr(T), _ptr(D), _ptr(tau), int(t_max), PRECISIONS[precision],
+                            LNN_MODES[lnn_mode], _ptr(L), _ptr(s), _ptr(flags), _stream(stream))
+    check(st, "taser_detect")
+    return s, L, flags
+
+
+def host_workspace_bytes(kind, batch, B, U_or_K):
+    return int(lib().taser_host_workspace_bytes(KINDS[kind], int(batch), int(B), int(U_or_K)))
+
+
+def run_host(kind, H_or_Y, y, alpha, t_max, precision, workspace, s_hat, flags=None, lnn_mode="fixed",
+             stream=None):
+    """End to end from host (ideally pinned) complex64 inputs to host int8 decisions.
+    `workspace` is a uint8 CUDA tensor of at least host_workspace_bytes(...) bytes."""
+    k = KINDS[kind]
+    n, B, M = H_or_Y.shape
+    for name, t in (("H_or_Y", H_or_Y), ("s_hat", s_hat)) + ((("y", y),) if k != JED_BPSK else ()):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous host tensor" % name)
+    _dev(workspace, torch.uint8, "workspace")
+    st = lib().taser_run_host(k, n, B, M, _ptr(H_or_Y), _ptr(y if k != JED_BPSK else None), float(alpha),
+                              int(t_max), PRECISIONS[precision], LNN_MODES[lnn_mode], _ptr(workspace),
+                              workspace.numel(), _ptr(s_hat), _ptr(flags), _stream(stream))
+    check(st, "taser_run_host")

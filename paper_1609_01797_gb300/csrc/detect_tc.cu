@@ -1,0 +1,292 @@
+// Tensor-core TASER iterations (Algorithm 1): the triangular product L~ T^ on the
+// tensor cores with BF16 or FP16 operands and FP32 accumulation; the master L~ and the
+// prox (column norms, rescaling) stay in FP32.
+//
+// One warp per instance.  L~ is kept in registers in the accumulator layout of
+// mma.m16n8k16: an accumulator pair of n-tiles (2k, 2k+1) is exactly the A operand of
+// k-tile k, so the next iteration's A operand is a register conversion, no shuffle or
+// shared-memory round trip.  The C operand is the FP32 master L~ and B = -2 tau T~, so
+// one mma gives V = L~ - L~ T^ directly.
+//
+// Tiles: rows are split into m-tiles of 16, variable columns into n-tiles of 8 and
+// k-tiles of 16.  Row block M (< NB/16) needs k-tiles 0..M and n-tiles 0..2M+1 only (L~
+// is lower-triangular, V is kept on and below the diagonal): the triangular skip of the
+// paper's array (Sec. IV-A) at tile granularity.  The augmented last row NB is one more
+// m-tile whose only live row is row NB; its L~_NN T^_{N,c} term is added in FP32.
+// The tensor-core instruction is the warp-level mma.sync: the per-instance operand B
+// changes with every instance and M is 33 rows, below the 64/128-row tiles of tcgen05.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "common.cuh"
+
+namespace taser {
+
+template <bool FP16>
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+  if constexpr (FP16) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&b);
+  }
+}
+
+template <bool FP16>
+__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  if constexpr (FP16) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  } else {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+}
+
+// Tile bookkeeping for bucket NB (16 or 32).
+template <int NB>
+struct TcCfg {
+  static constexpr int KT = NB / 16;     // k-tiles over the variable columns
+  static constexpr int NT = NB / 8;      // n-tiles over the variable columns
+  static constexpr int MT = KT + 1;      // m-tiles; the last holds row NB only
+  static constexpr int NV = 2 * NT;      // column-sum values per lane before reduction
+  static constexpr int WARPS = 4;
+  __host__ __device__ static constexpr bool has_tile(int M, int n) {
+    return M == MT - 1 ? true : n <= 2 * M + 1;
+  }
+  __host__ __device__ static constexpr int kmax(int M) { return M == MT - 1 ? KT - 1 : M; }
+};
+
+template <int NB, bool FP16>
+__global__ void __launch_bounds__(128)
+detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
+                 const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
+                 int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags) {
+  using C = TcCfg<NB>;
+  constexpr int KT = C::KT, NT = C::NT, MT = C::MT;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
+  if (inst >= batch) return;  // whole warp leaves together
+
+  const float* T = Tt + inst * (int64_t)N * N;
+  const float m2tau = -2.f * tau_g[inst];
+  auto tval = [&](int k, int n) -> float {  // -2 tau T~ at bucket indices (k, n < NB)
+    return (k < N - 1 && n < N - 1) ? m2tau * T[(int64_t)k * N + n] : 0.f;
+  };
+
+  // B operand: B[k][n] = -2 tau T~[k][n]; lane holds rows 2tq..2tq+1 and +8, column g.
+  uint32_t bf[KT][NT][2];
+#pragma unroll
+  for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
+      bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
+      bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
+    }
+  // Row N of T^ at this lane's accumulator columns c = 8n + 2tq + p (FP32).
+  float tN[NT][2];
+#pragma unroll
+  for (int nt = 0; nt < NT; ++nt)
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int c = 8 * nt + 2 * tq + p;
+      tN[nt][p] = c < N - 1 ? m2tau * T[(int64_t)(N - 1) * N + c] : 0.f;
+    }
+  const float tnNN = m2tau * T[(int64_t)(N - 1) * N + (N - 1)];
+  const float* Di = Dg + inst * (int64_t)N;
+  const float DN = Di[N - 1];
+  // After the column-sum reduction this lane owns column cown.
+  const int own_idx = NT == 4 ? g : (g >> 1);
+  const int cown = 8 * (own_idx >> 1) + 2 * tq + (own_idx & 1);
+  const float Down = cown < N - 1 ? Di[cown] : 0.f;
+
+  // L~(0) = D in accumulator layout: element (M, n, h, p) is row 16M + g + 8h, column
+  // 8n + 2tq + p.
+  float acc[MT][NT][4];
+#pragma unroll
+  for (int M = 0; M < MT; ++M)
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+        acc[M][n][e] = (M < MT - 1 && r == c && r < N - 1) ? Di[r] : 0.f;
+      }
+  float LNN = DN;
+  uint32_t fl = 0;
+
+  for (int t = 0; t < t_max; ++t) {
+    // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
+    float part = 0.f;
+#pragma unroll
+    for (int n = 0; n < NT; ++n) part = fmaf(acc[MT - 1][n][0], tN[n][0], fmaf(acc[MT - 1][n][1], tN[n][1], part));
+    part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
+    part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
+    part = __shfl_sync(TASER_FULL_MASK, part, 0);
+
+#pragma unroll
+    for (int M = 0; M < MT; ++M) {
+      // A operand of row block M from the FP32 master (old L~).
+      uint32_t a[KT][4];
+#pragma unroll
+      for (int kt = 0; kt <= C::kmax(M); ++kt) {
+        a[kt][0] = pack2<FP16>(acc[M][2 * kt][0], acc[M][2 * kt][1]);
+        a[kt][1] = pack2<FP16>(acc[M][2 * kt][2], acc[M][2 * kt][3]);
+        a[kt][2] = pack2<FP16>(acc[M][2 * kt + 1][0], acc[M][2 * kt + 1][1]);
+        a[kt][3] = pack2<FP16>(acc[M][2 * kt + 1][2], acc[M][2 * kt + 1][3]);
+      }
+      if (M == MT - 1) {
+        // k = N term of row N in FP32: L~_NN T^_{N,c}.
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          acc[M][n][0] = fmaf(LNN, g == 0 ? tN[n][0] : 0.f, acc[M][n][0]);
+          acc[M][n][1] = fmaf(LNN, g == 0 ? tN[n][1] : 0.f, acc[M][n][1]);
+        }
+      }
+#pragma unroll
+      for (int n = 0; n < NT; ++n) {
+        if (!C::has_tile(M, n)) continue;
+#pragma unroll
+        for (int kt = 0; kt <= C::kmax(M); ++kt) mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+      }
+    }
+    // Keep V lower-triangular inside the diagonal tiles.
+#pragma unroll
+    for (int M = 0; M < MT - 1; ++M)
+#pragma unroll
+      for (int n = 2 * M; n <= 2 * M + 1; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+          if (c > r) acc[M][n][e] = 0.f;
+        }
+
+    const float vnn = fmaf(LNN, tnNN, LNN) + part;
+    if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
+    if (literal) LNN = vnn >= 0.f ? DN : -DN;
+
+    // prox: column sums of squares, reduced over the 8 lanes sharing tq.
+    float s[C::NV];
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float v = 0.f;
+#pragma unroll
+        for (int M = 0; M < MT; ++M) {
+          if (!C::has_tile(M, n)) continue;
+          v = fmaf(acc[M][n][p], acc[M][n][p], v);
+          v = fmaf(acc[M][n][2 + p], acc[M][n][2 + p], v);
+        }
+        s[2 * n + p] = v;
+      }
+    // Transpose-reduce over lane bits 4, 3, 2: each step halves the values a lane keeps.
+    {
+      int len = C::NV;
+#pragma unroll
+      for (int m = 16; m >= 4; m >>= 1) {
+        const bool up = (lane & m) != 0;
+        if (len > 1) {
+          const int h = len >> 1;
+#pragma unroll
+          for (int i = 0; i < C::NV / 2; ++i) {
+            if (i >= h) break;
+            const float send = up ? s[i] : s[i + h];
+            const float keep = up ? s[i + h] : s[i];
+            s[i] = keep + __shfl_xor_sync(TASER_FULL_MASK, send, m);
+          }
+          len = h;
+        } else {
+          s[0] += __shfl_xor_sync(TASER_FULL_MASK, s[0], m);
+        }
+      }
+    }
+    float sc_own = 0.f;
+    if (s[0] > 0.f) {
+      sc_own = Down * rsqrtf(s[0]);
+    } else if (cown < N - 1) {
+      fl |= TASER_FLAG_ZERO_COLUMN;
+    }
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int idx = 2 * n + p;
+        const int src = 4 * (NT == 4 ? idx : 2 * idx) + tq;
+        const float sc = __shfl_sync(TASER_FULL_MASK, sc_own, src);
+#pragma unroll
+        for (int M = 0; M < MT; ++M) {
+          if (!C::has_tile(M, n)) continue;
+          acc[M][n][p] *= sc;
+          acc[M][n][2 + p] *= sc;
+        }
+      }
+  }
+
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
+  if (lane == 0 && flags != nullptr && fl) flags[inst] |= fl;
+
+  // Decisions from row N (lanes g == 0).
+  if (g == 0) {
+#pragma unroll
+    for (int n = 0; n < NT; ++n)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int c = 8 * n + 2 * tq + p;
+        if (c < N - 1) {
+          float r = acc[MT - 1][n][p];
+          if (literal && LNN < 0.f) r = -r;
+          s_hat[inst * (N - 1) + c] = r >= 0.f ? int8_t(1) : int8_t(-1);
+        }
+      }
+  }
+  if (Lout != nullptr) {
+    float* Lo = Lout + inst * (int64_t)N * N;
+#pragma unroll
+    for (int M = 0; M < MT; ++M)
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+          const int rr = bucket_to_real(r, N, NB);
+          if (rr < 0 || c >= N - 1) continue;
+          Lo[(int64_t)rr * N + c] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
+        }
+    for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+  }
+}
+
+template <int NB, bool FP16>
+static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                             int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
+  const int64_t blocks = (batch + TcCfg<NB>::WARPS - 1) / TcCfg<NB>::WARPS;
+  detect_tc_kernel<NB, FP16><<<(unsigned)blocks, 32 * TcCfg<NB>::WARPS, 0, st>>>(batch, N, Tt, D, tau, t_max,
+                                                                              literal, L, s, flags);
+  return cudaGetLastError();
+}
+
+// Returns cudaErrorNotSupported when the bucket has no tensor-core kernel.
+cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                      int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
+  switch (bucket_of(N)) {
+    case 16:
+      return fp16 ? launch_tc<16, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st)
+                  : launch_tc<16, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
+    case 32:
+      return fp16 ? launch_tc<32, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st)
+                  : launch_tc<32, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+}  // namespace taser

@@ -1,0 +1,230 @@
+// C ABI of libtaser: argument validation and kernel dispatch (see include/taser.h).
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+namespace taser {
+cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X, const void* y, float* Tt,
+                    float* D, uint32_t* flags, cudaStream_t st);
+cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, float* tau, float* nrm, cudaStream_t st);
+cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                        int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
+cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                      int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
+}  // namespace taser
+
+namespace {
+
+thread_local char g_err[512];
+
+taser_status fail(taser_status st, const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+  return st;
+}
+
+taser_status ok() {
+  g_err[0] = '\0';
+  return TASER_OK;
+}
+
+taser_status from_cuda(cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return ok();
+  return fail(TASER_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+#define TASER_REQUIRE(cond, ...)                                  \
+  do {                                                            \
+    if (!(cond)) return fail(TASER_ERR_INVALID_ARG, __VA_ARGS__); \
+  } while (0)
+
+#define TASER_REQUIRE_PTR(p, name)                                                        \
+  do {                                                                                    \
+    TASER_REQUIRE((p) != nullptr, "%s must not be NULL", name);                           \
+    TASER_REQUIRE(aligned16(p), "%s must be 16-byte aligned", name);                      \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+int taser_problem_size(int kind, int U_or_K) {
+  if (U_or_K <= 0) return -1;
+  switch (kind) {
+    case TASER_MIMO_BPSK: return U_or_K + 1;
+    case TASER_MIMO_QPSK: return 2 * U_or_K + 1;
+    case TASER_SIMO_JED_BPSK: return U_or_K;
+    default: return -1;
+  }
+}
+
+const char* taser_status_string(int status) {
+  switch (status) {
+    case TASER_OK: return "ok";
+    case TASER_ERR_INVALID_ARG: return "invalid argument";
+    case TASER_ERR_UNSUPPORTED: return "unsupported configuration";
+    case TASER_ERR_CUDA: return "CUDA error";
+    case TASER_ERR_TIMEOUT: return "device wait timed out";
+    case TASER_ERR_NUMERIC: return "numeric error";
+    default: return "unknown status";
+  }
+}
+
+const char* taser_last_error(void) { return g_err; }
+
+taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y, const void* y,
+                           float alpha, float* T_tilde, float* D, float* tau, float* spec_norm, uint32_t* flags,
+                           void* stream) {
+  TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK,
+                "unknown problem kind %d", kind);
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(B >= 1, "B must be >= 1 (got %d)", B);
+  TASER_REQUIRE(alpha > 0.f && alpha < 1.f, "alpha must lie in (0, 1) (got %g)", (double)alpha);
+  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  if (jed) {
+    TASER_REQUIRE(U_or_K >= 2 && U_or_K <= 33, "JED needs 2 <= K <= 33 (got %d)", U_or_K);
+    TASER_REQUIRE(y == nullptr, "y must be NULL for JED");
+  } else {
+    TASER_REQUIRE(U_or_K >= 1 && U_or_K <= 32, "MIMO needs 1 <= U <= 32 (got %d)", U_or_K);
+  }
+  const int N = taser_problem_size(kind, U_or_K);
+  TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "problem size N = %d outside [2, %d]", N, TASER_MAX_N);
+  if (batch == 0) return ok();
+  TASER_REQUIRE_PTR(H_or_Y, "H_or_Y");
+  if (!jed) TASER_REQUIRE_PTR(y, "y");
+  TASER_REQUIRE_PTR(T_tilde, "T_tilde");
+  TASER_REQUIRE_PTR(D, "D");
+  TASER_REQUIRE_PTR(tau, "tau");
+  if (spec_norm != nullptr) TASER_REQUIRE(aligned16(spec_norm), "spec_norm must be 16-byte aligned");
+  if (flags != nullptr) TASER_REQUIRE(aligned16(flags), "flags must be 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int P = jed ? U_or_K - 1 : U_or_K;
+  cudaError_t e = taser::build_T(kind, batch, B, P, N, H_or_Y, y, T_tilde, D, flags, st);
+  if (e == cudaErrorNotSupported) return fail(TASER_ERR_UNSUPPORTED, "no build kernel for %d columns", P + 1);
+  if (e != cudaSuccess) return from_cuda(e, "build_T");
+  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, tau, spec_norm, st), "spectral");
+}
+
+taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, float alpha, float* tau, float* spec_norm,
+                             void* stream) {
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
+  TASER_REQUIRE(alpha > 0.f && alpha < 1.f, "alpha must lie in (0, 1) (got %g)", (double)alpha);
+  if (batch == 0) return ok();
+  TASER_REQUIRE_PTR(T_tilde, "T_tilde");
+  TASER_REQUIRE_PTR(tau, "tau");
+  if (spec_norm != nullptr) TASER_REQUIRE(aligned16(spec_norm), "spec_norm must be 16-byte aligned");
+  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, tau, spec_norm, static_cast<cudaStream_t>(stream)),
+                   "spectral");
+}
+
+taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const float* D, const float* tau, int t_max,
+                          int precision, int lnn_mode, float* L, int8_t* s_hat, uint32_t* flags, void* stream) {
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
+  TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC,
+                "unknown precision %d", precision);
+  TASER_REQUIRE(lnn_mode == TASER_LNN_FIXED || lnn_mode == TASER_LNN_LITERAL, "unknown lnn_mode %d", lnn_mode);
+  if (batch == 0) return ok();
+  TASER_REQUIRE_PTR(T_tilde, "T_tilde");
+  TASER_REQUIRE_PTR(D, "D");
+  TASER_REQUIRE_PTR(tau, "tau");
+  TASER_REQUIRE_PTR(s_hat, "s_hat");
+  if (L != nullptr) TASER_REQUIRE(aligned16(L), "L must be 16-byte aligned");
+  if (flags != nullptr) TASER_REQUIRE(aligned16(flags), "flags must be 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int literal = lnn_mode == TASER_LNN_LITERAL;
+  if (precision != TASER_FP32 && taser::bucket_of(N) >= 16 && taser::bucket_of(N) <= 32) {
+    return from_cuda(taser::detect_tc(batch, N, T_tilde, D, tau, t_max, literal, precision == TASER_FP16_TC, L,
+                                      s_hat, flags, st),
+                     "detect_tc");
+  }
+  return from_cuda(taser::detect_fp32(batch, N, T_tilde, D, tau, t_max, literal, L, s_hat, flags, st),
+                   "detect_fp32");
+}
+
+}  // extern "C"
+
+namespace {
+struct HostLayout {
+  size_t x, y, t, d, tau, s, flags, total;
+};
+size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
+bool host_layout(int kind, int64_t batch, int B, int M, HostLayout& L) {
+  const int N = taser_problem_size(kind, M);
+  if (N < 2 || batch < 0 || B < 1) return false;
+  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  size_t off = 0;
+  L.x = off; off = up256(off + size_t(batch) * B * M * 8);
+  L.y = off; off = up256(off + (jed ? 0 : size_t(batch) * B * 8));
+  L.t = off; off = up256(off + size_t(batch) * N * N * 4);
+  L.d = off; off = up256(off + size_t(batch) * N * 4);
+  L.tau = off; off = up256(off + size_t(batch) * 4);
+  L.s = off; off = up256(off + size_t(batch) * (N - 1));
+  L.flags = off; off = up256(off + size_t(batch) * 4);
+  L.total = off;
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+size_t taser_host_workspace_bytes(int kind, int64_t batch, int B, int U_or_K) {
+  HostLayout L;
+  if (!host_layout(kind, batch, B, U_or_K, L)) return 0;
+  return L.total;
+}
+
+taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y, const void* y,
+                            float alpha, int t_max, int precision, int lnn_mode, void* workspace,
+                            size_t workspace_bytes, int8_t* s_hat, uint32_t* flags, void* stream) {
+  TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK,
+                "unknown problem kind %d", kind);
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
+  HostLayout L;
+  TASER_REQUIRE(host_layout(kind, batch, B, U_or_K, L), "invalid problem shape");
+  if (batch == 0) return ok();
+  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  TASER_REQUIRE(H_or_Y != nullptr, "H_or_Y must not be NULL");
+  TASER_REQUIRE(jed || y != nullptr, "y must not be NULL");
+  TASER_REQUIRE(s_hat != nullptr, "s_hat must not be NULL");
+  TASER_REQUIRE(workspace != nullptr && (reinterpret_cast<uintptr_t>(workspace) & 255u) == 0,
+                "workspace must be a 256-byte aligned device pointer");
+  TASER_REQUIRE(workspace_bytes >= L.total, "workspace too small: %zu < %zu bytes", workspace_bytes, L.total);
+  const int N = taser_problem_size(kind, U_or_K);
+  char* w = static_cast<char*>(workspace);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaMemcpyAsync(w + L.x, H_or_Y, size_t(batch) * B * U_or_K * 8, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return from_cuda(e, "copy H_or_Y");
+  if (!jed) {
+    e = cudaMemcpyAsync(w + L.y, y, size_t(batch) * B * 8, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return from_cuda(e, "copy y");
+  }
+  float* Tt = reinterpret_cast<float*>(w + L.t);
+  float* D = reinterpret_cast<float*>(w + L.d);
+  float* tau = reinterpret_cast<float*>(w + L.tau);
+  int8_t* s = reinterpret_cast<int8_t*>(w + L.s);
+  uint32_t* fl = reinterpret_cast<uint32_t*>(w + L.flags);
+  taser_status rs = taser_build_T(kind, batch, B, U_or_K, w + L.x, jed ? nullptr : w + L.y, alpha, Tt, D, tau,
+                                  nullptr, fl, stream);
+  if (rs != TASER_OK) return rs;
+  rs = taser_detect(batch, N, Tt, D, tau, t_max, precision, lnn_mode, nullptr, s, fl, stream);
+  if (rs != TASER_OK) return rs;
+  e = cudaMemcpyAsync(s_hat, s, size_t(batch) * (N - 1), cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return from_cuda(e, "copy s_hat");
+  if (flags != nullptr) {
+    e = cudaMemcpyAsync(flags, fl, size_t(batch) * 4, cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return from_cuda(e, "copy flags");
+  }
+  return ok();
+}
+
+}  // extern "C"

@@ -1,0 +1,234 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Tolerances (written here, derived in the design doc):
+  * FP32 iterations: relative Frobenius error of L~ <= 1e-5 per instance; decisions
+    identical wherever |L~_{N,k}| > 1e-3 ||l~_N||.
+  * BF16 / FP16 tensor-core iterations: relative Frobenius error <= 3e-2; decisions
+    identical wherever |L~_{N,k}| > 5e-2 ||l~_N||.
+  * T~ (FP32 Gram of B complex rows): |T~_gpu - T~| <= 2e-5, D and tau within 1e-5
+    relative.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import taser_oracle as O
+from synth import make_jed, make_mimo
+
+pytestmark = pytest.mark.gpu
+
+ALPHA = 0.5
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_01797_gb300 as taser
+    return taser
+
+
+def rel_frob(A, B):
+    return np.linalg.norm(A - B, axis=(1, 2)) / np.linalg.norm(B, axis=(1, 2))
+
+
+def confident(Lo, margin):
+    row = Lo[:, -1, :]
+    return np.abs(row[:, :-1]) > margin * np.linalg.norm(row, axis=1, keepdims=True)
+
+
+def oracle_inputs(N, n, seed, snr=5.0):
+    """Oracle-built (T~, D, tau) of BPSK MIMO instances with U = N-1 users, rounded to fp32."""
+    U = N - 1
+    w = make_mimo(n, max(2 * U, 4), U, snr, "bpsk", seed=seed)
+    r = O.detect("mimo_bpsk", w["H"], w["y"], ALPHA, 1)
+    return (r["T_tilde"].astype(np.float32), r["D"].astype(np.float32), r["tau"].astype(np.float32))
+
+
+def to_dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+SIZES = [2, 3, 5, 9, 10, 16, 17, 18, 31, 32, 33, 34, 50, 64, 65]
+
+
+@pytest.mark.parametrize("N", SIZES)
+@pytest.mark.parametrize("t_max", [1, 20])
+@pytest.mark.parametrize("mode", ["fixed", "literal"])
+def test_detect_fp32_matches_oracle(T, N, t_max, mode):
+    n = 67 if N > 32 else 131                       # several CTAs and a ragged tail
+    Tt, D, tau = oracle_inputs(N, n, seed=1000 + N)
+    Lo, fo = O.taser(Tt.astype(np.float64), D.astype(np.float64), tau.astype(np.float64), t_max, mode)
+    so = O.decisions(Lo, mode)
+    dT, dD, dtau = to_dev(Tt, D, tau)
+    s, L, flags = T.detect(dT, dD, dtau, t_max, "fp32", mode)
+    torch.cuda.synchronize()
+    L = L.cpu().numpy().astype(np.float64)
+    err = rel_frob(L, Lo)
+    assert err.max() <= 1e-5, (err.max(), int(err.argmax()))
+    assert np.all(np.triu(L, 1) == 0)
+    m = confident(Lo, 1e-3)
+    np.testing.assert_array_equal(s.cpu().numpy()[m], so[m])
+    got = flags.cpu().numpy().astype(np.uint32)
+    np.testing.assert_array_equal(got & O.FLAG_ZERO_COLUMN, fo & O.FLAG_ZERO_COLUMN)
+
+
+@pytest.mark.parametrize("N", [10, 16, 17, 24, 32, 33])
+@pytest.mark.parametrize("precision", ["bf16_tc", "fp16_tc"])
+@pytest.mark.parametrize("t_max", [1, 20])
+def test_detect_tensor_core_matches_oracle(T, N, precision, t_max):
+    n = 133
+    Tt, D, tau = oracle_inputs(N, n, seed=2000 + N)
+    Lo, _ = O.taser(Tt.astype(np.float64), D.astype(np.float64), tau.astype(np.float64), t_max)
+    so = O.decisions(Lo)
+    dT, dD, dtau = to_dev(Tt, D, tau)
+    s, L, _ = T.detect(dT, dD, dtau, t_max, precision)
+    torch.cuda.synchronize()
+    L = L.cpu().numpy().astype(np.float64)
+    err = rel_frob(L, Lo)
+    assert err.max() <= 3e-2, err.max()
+    # column norms are restored by the FP32 prox every iteration
+    np.testing.assert_allclose(np.linalg.norm(L[:, :, :-1], axis=1), D[:, :-1], rtol=1e-5)
+    m = confident(Lo, 5e-2)
+    np.testing.assert_array_equal(s.cpu().numpy()[m], so[m])
+
+
+def test_tensor_core_falls_back_to_fp32_below_10(T):
+    Tt, D, tau = oracle_inputs(9, 40, seed=77)
+    dT, dD, dtau = to_dev(Tt, D, tau)
+    s1, L1, _ = T.detect(dT, dD, dtau, 10, "fp32")
+    s2, L2, _ = T.detect(dT, dD, dtau, 10, "bf16_tc")
+    assert torch.equal(L1, L2) and torch.equal(s1, s2)
+
+
+BUILD_CASES = [("mimo_bpsk", 32, 8), ("mimo_bpsk", 7, 3), ("mimo_bpsk", 64, 16), ("mimo_bpsk", 96, 32),
+               ("mimo_qpsk", 128, 16), ("mimo_qpsk", 32, 4), ("mimo_qpsk", 64, 8), ("mimo_qpsk", 13, 5),
+               ("mimo_qpsk", 256, 32), ("mimo_qpsk", 200, 12), ("jed_bpsk", 16, 16), ("jed_bpsk", 16, 32),
+               ("jed_bpsk", 5, 2), ("jed_bpsk", 40, 9)]
+
+
+@pytest.mark.parametrize("kind,B,M", BUILD_CASES)
+def test_build_T_matches_oracle(T, kind, B, M):
+    n = 37
+    if kind == "jed_bpsk":
+        w = make_jed(n, B, M, 6.0, seed=B * 100 + M)
+        X, y = w["Y"], None
+    else:
+        w = make_mimo(n, B, M, 6.0, kind[5:], seed=B * 100 + M)
+        X, y = w["H"], w["y"]
+    r = O.detect(kind, X, y, ALPHA, 1)
+    out = T.build_T(kind, *to_dev(X), None if y is None else to_dev(y)[0], alpha=ALPHA)
+    torch.cuda.synchronize()
+    Tt = out["T_tilde"].cpu().numpy()
+    assert np.abs(Tt - r["T_tilde"]).max() <= 2e-5
+    np.testing.assert_allclose(out["D"].cpu().numpy(), r["D"], rtol=1e-5)
+    np.testing.assert_allclose(out["spec_norm"].cpu().numpy(), O.spectral_norm(r["T_tilde"]), rtol=1e-5)
+    np.testing.assert_allclose(out["tau"].cpu().numpy(), r["tau"], rtol=1e-5)
+    assert (out["flags"].cpu().numpy() == 0).all()
+
+
+def test_step_size_closed_forms(T):
+    rng = np.random.default_rng(5)
+    mats, want = [], []
+    for N in (2, 9, 17, 33, 65):
+        b = rng.uniform(-0.2, 0.2, size=N - 1)
+        M = np.eye(N)
+        M[:-1, -1] = b
+        M[-1, :-1] = b
+        mats.append(M)
+        want.append(1 + np.linalg.norm(b))                     # bordered identity
+        s = rng.choice([-1.0, 1.0], size=N)
+        mats.append(-np.outer(s, s))
+        want.append(float(N))                                  # -s s^T
+    for M, w in zip(mats, want):
+        tau, nrm = T.step_size(to_dev(M.astype(np.float32)[None])[0], 0.5)
+        np.testing.assert_allclose(nrm.cpu().numpy()[0], w, rtol=1e-5)
+        np.testing.assert_allclose(tau.cpu().numpy()[0], 0.5 / w, rtol=1e-5)
+
+
+@pytest.mark.parametrize("N", [2, 5, 9, 16, 17, 30, 33, 47, 65])
+def test_step_size_matches_oracle(T, N):
+    rng = np.random.default_rng(N)
+    A = rng.standard_normal((29, N, N))
+    M = (A + np.transpose(A, (0, 2, 1))) / 2
+    M = M.astype(np.float32)
+    tau, nrm = T.step_size(to_dev(M)[0], 0.3)
+    np.testing.assert_allclose(nrm.cpu().numpy(), O.spectral_norm(M.astype(np.float64)), rtol=1e-5)
+
+
+@pytest.mark.parametrize("kind,B,M,t_max,precision", [
+    ("mimo_bpsk", 32, 8, 10, "fp32"), ("mimo_qpsk", 128, 16, 20, "fp32"), ("jed_bpsk", 16, 16, 20, "fp32"),
+    ("jed_bpsk", 16, 32, 20, "fp32"), ("mimo_qpsk", 64, 8, 20, "fp32"), ("mimo_qpsk", 256, 32, 10, "fp32"),
+    ("mimo_qpsk", 128, 16, 20, "bf16_tc"), ("mimo_qpsk", 128, 16, 20, "fp16_tc"), ("jed_bpsk", 16, 32, 20, "bf16_tc")])
+def test_end_to_end_matches_oracle(T, kind, B, M, t_max, precision):
+    n = 203
+    snr = np.linspace(0.0, 20.0, n)
+    if kind == "jed_bpsk":
+        w = make_jed(n, B, M, np.linspace(0, 12, n), seed=7 + M)
+        X, y, truth = w["Y"], None, w["s"][:, 1:]
+    else:
+        w = make_mimo(n, B, M, snr, kind[5:], seed=7 + M)
+        X, y = w["H"], w["y"]
+        truth = w["bits_re"] if kind == "mimo_bpsk" else np.concatenate([w["bits_re"], w["bits_im"]], 1)
+    r = O.detect(kind, X, y, ALPHA, t_max)
+    out = T.build_T(kind, *to_dev(X), None if y is None else to_dev(y)[0], alpha=ALPHA)
+    s, L, flags = T.detect(out["T_tilde"], out["D"], out["tau"], t_max, precision, flags=out["flags"])
+    torch.cuda.synchronize()
+    L = L.cpu().numpy().astype(np.float64)
+    err = rel_frob(L, r["L"])
+    tol = 1e-5 if precision == "fp32" else 3e-2
+    assert err.max() <= tol, (err.max(), int(err.argmax()))
+    m = confident(r["L"], 1e-3 if precision == "fp32" else 5e-2)
+    s = s.cpu().numpy()
+    np.testing.assert_array_equal(s[m], r["s_hat"][m])
+    # errors against the transmitted symbols agree with the oracle's up to unconfident entries
+    assert abs(int((s != truth).sum()) - int((r["s_hat"] != truth).sum())) <= int((~m).sum())
+
+
+def test_zero_channel_column_is_flagged(T):
+    w = make_mimo(9, 16, 4, 10.0, "qpsk", seed=3)
+    H = w["H"].copy()
+    H[2, :, 1] = 0
+    r = O.detect("mimo_qpsk", H, w["y"], ALPHA, 5)
+    out = T.build_T("mimo_qpsk", *to_dev(H, w["y"]), alpha=ALPHA)
+    s, L, flags = T.detect(out["T_tilde"], out["D"], out["tau"], 5, "fp32", flags=out["flags"])
+    torch.cuda.synchronize()
+    f = flags.cpu().numpy().astype(np.uint32)
+    assert f[2] & O.FLAG_ZERO_DIAG and (f[[0, 1, 3, 4, 5, 6, 7, 8]] & O.FLAG_ZERO_DIAG == 0).all()
+    np.testing.assert_array_equal(out["D"].cpu().numpy()[2], r["D"][2].astype(np.float32))
+
+
+def test_nonfinite_input_is_flagged(T):
+    w = make_mimo(5, 16, 4, 10.0, "bpsk", seed=4)
+    H = w["H"].copy()
+    H[1, 3, 2] = np.nan
+    out = T.build_T("mimo_bpsk", *to_dev(H, w["y"]), alpha=ALPHA)
+    torch.cuda.synchronize()
+    f = out["flags"].cpu().numpy().astype(np.uint32)
+    assert f[1] & O.FLAG_NONFINITE and (f[[0, 2, 3, 4]] == 0).all()
+
+
+@pytest.mark.parametrize("precision", ["fp32", "bf16_tc"])
+def test_full_size_qpsk_128x16_sampled(T, precision):
+    """The benchmark's workload (65,536 QPSK 128x16 instances, t_max = 20, SNR 0..20 dB)
+    in the benchmark's launch configuration: sampled instances against the oracle, and
+    properties that hold at any size on all of them."""
+    n = 65536
+    snr = np.tile(np.arange(0.0, 21.0, 2.0), n // 11 + 1)[:n]
+    w = make_mimo(n, 128, 16, snr, "qpsk", seed=1)
+    out = T.build_T("mimo_qpsk", *to_dev(w["H"], w["y"]), alpha=ALPHA)
+    s, L, flags = T.detect(out["T_tilde"], out["D"], out["tau"], 20, precision, flags=out["flags"])
+    torch.cuda.synchronize()
+    idx = np.random.default_rng(0).choice(n, size=192, replace=False)
+    r = O.detect("mimo_qpsk", w["H"][idx], w["y"][idx], ALPHA, 20)
+    Ls = L[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    err = rel_frob(Ls, r["L"])
+    assert err.max() <= (1e-5 if precision == "fp32" else 3e-2)
+    m = confident(r["L"], 1e-3 if precision == "fp32" else 5e-2)
+    np.testing.assert_array_equal(s.cpu().numpy()[idx][m], r["s_hat"][m])
+    # all instances: lower-triangular, column norms D, decisions +-1
+    Lg = L
+    assert torch.all(torch.triu(Lg, 1) == 0)
+    cn = torch.linalg.vector_norm(Lg, dim=1)
+    assert torch.allclose(cn, out["D"], rtol=1e-4)
+    assert torch.all(s.abs() == 1)
