@@ -5,86 +5,102 @@
 // X = [H, y] (MIMO) or X = [Y_1 .. Y_{K-1}, Y_0] (JED, pilot moved last), because
 //   Hbar^T Hbar = [[Re G, -Im G], [Im G, Re G]],  Hbar^T ybar = [Re z; Im z]   (QPSK)
 //   Hunder^T Hunder = Re G,  Hunder^T ybar = Re z                               (BPSK, JED)
-// with G = H^H H and z = H^H y.  Reading the complex input once, this halves the work
-// of the real route and the B x M input is the only HBM traffic besides T~ and D.
+// with G = H^H H and z = H^H y.  The complex input is read once; it is the only HBM
+// traffic besides the T~ and D outputs.
 //
-// Mapping: one warp per instance.  X is staged in shared memory 128 (or 64) antennas at a
-// time with cp.async; each lane takes whole antenna rows and accumulates a pass of 32 (or
-// 16) Gram entries in registers (register-only FFMAs), then a 5-step transpose-reduce
-// over the lanes leaves every lane with complete sums for one entry (or half of one).  Entries are
-// enumerated cyclically (entry (a, d) is Gamma[a][(a + d) mod MP], d <= (MP-1)/2), which
-// covers each unordered pair once.
+// Gamma comes from the real Gram G' = W^T W of W = X viewed as B x 2M floats (real and
+// imaginary parts interleaved, exactly the complex64 memory layout):
+//   Re Gamma_pq = G'[2p][2q] + G'[2p+1][2q+1],   Im Gamma_pq = G'[2p][2q+1] - G'[2p+1][2q].
+// G' is a dense contraction over the B antennas, so it runs on the tensor cores with
+// mma.sync m16n8k8 TF32 in the split form x = hi + lo (hi = tf32(x), lo = tf32(x - hi)),
+// G' = hi^T hi + hi^T lo + lo^T hi, which keeps FP32-level accuracy (relative error about
+// 2^-22 per product) while the reduction over B happens inside the tensor core.
+//
+// Mapping: one warp per instance.  X is staged into shared memory 32 antennas at a time
+// (double-buffered cp.async); only the upper-triangular 16 x 8 tiles of G' are computed.
 #include "common.cuh"
 
 namespace taser {
 
 template <int MP>
 struct BuildCfg {
-  static constexpr int E = MP * (MP + 1) / 2;        // Gram entries
-  static constexpr int DMAX = (MP - 1) / 2;
-  static constexpr int SLOTS = MP <= 17 ? 32 : 16;   // entries per pass
-  static constexpr int NVAL = 2 * SLOTS;             // floats reduced per pass
-  static constexpr int PASSES = (E + SLOTS - 1) / SLOTS;
-  static constexpr int CH = MP <= 17 ? 128 : 64;     // antennas per staged chunk
-  static constexpr int RPL = CH / 32;                // antennas per lane per chunk
+  static constexpr int NCR = 2 * MP;                  // real columns of W
+  static constexpr int NT = (NCR + 7) / 8;            // n-tiles of 8 columns
+  static constexpr int MT = (NCR + 15) / 16;          // m-tiles of 16 columns
+  // Row stride (floats) of a staged antenna row: >= 8 NT and = 8 or 24 mod 32, so the
+  // fragment loads (rows t and t + 4, columns 8j + g) hit 32 distinct banks.
+  static constexpr int WS = (8 * NT) % 32 == 8 || (8 * NT) % 32 == 24 ? 8 * NT : 8 * NT + 8;
+  static constexpr int CH = 32;                       // antennas per staged chunk
+  static constexpr int BUF_FLOATS = CH * WS;
   static constexpr int WARPS = 4;
-  static constexpr int X_FLOATS = CH * MP * 2;
-  static constexpr int G_FLOATS = NVAL * PASSES;
-  static constexpr int WARP_FLOATS = X_FLOATS + G_FLOATS;
+  static constexpr int WARP_FLOATS = 2 * BUF_FLOATS;  // double buffer; reused by the epilogue
   static constexpr int SMEM_BYTES = WARPS * WARP_FLOATS * 4;
+  __host__ __device__ static constexpr bool tile(int i, int j) { return j >= 2 * i && j < NT; }
 };
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(d), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NLEFT>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NLEFT) : "memory"); }
 
-template <int MP>
-__device__ __forceinline__ float2 gram_at(const float* Gs, int p, int q) {
-  using C = BuildCfg<MP>;
-  int d = q - p;
-  if (d < 0) d += MP;
-  if (d <= C::DMAX) {
-    const int e = d * MP + p;
-    return make_float2(Gs[2 * e], Gs[2 * e + 1]);
-  }
-  const int e = (MP - d) * MP + q;  // stored as Gamma[q][p] = conj(Gamma[p][q])
-  return make_float2(Gs[2 * e], -Gs[2 * e + 1]);
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // Real index a of T -> (complex column of X, part): part 0 = real, 1 = imaginary,
 // 2 = the augmented column.
 __device__ __forceinline__ void t_index(int kind, int a, int P, int MP, int& col, int& part) {
-  if (kind == TASER_MIMO_QPSK) {
-    if (a < P) { col = a; part = 0; }
-    else if (a < 2 * P) { col = a - P; part = 1; }
-    else { col = MP - 1; part = 2; }
+  if (kind == TASER_MIMO_QPSK && a >= P && a < 2 * P) {
+    col = a - P;
+    part = 1;
+  } else if (a < P) {
+    col = a;
+    part = 0;
   } else {
-    if (a < P) { col = a; part = 0; }
-    else { col = MP - 1; part = 2; }
+    col = MP - 1;
+    part = 2;
   }
 }
 
-template <int MP>
-__device__ __forceinline__ float t_entry(const float* Gs, int kind, int P, int a, int b) {
-  int ca, pa, cb, pb;
-  t_index(kind, a, P, MP, ca, pa);
-  t_index(kind, b, P, MP, cb, pb);
-  const float2 g = gram_at<MP>(Gs, ca, cb);
-  if (kind == TASER_SIMO_JED_BPSK) return -g.x;
-  if (kind == TASER_MIMO_BPSK) return (pa == 2) == (pb == 2) ? g.x : -g.x;
-  // QPSK with the effective channel H / sqrt2.
+// T_ab = cr * Re(Gamma[col_a][col_b]) + ci * Im(Gamma[col_a][col_b]).
+//   QPSK (effective channel H / sqrt2, c = 1/sqrt2):
+//     user-user  [[Re G, -Im G], [Im G, Re G]] / 2;  user-aug -c [Re z; Im z];  aug-aug ||y||^2
+//   BPSK: Re G, -Re z, ||y||^2.   JED: -Re Gamma.
+__device__ __forceinline__ void t_coef(int kind, int pa, int pb, float& cr, float& ci) {
   const float c = 0.70710678118654752f;
-  if (pa == 2 && pb == 2) return g.x;
-  if (pa == 2 || pb == 2) {
-    // one augmented index: -c * (Re or Im) of Gamma[user][aug]
-    const int pu = pa == 2 ? pb : pa;
-    const float2 z = pa == 2 ? make_float2(g.x, -g.y) : g;  // Gamma[user][aug]
-    return -c * (pu == 0 ? z.x : z.y);
+  cr = 0.f;
+  ci = 0.f;
+  if (kind == TASER_SIMO_JED_BPSK) {
+    cr = -1.f;
+  } else if (kind == TASER_MIMO_BPSK) {
+    cr = ((pa == 2) == (pb == 2)) ? 1.f : -1.f;
+  } else if (pa == 2 && pb == 2) {
+    cr = 1.f;
+  } else if (pa == 2) {          // Gamma[aug][user] = conj(z_user)
+    if (pb == 0) cr = -c; else ci = c;
+  } else if (pb == 2) {          // Gamma[user][aug] = z_user
+    if (pa == 0) cr = -c; else ci = -c;
+  } else if (pa == pb) {
+    cr = 0.5f;
+  } else {
+    ci = pa == 0 ? -0.5f : 0.5f;
   }
-  if (pa == pb) return 0.5f * g.x;
-  return pa == 0 ? -0.5f * g.y : 0.5f * g.y;
 }
 
 template <int MP>
@@ -93,107 +109,154 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
                const float2* __restrict__ yv, float* __restrict__ Tt, float* __restrict__ Dout,
                uint32_t* __restrict__ flags) {
   using C = BuildCfg<MP>;
+  constexpr int NT = C::NT, MT = C::MT, WS = C::WS, CH = C::CH;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
   const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
   if (inst >= batch) return;
-  float* Xs = smem + warp * C::WARP_FLOATS;
-  float* Gs = Xs + C::X_FLOATS;
-  float2* Xc = reinterpret_cast<float2*>(Xs);
+  float* Ws = smem + warp * C::WARP_FLOATS;
 
-  for (int i = lane; i < C::G_FLOATS; i += 32) Gs[i] = 0.f;
-  // Padding columns P..MP-2 stay zero for the whole kernel.
-  if (P < MP - 1) {
-    for (int i = lane; i < C::CH * MP; i += 32) Xc[i] = make_float2(0.f, 0.f);
-  }
+  // Padding columns (2P .. 2MP-3 and >= 2MP) stay zero for the whole Gram phase.
+  for (int i = lane; i < C::WARP_FLOATS; i += 32) Ws[i] = 0.f;
+  __syncwarp();
   const bool jed = kind == TASER_SIMO_JED_BPSK;
-  const int src_cols = jed ? P + 1 : P;                 // columns per antenna row in X
+  const int src_cols = jed ? P + 1 : P;                 // complex columns per antenna row
   const float2* Xi = X + inst * (int64_t)B * src_cols;
   const float2* yi = jed ? nullptr : yv + inst * (int64_t)B;
-  // lane -> (row offset, column) for the staging copy
-  const int rows_per_iter = P <= 32 ? 32 / P : 1;
-  const int cr = lane / P, cc = lane % P;
+  const bool pairs = !jed && (P % 2 == 0) && ((reinterpret_cast<uintptr_t>(Xi) & 15) == 0);
+  const int units = pairs ? P / 2 : P;                  // copy units per antenna row
+  const int rows_per_iter = units <= 32 ? 32 / units : 1;
+  const int crow = lane / units, cu = lane % units;
+  const int nchunks = (B + CH - 1) / CH;
 
-  for (int r0 = 0; r0 < B; r0 += C::CH) {
-    const int rows = min(C::CH, B - r0);
-    __syncwarp();
-    if (rows < C::CH) {
-      for (int i = rows * MP + lane; i < C::CH * MP; i += 32) Xc[i] = make_float2(0.f, 0.f);
-    }
-    // Stage X[r0 .. r0+rows) into padded rows of MP complex values.
-    if (P <= 32) {
-      if (cr < rows_per_iter) {
-        for (int r = cr; r < rows; r += rows_per_iter) {
-          const float2* src = Xi + (int64_t)(r0 + r) * src_cols + (jed ? cc + 1 : cc);
-          cp_async8(&Xc[r * MP + cc], src);
-        }
+  auto stage = [&](int chunk) {
+    float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
+    const int r0 = chunk * CH;
+    const int rows = min(CH, B - r0);
+    if (crow < rows_per_iter) {
+      for (int r = crow; r < rows; r += rows_per_iter) {
+        const float2* src = Xi + (int64_t)(r0 + r) * src_cols;
+        if (pairs) cp_async16(buf + r * WS + 4 * cu, src + 2 * cu);
+        else cp_async8(buf + r * WS + 2 * cu, src + (jed ? cu + 1 : cu));
       }
     }
     for (int r = lane; r < rows; r += 32) {
       const float2* src = jed ? Xi + (int64_t)(r0 + r) * src_cols : yi + (r0 + r);
-      cp_async8(&Xc[r * MP + MP - 1], src);
+      cp_async8(buf + r * WS + 2 * (MP - 1), src);
     }
-    cp_async_wait_all();
-    __syncwarp();
+    cp_async_commit();
+  };
 
-    const int nrr = (rows + 31) >> 5;  // antenna rows per lane in this chunk
+  float acc[MT][NT][4];
 #pragma unroll
-    for (int pass = 0; pass < C::PASSES; ++pass) {
-      float acc[C::NVAL];
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-      for (int i = 0; i < C::NVAL; ++i) acc[i] = 0.f;
-#pragma unroll 1
-      for (int rr = 0; rr < nrr; ++rr) {
-        const float2* xr = Xc + (lane + 32 * rr) * MP;
-        float2 x[MP];
+    for (int j = 0; j < NT; ++j)
 #pragma unroll
-        for (int c = 0; c < MP; ++c) x[c] = xr[c];  // unused columns are dead loads
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+  stage(0);
+  if (nchunks > 1) stage(1);
+  for (int chunk = 0; chunk < nchunks; ++chunk) {
+    if (chunk + 1 < nchunks) cp_async_wait<1>(); else cp_async_wait<0>();
+    __syncwarp();
+    float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
+    const int rows = min(CH, B - chunk * CH);
+    if (rows < CH) {  // zero the unused tail rows of the last chunk
+      for (int i = rows * WS + lane; i < CH * WS; i += 32) buf[i] = 0.f;
+      __syncwarp();
+    }
 #pragma unroll
-        for (int s = 0; s < C::SLOTS; ++s) {
-          const int e = pass * C::SLOTS + s;  // compile-time after unrolling
-          if (e < C::E) {
-            const int a = e % MP, d = e / MP;
-            const int b = (a + d) % MP;
-            // conj(x_a) x_b
-            acc[2 * s] = fmaf(x[a].x, x[b].x, fmaf(x[a].y, x[b].y, acc[2 * s]));
-            if (d != 0) acc[2 * s + 1] = fmaf(x[a].x, x[b].y, fmaf(-x[a].y, x[b].x, acc[2 * s + 1]));
+    for (int ks = 0; ks < CH / 8; ++ks) {
+      // B fragments of every n-tile (k = 8 ks + tq, 8 ks + tq + 4; column 8j + g), split.
+      uint32_t bh[NT][2], bl[NT][2];
+      const float* r0p = buf + (8 * ks + tq) * WS + g;
+      const float* r1p = r0p + 4 * WS;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const float x0 = r0p[8 * j], x1 = r1p[8 * j];
+        bh[j][0] = to_tf32(x0);
+        bh[j][1] = to_tf32(x1);
+        bl[j][0] = to_tf32(x0 - __uint_as_float(bh[j][0]));
+        bl[j][1] = to_tf32(x1 - __uint_as_float(bh[j][1]));
+      }
+#pragma unroll
+      for (int i = 0; i < MT; ++i) {
+        // A = W^T: rows 16i + g (+8) are n-tiles 2i and 2i+1 of the same loads.
+        const int j0 = 2 * i, j1 = 2 * i + 1;
+        uint32_t ah[4], al[4];
+        ah[0] = bh[j0][0];
+        ah[2] = bh[j0][1];
+        al[0] = bl[j0][0];
+        al[2] = bl[j0][1];
+        if (j1 < NT) {
+          ah[1] = bh[j1][0];
+          ah[3] = bh[j1][1];
+          al[1] = bl[j1][0];
+          al[3] = bl[j1][1];
+        } else {
+          ah[1] = ah[3] = al[1] = al[3] = 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          if (!C::tile(i, j)) continue;
+          mma_tf32(acc[i][j], ah, bh[j][0], bh[j][1]);
+          mma_tf32(acc[i][j], ah, bl[j][0], bl[j][1]);
+          mma_tf32(acc[i][j], al, bh[j][0], bh[j][1]);
+        }
+      }
+    }
+    __syncwarp();  // every lane has read this buffer
+    if (chunk + 2 < nchunks) stage(chunk + 2);
+  }
+
+  // Gamma_pq (p <= q) from the accumulators: lane (g, tq) holds rows 16i + g (+8) and
+  // columns 8j + 2tq, +1 of G', i.e. complex column q = 4j + tq; rows 2p and 2p+1 of
+  // complex row p sit in lanes g and g + 1.  Each (p, q) with p <= q lies in exactly one
+  // computed tile, so Gamma is written once per entry (and mirrored).
+  float2* Gf = reinterpret_cast<float2*>(Ws);   // MP x MP complex, reuses the buffers
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      if (!C::tile(i, j)) continue;
+      float o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) o[e] = __shfl_xor_sync(TASER_FULL_MASK, acc[i][j][e], 4);
+      if ((g & 1) == 0) {
+        const int q = 4 * j + tq;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int p = 8 * i + 4 * h + (g >> 1);
+          if (p <= q && q < MP) {
+            const float re = acc[i][j][2 * h] + o[2 * h + 1];
+            const float im = p == q ? 0.f : acc[i][j][2 * h + 1] - o[2 * h];
+            Gf[p * MP + q] = make_float2(re, im);
+            Gf[q * MP + p] = make_float2(re, -im);
           }
         }
       }
-      // Transpose-reduce over lane bits 4..0 (bit 4 first, keeping the upper half when
-      // the bit is set): the lane ends with values [off, off + NVAL/32), off = (NVAL/32) * lane.
-#pragma unroll
-      for (int step = 0; step < 5; ++step) {
-        const int m = 16 >> step;
-        const int h = C::NVAL >> (step + 1);
-        const bool up = (lane & m) != 0;
-#pragma unroll
-        for (int i = 0; i < h; ++i) {
-          const float send = up ? acc[i] : acc[i + h];
-          const float keep = up ? acc[i + h] : acc[i];
-          acc[i] = keep + __shfl_xor_sync(TASER_FULL_MASK, send, m);
-        }
-      }
-      constexpr int PER = C::NVAL / 32;
-#pragma unroll
-      for (int q = 0; q < PER; ++q) Gs[pass * C::NVAL + PER * lane + q] += acc[q];
     }
-  }
   __syncwarp();
 
   // D_a = sqrt|T_aa| (1 where T_aa == 0) and the flags.
+  float* Tdg = Ws + 2 * MP * MP;   // T_aa
+  float* rDsm = Tdg + 72;          // 1 / D_a
   uint32_t fl = 0;
-  float* Dsm = Xs;  // reuse the staging buffer: D then 1/D
-  float* rDsm = Xs + 128;
   for (int a = lane; a < N; a += 32) {
-    const float taa = t_entry<MP>(Gs, kind, P, a, a);
+    int ca, pa;
+    t_index(kind, a, P, MP, ca, pa);
+    float dcr, dci;
+    t_coef(kind, pa, pa, dcr, dci);
+    const float taa = dcr * Gf[ca * MP + ca].x;
     if (!isfinite(taa)) fl |= TASER_FLAG_NONFINITE;
     float da = sqrtf(fabsf(taa));
     if (taa == 0.f) {
       da = 1.f;
       fl |= TASER_FLAG_ZERO_DIAG;
     }
-    Dsm[a] = da;
+    Tdg[a] = taa;
     rDsm[a] = 1.f / da;
     Dout[inst * N + a] = da;
   }
@@ -201,18 +264,41 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
   if (lane == 0 && flags != nullptr) flags[inst] = fl;
   __syncwarp();
+
+  // T~_ab = T_ab / (D_a D_b); the diagonal is exactly sign(T_aa).  Per lane the
+  // coefficients of its columns b are precomputed for the three parts of row a.
+  const int nslot = (N + 31) >> 5;
+  int cb[3];
+  float rdb[3], cr[3][3], ci[3][3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int b = lane + 32 * k;
+    int pb;
+    t_index(kind, b < N ? b : 0, P, MP, cb[k], pb);
+    rdb[k] = b < N ? rDsm[b] : 0.f;
+#pragma unroll
+    for (int pa = 0; pa < 3; ++pa) t_coef(kind, pa, pb, cr[k][pa], ci[k][pa]);
+  }
   float* To = Tt + inst * (int64_t)N * N;
   for (int a = 0; a < N; ++a) {
+    int ca, pa;
+    t_index(kind, a, P, MP, ca, pa);
     const float ra = rDsm[a];
-    for (int b = lane; b < N; b += 32) {
-      const float tab = t_entry<MP>(Gs, kind, P, a, b);
-      float v;
-      if (a == b) {
-        v = tab > 0.f ? 1.f : (tab < 0.f ? -1.f : 0.f);
-      } else {
-        v = tab * ra * rDsm[b];
+    const float taa = Tdg[a];
+    const float sgn = taa > 0.f ? 1.f : (taa < 0.f ? -1.f : 0.f);
+    const float2* grow = Gf + ca * MP;
+    float* trow = To + (int64_t)a * N;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      if (k >= nslot) break;
+      const int b = lane + 32 * k;
+      if (b < N) {
+        const float c0 = pa == 0 ? cr[k][0] : (pa == 1 ? cr[k][1] : cr[k][2]);
+        const float c1 = pa == 0 ? ci[k][0] : (pa == 1 ? ci[k][1] : ci[k][2]);
+        const float2 gv = grow[cb[k]];
+        const float tab = fmaf(c0, gv.x, c1 * gv.y);
+        trow[b] = (a == b) ? sgn : tab * ra * rdb[k];
       }
-      To[(int64_t)a * N + b] = v;
     }
   }
 }
@@ -221,9 +307,12 @@ template <int MP>
 static cudaError_t launch_build(int kind, int64_t batch, int B, int P, int N, const float2* X, const float2* y,
                                 float* Tt, float* D, uint32_t* flags, cudaStream_t st) {
   using C = BuildCfg<MP>;
-  cudaError_t e = cudaFuncSetAttribute(build_T_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       C::SMEM_BYTES);
-  if (e != cudaSuccess) return e;
+  static_assert(2 * MP * MP + 144 <= C::WARP_FLOATS, "epilogue scratch must fit the staging buffers");
+  if (C::SMEM_BYTES > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(build_T_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         C::SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+  }
   const int64_t blocks = (batch + C::WARPS - 1) / C::WARPS;
   build_T_kernel<MP><<<(unsigned)blocks, 32 * C::WARPS, C::SMEM_BYTES, st>>>(kind, batch, B, P, N, X, y, Tt, D,
                                                                            flags);

@@ -62,194 +62,76 @@ struct TcCfg {
   __host__ __device__ static constexpr int kmax(int M) { return M == MT - 1 ? KT - 1 : M; }
 };
 
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// Stage T~ (N x N), D (N) and tau of one instance into the warp's shared slot.
+__device__ __forceinline__ void stage_instance(float* slot, const float* Tt, const float* Dg, const float* tau_g,
+                                               int64_t inst, int N, int lane) {
+  const int nn = N * N;
+  const float* T = Tt + inst * (int64_t)nn;
+  for (int i = lane; i < nn; i += 32) cp_async4(slot + i, T + i);
+  for (int i = lane; i < N; i += 32) cp_async4(slot + nn + i, Dg + inst * (int64_t)N + i);
+  if (lane == 0) cp_async4(slot + nn + N, tau_g + inst);
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// Persistent: each warp walks instances inst, inst + stride, ... and prefetches the next
+// instance's inputs with cp.async while it iterates on the current one.
 template <int NB, bool FP16>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
                  const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
-                 int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags) {
+                 int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags, int slot_floats) {
   using C = TcCfg<NB>;
   constexpr int KT = C::KT, NT = C::NT, MT = C::MT;
+  extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
-  const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
-  if (inst >= batch) return;  // whole warp leaves together
+  float* slot = smem + warp * slot_floats;
+  const int64_t stride = (int64_t)gridDim.x * C::WARPS;
+  int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
+  if (inst < batch) stage_instance(slot, Tt, Dg, tau_g, inst, N, lane);
 
-  const float* T = Tt + inst * (int64_t)N * N;
-  const float m2tau = -2.f * tau_g[inst];
-  auto tval = [&](int k, int n) -> float {  // -2 tau T~ at bucket indices (k, n < NB)
-    return (k < N - 1 && n < N - 1) ? m2tau * T[(int64_t)k * N + n] : 0.f;
-  };
-
-  // B operand: B[k][n] = -2 tau T~[k][n]; lane holds rows 2tq..2tq+1 and +8, column g.
-  uint32_t bf[KT][NT][2];
+  for (; inst < batch; inst += stride) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    const float* T = slot;
+    const float* Di = slot + N * N;
+    const float m2tau = -2.f * slot[N * N + N];
+    auto tval = [&](int k, int n) -> float {  // -2 tau T~ at bucket indices (k, n < NB)
+      return (k < N - 1 && n < N - 1) ? m2tau * T[k * N + n] : 0.f;
+    };
+    // B operand: B[k][n] = -2 tau T~[k][n]; lane holds rows 2tq..2tq+1 and +8, column g.
+    uint32_t bf[KT][NT][2];
 #pragma unroll
-  for (int kt = 0; kt < KT; ++kt)
+    for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
-      bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
-      bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
-    }
-  // Row N of T^ at this lane's accumulator columns c = 8n + 2tq + p (FP32).
-  float tN[NT][2];
-#pragma unroll
-  for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-      const int c = 8 * nt + 2 * tq + p;
-      tN[nt][p] = c < N - 1 ? m2tau * T[(int64_t)(N - 1) * N + c] : 0.f;
-    }
-  const float tnNN = m2tau * T[(int64_t)(N - 1) * N + (N - 1)];
-  const float* Di = Dg + inst * (int64_t)N;
-  const float DN = Di[N - 1];
-  // After the column-sum reduction this lane owns column cown.
-  const int own_idx = NT == 4 ? g : (g >> 1);
-  const int cown = 8 * (own_idx >> 1) + 2 * tq + (own_idx & 1);
-  const float Down = cown < N - 1 ? Di[cown] : 0.f;
-
-  // L~(0) = D in accumulator layout: element (M, n, h, p) is row 16M + g + 8h, column
-  // 8n + 2tq + p.
-  float acc[MT][NT][4];
-#pragma unroll
-  for (int M = 0; M < MT; ++M)
-#pragma unroll
-    for (int n = 0; n < NT; ++n)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
-        acc[M][n][e] = (M < MT - 1 && r == c && r < N - 1) ? Di[r] : 0.f;
+      for (int nt = 0; nt < NT; ++nt) {
+        const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
+        bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
+        bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
       }
-  float LNN = DN;
-  uint32_t fl = 0;
-
-  for (int t = 0; t < t_max; ++t) {
-    // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
-    float part = 0.f;
+    // Row N of T^ at this lane's accumulator columns c = 8n + 2tq + p (FP32).
+    float tN[NT][2];
 #pragma unroll
-    for (int n = 0; n < NT; ++n) part = fmaf(acc[MT - 1][n][0], tN[n][0], fmaf(acc[MT - 1][n][1], tN[n][1], part));
-    part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
-    part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
-    part = __shfl_sync(TASER_FULL_MASK, part, 0);
-
-#pragma unroll
-    for (int M = 0; M < MT; ++M) {
-      // A operand of row block M from the FP32 master (old L~).
-      uint32_t a[KT][4];
-#pragma unroll
-      for (int kt = 0; kt <= C::kmax(M); ++kt) {
-        a[kt][0] = pack2<FP16>(acc[M][2 * kt][0], acc[M][2 * kt][1]);
-        a[kt][1] = pack2<FP16>(acc[M][2 * kt][2], acc[M][2 * kt][3]);
-        a[kt][2] = pack2<FP16>(acc[M][2 * kt + 1][0], acc[M][2 * kt + 1][1]);
-        a[kt][3] = pack2<FP16>(acc[M][2 * kt + 1][2], acc[M][2 * kt + 1][3]);
-      }
-      if (M == MT - 1) {
-        // k = N term of row N in FP32: L~_NN T^_{N,c}.
-#pragma unroll
-        for (int n = 0; n < NT; ++n) {
-          acc[M][n][0] = fmaf(LNN, g == 0 ? tN[n][0] : 0.f, acc[M][n][0]);
-          acc[M][n][1] = fmaf(LNN, g == 0 ? tN[n][1] : 0.f, acc[M][n][1]);
-        }
-      }
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        if (!C::has_tile(M, n)) continue;
-#pragma unroll
-        for (int kt = 0; kt <= C::kmax(M); ++kt) mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
-      }
-    }
-    // Keep V lower-triangular inside the diagonal tiles.
-#pragma unroll
-    for (int M = 0; M < MT - 1; ++M)
-#pragma unroll
-      for (int n = 2 * M; n <= 2 * M + 1; ++n)
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
-          if (c > r) acc[M][n][e] = 0.f;
-        }
-
-    const float vnn = fmaf(LNN, tnNN, LNN) + part;
-    if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
-    if (literal) LNN = vnn >= 0.f ? DN : -DN;
-
-    // prox: column sums of squares, reduced over the 8 lanes sharing tq.
-    float s[C::NV];
-#pragma unroll
-    for (int n = 0; n < NT; ++n)
+    for (int nt = 0; nt < NT; ++nt)
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        float v = 0.f;
-#pragma unroll
-        for (int M = 0; M < MT; ++M) {
-          if (!C::has_tile(M, n)) continue;
-          v = fmaf(acc[M][n][p], acc[M][n][p], v);
-          v = fmaf(acc[M][n][2 + p], acc[M][n][2 + p], v);
-        }
-        s[2 * n + p] = v;
+        const int c = 8 * nt + 2 * tq + p;
+        tN[nt][p] = c < N - 1 ? m2tau * T[(N - 1) * N + c] : 0.f;
       }
-    // Transpose-reduce over lane bits 4, 3, 2: each step halves the values a lane keeps.
-    {
-      int len = C::NV;
-#pragma unroll
-      for (int m = 16; m >= 4; m >>= 1) {
-        const bool up = (lane & m) != 0;
-        if (len > 1) {
-          const int h = len >> 1;
-#pragma unroll
-          for (int i = 0; i < C::NV / 2; ++i) {
-            if (i >= h) break;
-            const float send = up ? s[i] : s[i + h];
-            const float keep = up ? s[i + h] : s[i];
-            s[i] = keep + __shfl_xor_sync(TASER_FULL_MASK, send, m);
-          }
-          len = h;
-        } else {
-          s[0] += __shfl_xor_sync(TASER_FULL_MASK, s[0], m);
-        }
-      }
-    }
-    float sc_own = 0.f;
-    if (s[0] > 0.f) {
-      sc_own = Down * rsqrtf(s[0]);
-    } else if (cown < N - 1) {
-      fl |= TASER_FLAG_ZERO_COLUMN;
-    }
-#pragma unroll
-    for (int n = 0; n < NT; ++n)
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const int idx = 2 * n + p;
-        const int src = 4 * (NT == 4 ? idx : 2 * idx) + tq;
-        const float sc = __shfl_sync(TASER_FULL_MASK, sc_own, src);
-#pragma unroll
-        for (int M = 0; M < MT; ++M) {
-          if (!C::has_tile(M, n)) continue;
-          acc[M][n][p] *= sc;
-          acc[M][n][2 + p] *= sc;
-        }
-      }
-  }
-
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
-  if (lane == 0 && flags != nullptr && fl) flags[inst] |= fl;
-
-  // Decisions from row N (lanes g == 0).
-  if (g == 0) {
-#pragma unroll
-    for (int n = 0; n < NT; ++n)
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const int c = 8 * n + 2 * tq + p;
-        if (c < N - 1) {
-          float r = acc[MT - 1][n][p];
-          if (literal && LNN < 0.f) r = -r;
-          s_hat[inst * (N - 1) + c] = r >= 0.f ? int8_t(1) : int8_t(-1);
-        }
-      }
-  }
-  if (Lout != nullptr) {
-    float* Lo = Lout + inst * (int64_t)N * N;
+    const float tnNN = m2tau * T[(N - 1) * N + (N - 1)];
+    const float DN = Di[N - 1];
+    // After the column-sum reduction this lane owns column cown.
+    const int own_idx = NT == 4 ? g : (g >> 1);
+    const int cown = 8 * (own_idx >> 1) + 2 * tq + (own_idx & 1);
+    const float Down = cown < N - 1 ? Di[cown] : 0.f;
+    // L~(0) = D in accumulator layout: element (M, n, e) is row 16M + g + 8(e >> 1),
+    // column 8n + 2tq + (e & 1).
+    float acc[MT][NT][4];
 #pragma unroll
     for (int M = 0; M < MT; ++M)
 #pragma unroll
@@ -257,20 +139,184 @@ detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
-          const int rr = bucket_to_real(r, N, NB);
-          if (rr < 0 || c >= N - 1) continue;
-          Lo[(int64_t)rr * N + c] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
+          acc[M][n][e] = (M < MT - 1 && r == c && r < N - 1) ? Di[r] : 0.f;
         }
-    for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+    __syncwarp();  // every lane has read the slot
+    {
+      const int64_t next = inst + stride;
+      if (next < batch) stage_instance(slot, Tt, Dg, tau_g, next, N, lane);
+    }
+    float LNN = DN;
+    uint32_t fl = 0;
+
+    for (int t = 0; t < t_max; ++t) {
+      // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
+      float part = 0.f;
+#pragma unroll
+      for (int n = 0; n < NT; ++n) part = fmaf(acc[MT - 1][n][0], tN[n][0], fmaf(acc[MT - 1][n][1], tN[n][1], part));
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
+      part = __shfl_sync(TASER_FULL_MASK, part, 0);
+
+#pragma unroll
+      for (int M = 0; M < MT; ++M) {
+        // A operand of row block M from the FP32 master (old L~).  The last row block
+        // holds row N only (its rows g + 8 are identically zero).
+        uint32_t a[KT][4];
+#pragma unroll
+        for (int kt = 0; kt <= C::kmax(M); ++kt) {
+          a[kt][0] = pack2<FP16>(acc[M][2 * kt][0], acc[M][2 * kt][1]);
+          a[kt][2] = pack2<FP16>(acc[M][2 * kt + 1][0], acc[M][2 * kt + 1][1]);
+          if (M < MT - 1) {
+            a[kt][1] = pack2<FP16>(acc[M][2 * kt][2], acc[M][2 * kt][3]);
+            a[kt][3] = pack2<FP16>(acc[M][2 * kt + 1][2], acc[M][2 * kt + 1][3]);
+          } else {
+            a[kt][1] = 0u;
+            a[kt][3] = 0u;
+          }
+        }
+        if (M == MT - 1) {
+          // k = N term of row N in FP32: L~_NN T^_{N,c}.
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            acc[M][n][0] = fmaf(LNN, g == 0 ? tN[n][0] : 0.f, acc[M][n][0]);
+            acc[M][n][1] = fmaf(LNN, g == 0 ? tN[n][1] : 0.f, acc[M][n][1]);
+          }
+        }
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          if (!C::has_tile(M, n)) continue;
+#pragma unroll
+          for (int kt = 0; kt <= C::kmax(M); ++kt) mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+        }
+      }
+      // Keep V lower-triangular inside the diagonal tiles.
+#pragma unroll
+      for (int M = 0; M < MT - 1; ++M)
+#pragma unroll
+        for (int n = 2 * M; n <= 2 * M + 1; ++n)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+            if (c > r) acc[M][n][e] = 0.f;
+          }
+
+      const float vnn = fmaf(LNN, tnNN, LNN) + part;
+      if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
+      if (literal) LNN = vnn >= 0.f ? DN : -DN;
+
+      // prox: column sums of squares, reduced over the 8 lanes sharing tq.
+      float s[C::NV];
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          float v = 0.f;
+#pragma unroll
+          for (int M = 0; M < MT; ++M) {
+            if (!C::has_tile(M, n)) continue;
+            v = fmaf(acc[M][n][p], acc[M][n][p], v);
+            if (M < MT - 1) v = fmaf(acc[M][n][2 + p], acc[M][n][2 + p], v);
+          }
+          s[2 * n + p] = v;
+        }
+      // Transpose-reduce over lane bits 4, 3, 2: each step halves the values a lane keeps.
+      {
+        int len = C::NV;
+#pragma unroll
+        for (int m = 16; m >= 4; m >>= 1) {
+          const bool up = (lane & m) != 0;
+          if (len > 1) {
+            const int h = len >> 1;
+#pragma unroll
+            for (int i = 0; i < C::NV / 2; ++i) {
+              if (i >= h) break;
+              const float send = up ? s[i] : s[i + h];
+              const float keep = up ? s[i + h] : s[i];
+              s[i] = keep + __shfl_xor_sync(TASER_FULL_MASK, send, m);
+            }
+            len = h;
+          } else {
+            s[0] += __shfl_xor_sync(TASER_FULL_MASK, s[0], m);
+          }
+        }
+      }
+      float sc_own = 0.f;
+      if (s[0] > 0.f) {
+        sc_own = Down * rsqrtf(s[0]);
+      } else if (cown < N - 1) {
+        fl |= TASER_FLAG_ZERO_COLUMN;
+      }
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int idx = 2 * n + p;
+          const int src = 4 * (NT == 4 ? idx : 2 * idx) + tq;
+          const float sc = __shfl_sync(TASER_FULL_MASK, sc_own, src);
+#pragma unroll
+          for (int M = 0; M < MT; ++M) {
+            if (!C::has_tile(M, n)) continue;
+            acc[M][n][p] *= sc;
+            if (M < MT - 1) acc[M][n][2 + p] *= sc;
+          }
+        }
+    }
+
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
+    if (lane == 0 && flags != nullptr && fl) flags[inst] |= fl;
+
+    // Decisions from row N (lanes g == 0).
+    if (g == 0) {
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int c = 8 * n + 2 * tq + p;
+          if (c < N - 1) {
+            float r = acc[MT - 1][n][p];
+            if (literal && LNN < 0.f) r = -r;
+            s_hat[inst * (N - 1) + c] = r >= 0.f ? int8_t(1) : int8_t(-1);
+          }
+        }
+    }
+    if (Lout != nullptr) {
+      float* Lo = Lout + inst * (int64_t)N * N;
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (M == MT - 1 && e >= 2) continue;
+            const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+            const int rr = bucket_to_real(r, N, NB);
+            if (rr < 0 || c >= N - 1) continue;
+            Lo[(int64_t)rr * N + c] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
+          }
+      for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+    }
   }
 }
 
 template <int NB, bool FP16>
 static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                              int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
-  const int64_t blocks = (batch + TcCfg<NB>::WARPS - 1) / TcCfg<NB>::WARPS;
-  detect_tc_kernel<NB, FP16><<<(unsigned)blocks, 32 * TcCfg<NB>::WARPS, 0, st>>>(batch, N, Tt, D, tau, t_max,
-                                                                              literal, L, s, flags);
+  using C = TcCfg<NB>;
+  const int slot_floats = ((N * N + N + 1) + 3) & ~3;
+  const size_t smem = (size_t)C::WARPS * slot_floats * sizeof(float);
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, detect_tc_kernel<NB, FP16>, 32 * C::WARPS, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (batch + C::WARPS - 1) / C::WARPS;
+  const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  const int64_t blocks = need < resident ? need : resident;
+  detect_tc_kernel<NB, FP16><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(batch, N, Tt, D, tau, t_max, literal, L,
+                                                                          s, flags, slot_floats);
   return cudaGetLastError();
 }
 

@@ -4,14 +4,17 @@
 // used: on MU-MIMO matrices the two largest eigenvalues are often close and hundreds of
 // steps still leave errors of 1e-3.  Instead each warp reduces one T~ to tridiagonal form
 // with Householder reflections (FP32, backward stable) and then finds the extreme
-// eigenvalues of the tridiagonal matrix by Sturm-count multisection: lanes 0..15 bracket
-// lambda_max(T~), lanes 16..31 bracket lambda_max(-T~), each round splitting the bracket
-// into 17 parts.
+// eigenvalues of the tridiagonal matrix by Sturm-count multisection.  When T~ is known
+// to be semidefinite (MU-MIMO: T = A^T A; JED: T = -A^T A) only that end is searched by
+// all 32 lanes (33 parts per round); otherwise lanes 0..15 bracket lambda_max(T~) and
+// lanes 16..31 lambda_max(-T~) (17 parts per round).
 //
 // Layout: T~ is embedded in an (NV+1) x (NV+1) matrix with zero padding (zero rows and
 // columns add zero eigenvalues, which do not change ||T~||_2 since ||T~||_2 >= 0).  The
 // first reflection eliminates column 0, leaving an NV x NV trailing matrix whose column
 // c (1..NV) lives in the registers of lane (c-1) mod 32.
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace taser {
@@ -23,23 +26,50 @@ struct SpecCfg {
   static constexpr int VB = ((NP + 3) / 4) * 4;    // padded vector length (16B rows)
   static constexpr int WARPS = 4;
   static constexpr int WARP_FLOATS = 2 * VB + 2 * VB;  // x, w, d, e
-  static constexpr int ROUNDS = 7;                 // 17^7 > 4e8: ~fp32 resolution
 };
 
+constexpr int KBLK = 4;  // Householder steps per compiled block
+
+// Calls f(std::integral_constant<int, KB>) for KB = 0, KBLK, 2 KBLK, ... < NV - 1.
+template <int NV, int KB = 0, typename F>
+__device__ __forceinline__ void static_for_blocks(F&& f) {
+  if constexpr (KB < NV - 1) {
+    f(std::integral_constant<int, KB>{});
+    static_for_blocks<NV, KB + KBLK>(f);
+  }
+}
+
+// Sturm count: number of eigenvalues of the tridiagonal (sg*d, e) below sigma.
+template <int NP>
+__device__ __forceinline__ int sturm_count(const float (&d)[NP], const float (&e2)[NP], float sg, float sigma) {
+  const float pivmin = 1e-30f;
+  float q = sg * d[0] - sigma;
+  int cnt = q < 0.f;
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    if (fabsf(q) < pivmin) q = -pivmin;
+    q = (sg * d[j] - sigma) - __fdividef(e2[j - 1], q);
+    cnt += q < 0.f;
+  }
+  return cnt;
+}
+
+// sign_hint: +1 -> T~ is positive semidefinite (||T~|| = lambda_max), -1 -> negative
+// semidefinite (||T~|| = lambda_max(-T~)), 0 -> unknown (both ends are searched).
 template <int NV>
 __global__ void __launch_bounds__(128)
-spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha, float* __restrict__ tau,
-                float* __restrict__ nrm_out) {
+spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha, int sign_hint,
+                float* __restrict__ tau, float* __restrict__ nrm_out) {
   using C = SpecCfg<NV>;
-  constexpr int S = C::S, NP = C::NP;
+  constexpr int S = C::S, NP = C::NP, VB = C::VB;
   __shared__ __align__(16) float sm[C::WARPS * C::WARP_FLOATS];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
   if (inst >= batch) return;
   float* xb = sm + warp * C::WARP_FLOATS;
-  float* wb = xb + C::VB;
-  float* db = wb + C::VB;
-  float* eb = db + C::VB;
+  float* wb = xb + VB;
+  float* db = wb + VB;
+  float* eb = db + VB;
 
   const float* T = Tt + inst * (int64_t)N * N;
   // col[s][r] = A[r][c_s], c_s = lane + 1 + 32 s.
@@ -51,69 +81,94 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
     for (int r = 0; r < NP; ++r) col[s][r] = (r < N && c < N) ? T[(int64_t)r * N + c] : 0.f;
   }
   const float d0 = T[0];
-  for (int i = lane; i < C::VB; i += 32) {
+  for (int i = lane; i < VB; i += 32) {
     xb[i] = 0.f;
     wb[i] = 0.f;
   }
   __syncwarp();
 
+  // Householder steps k = 0 .. NV-2 in blocks of KBLK: each block body is compiled once
+  // with its trailing range starting at KB + 1 (entries j <= k inside the block are zero
+  // in the published vector), which keeps the code inside the instruction cache.  Only
+  // the entry k+1 of the reflector differs from the published column, so it is corrected
+  // through short select chains over the block's rows.
+  if (lane == 0) db[0] = d0;
+  static_for_blocks<NV>([&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    constexpr int KE = (KB + KBLK < NV - 1) ? KB + KBLK : NV - 1;   // k in [KB, KE)
+#pragma unroll 1
+    for (int k = KB; k < KE; ++k) {
+      // Publish column k below the diagonal: xb[j] = A[j][k] = A[k][j] for j > k, else 0;
+      // the owner of column k records d_k = A[k][k].
 #pragma unroll
-  for (int k = 0; k + 2 <= NV; ++k) {
-    // Publish column k on and below the diagonal: xb[j] = A[j][k] = A[k][j], j >= k.
+      for (int s = 0; s < S; ++s) {
+        const int c = lane + 1 + 32 * s;
+        float ck = 0.f;
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const int c = lane + 1 + 32 * s;
-      if (c <= NV) xb[c] = (c >= k) ? col[s][k] : 0.f;
+        for (int r = KB; r < KE; ++r) ck = (r == k) ? col[s][r] : ck;
+        if (c <= NV) xb[c] = (c > k) ? ck : 0.f;
+        if (c == k) db[k] = ck;
+      }
+      __syncwarp();
+      float x[VB];
+#pragma unroll
+      for (int j4 = (KB + 1) & ~3; j4 < VB; j4 += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(xb + j4);
+        x[j4] = q.x; x[j4 + 1] = q.y; x[j4 + 2] = q.z; x[j4 + 3] = q.w;
+      }
+      const float x1 = xb[k + 1];
+      float sig2 = 0.f;
+#pragma unroll
+      for (int j = KB + 1; j < NP; ++j) sig2 = fmaf(x[j], x[j], sig2);
+      const float sig = sqrtf(sig2);
+      const float ah = x1 >= 0.f ? -sig : sig;             // new subdiagonal entry
+      const float vv2 = 2.f * (sig2 + sig * fabsf(x1));    // ||v||^2, v = x - ah e_{k+1}
+      const float beta = vv2 > 0.f ? 2.f / vv2 : 0.f;
+      // p_i = beta (sum_j A[j][i] x_j - ah A[k+1][i]) for this lane's columns i > k.
+      float p[S], vi[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int c = lane + 1 + 32 * s;
+        float acc = 0.f, ck1 = 0.f;
+#pragma unroll
+        for (int j = KB + 1; j < NP; ++j) acc = fmaf(col[s][j], x[j], acc);
+#pragma unroll
+        for (int r = KB + 1; r <= KE && r < NP; ++r) ck1 = (r == k + 1) ? col[s][r] : ck1;
+        const bool live = c > k && c <= NV;
+        p[s] = live ? beta * fmaf(-ah, ck1, acc) : 0.f;
+        const float vc = (c == k + 1) ? x1 - ah : xb[c <= NV ? c : 0];
+        vi[s] = live ? vc : 0.f;
+      }
+      float kk = 0.f;
+#pragma unroll
+      for (int s = 0; s < S; ++s) kk = fmaf(vi[s], p[s], kk);
+      kk = 0.5f * beta * warp_sum(kk);
+      float w[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int c = lane + 1 + 32 * s;
+        w[s] = fmaf(-kk, vi[s], p[s]);
+        if (c <= NV) wb[c] = w[s];
+      }
+      if (lane == 0) eb[k] = ah;
+      __syncwarp();
+      float wv[VB];
+#pragma unroll
+      for (int j4 = (KB + 1) & ~3; j4 < VB; j4 += 4) {
+        const float4 q = *reinterpret_cast<const float4*>(wb + j4);
+        wv[j4] = q.x; wv[j4 + 1] = q.y; wv[j4 + 2] = q.z; wv[j4 + 3] = q.w;
+      }
+      // A <- A - v w^T - w v^T on the trailing block; v = x except v_{k+1} = x_{k+1} - ah.
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int j = KB + 1; j < NP; ++j) col[s][j] = fmaf(-x[j], w[s], fmaf(-wv[j], vi[s], col[s][j]));
+#pragma unroll
+        for (int r = KB + 1; r <= KE && r < NP; ++r) col[s][r] = fmaf((r == k + 1) ? ah : 0.f, w[s], col[s][r]);
+      }
+      __syncwarp();
     }
-    if (lane == 0) xb[0] = (k == 0) ? d0 : 0.f;
-    __syncwarp();
-    const float dk = xb[k];
-    const float x1 = xb[k + 1];
-    float sig2 = 0.f;
-#pragma unroll
-    for (int j = k + 1; j < NP; ++j) sig2 = fmaf(xb[j], xb[j], sig2);
-    const float sig = sqrtf(sig2);
-    const float ah = x1 >= 0.f ? -sig : sig;             // new subdiagonal entry
-    const float vv2 = 2.f * (sig2 + sig * fabsf(x1));    // ||v||^2, v = x - ah e_{k+1}
-    const float beta = vv2 > 0.f ? 2.f / vv2 : 0.f;
-    const float v1 = x1 - ah;
-    // p_i = beta sum_j A[j][i] v_j for this lane's columns i > k.
-    float p[S], vi[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const int c = lane + 1 + 32 * s;
-      float acc = col[s][k + 1] * v1;
-#pragma unroll
-      for (int j = k + 2; j < NP; ++j) acc = fmaf(col[s][j], xb[j], acc);
-      const bool live = c > k && c <= NV;
-      p[s] = live ? beta * acc : 0.f;
-      vi[s] = live ? (c == k + 1 ? v1 : xb[c]) : 0.f;
-    }
-    float kk = 0.f;
-#pragma unroll
-    for (int s = 0; s < S; ++s) kk = fmaf(vi[s], p[s], kk);
-    kk = 0.5f * beta * warp_sum(kk);
-    float w[S];
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const int c = lane + 1 + 32 * s;
-      w[s] = fmaf(-kk, vi[s], p[s]);
-      if (c <= NV) wb[c] = w[s];
-    }
-    if (lane == 0) {
-      db[k] = dk;
-      eb[k] = ah;
-    }
-    __syncwarp();
-    // A <- A - v w^T - w v^T on the trailing block (rows j > k of this lane's columns).
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      col[s][k + 1] = fmaf(-v1, w[s], fmaf(-wb[k + 1], vi[s], col[s][k + 1]));
-#pragma unroll
-      for (int j = k + 2; j < NP; ++j) col[s][j] = fmaf(-xb[j], w[s], fmaf(-wb[j], vi[s], col[s][j]));
-    }
-    __syncwarp();
-  }
+  });
   // Trailing 2 x 2 block: d_{NV-1}, e_{NV-1}, d_NV.
 #pragma unroll
   for (int s = 0; s < S; ++s) {
@@ -125,36 +180,38 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
     if (c == NV) db[NV] = col[s][NV];
   }
   __syncwarp();
+  float d[NP], e2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    d[j] = db[j];
+    e2[j] = j < NV ? eb[j] * eb[j] : 0.f;
+  }
 
-  // Sturm multisection on the tridiagonal (d, e): half 0 -> lambda_max(A), half 1 ->
-  // lambda_max(-A).
-  const float sg = lane < 16 ? 1.f : -1.f;
-  const int l = lane & 15;
+  // Sturm multisection.  Two-sided (hint 0): lanes 0..15 bracket lambda_max(A), lanes
+  // 16..31 lambda_max(-A), 17 parts per round.  One-sided: all lanes, 33 parts.
+  const bool two = sign_hint == 0;
+  const float sg = two ? (lane < 16 ? 1.f : -1.f) : (sign_hint > 0 ? 1.f : -1.f);
+  const int l = two ? (lane & 15) : lane;
+  const int parts = two ? 17 : 33;
+  const int rounds = two ? 7 : 5;   // 17^7 > 4e8, 33^5 > 3.9e7
   float lo = -3.0e38f, hi = -3.0e38f;
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    const float dj = sg * db[j];
-    const float r = (j > 0 ? fabsf(eb[j - 1]) : 0.f) + (j < NV ? fabsf(eb[j]) : 0.f);
+    const float dj = sg * d[j];
+    const float r = (j > 0 ? sqrtf(e2[j - 1]) : 0.f) + sqrtf(e2[j]);
     lo = fmaxf(lo, dj);
     hi = fmaxf(hi, dj + r);
   }
-  const float pivmin = 1e-30f;
+  const float inv_parts = 1.f / (float)parts;
 #pragma unroll 1
-  for (int round = 0; round < C::ROUNDS; ++round) {
-    const float step = (hi - lo) * (1.f / 17.f);
+  for (int round = 0; round < rounds; ++round) {
+    const float step = (hi - lo) * inv_parts;
     const float sigma = fmaf(step, (float)(l + 1), lo);
-    float q = sg * db[0] - sigma;
-    int cnt = q < 0.f;
-#pragma unroll
-    for (int j = 1; j < NP; ++j) {
-      if (fabsf(q) < pivmin) q = -pivmin;
-      q = (sg * db[j] - sigma) - __fdividef(eb[j - 1] * eb[j - 1], q);
-      cnt += q < 0.f;
-    }
+    const int cnt = sturm_count<NP>(d, e2, sg, sigma);
     const unsigned ball = __ballot_sync(TASER_FULL_MASK, cnt == NP);
-    const unsigned half = lane < 16 ? (ball & 0xffffu) : (ball >> 16);
+    const unsigned half = two ? (lane < 16 ? (ball & 0xffffu) : (ball >> 16)) : ball;
     if (half == 0u) {
-      lo = fmaf(step, 16.f, lo);
+      lo = fmaf(step, (float)(parts - 1), lo);
     } else {
       const int f = __ffs(half) - 1;
       const float nhi = fmaf(step, (float)(f + 1), lo);
@@ -163,29 +220,238 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
       hi = nhi;
     }
   }
-  const float lam = 0.5f * (lo + hi);
-  const float nrm = fmaxf(lam, __shfl_xor_sync(TASER_FULL_MASK, lam, 16));
+  float nrm = 0.5f * (lo + hi);
+  if (two) nrm = fmaxf(nrm, __shfl_xor_sync(TASER_FULL_MASK, nrm, 16));
   if (lane == 0) {
     tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
     if (nrm_out != nullptr) nrm_out[inst] = nrm;
   }
 }
 
-template <int NV>
-static cudaError_t launch_spectral(int64_t batch, int N, const float* Tt, float alpha, float* tau, float* nrm,
-                                   cudaStream_t st) {
-  const int64_t blocks = (batch + SpecCfg<NV>::WARPS - 1) / SpecCfg<NV>::WARPS;
-  spectral_kernel<NV><<<(unsigned)blocks, 32 * SpecCfg<NV>::WARPS, 0, st>>>(batch, N, Tt, alpha, tau, nrm);
+// ---------------------------------------------------------------------------------
+// QPSK: ||T~||_2 from the complex Hermitian form.
+//
+// For QPSK, T~ (N = 2U + 1) is the real form [[Re M, -Im M], [Im M, Re M]] of the
+// preconditioned complex Gram M~ of [H / sqrt2, -y] ((U+1) x (U+1), Hermitian) with the
+// row and column of the imaginary part of the augmented coordinate deleted.  Every
+// eigenvalue of M~ appears twice in its real form, so by Cauchy interlacing the largest
+// and smallest eigenvalues of T~ are those of M~, and ||T~||_2 = ||M~||_2.  M~ is read
+// from T~:  M~_ab = T~_ab + i T~_{U+a,b},  M~_{a,N} = T~_{a,2U} + i T~_{U+a,2U}.
+// Tridiagonalising the (U+1) complex matrix costs about 2.5x fewer flops and half the
+// sequential steps of the real (2U+1) one, and its UV = 16 trailing columns let two
+// instances share a warp.
+// ---------------------------------------------------------------------------------
+template <int UV>
+struct HermCfg {
+  static constexpr int G = UV;                 // lanes per instance (columns 1..UV)
+  static constexpr int IPW = 32 / UV;          // instances per warp
+  static constexpr int NP = UV + 1;            // padded complex order; aug at index UV
+  static constexpr int VB = (NP + 1) & ~1;     // complex vector length (16B pairs)
+  static constexpr int WARPS = 4;
+  static constexpr int IPC = WARPS * IPW;
+  static constexpr int INST_FLOATS = 4 * VB + 2 * VB;  // xb, wb (complex), db, eb2
+  static constexpr int ROUNDS = UV == 32 ? 5 : (UV == 16 ? 6 : 8);   // (UV+1)^ROUNDS >= 2e7
+};
+
+__device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * b
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+template <int UV>
+__global__ void __launch_bounds__(128)
+spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float alpha, float* __restrict__ tau,
+                     float* __restrict__ nrm_out) {
+  using C = HermCfg<UV>;
+  constexpr int NP = C::NP, VB = C::VB, G = C::G;
+  __shared__ __align__(16) float sm[C::IPC * C::INST_FLOATS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane % G;
+  const int local = warp * C::IPW + grp;
+  const int64_t inst = (int64_t)blockIdx.x * C::IPC + local;
+  const bool active = inst < batch;
+  float2* xb = reinterpret_cast<float2*>(sm + local * C::INST_FLOATS);
+  float2* wb = xb + VB;
+  float* db = reinterpret_cast<float*>(wb + VB);
+  float* eb2 = db + VB;
+  const int N = 2 * U + 1;
+  const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
+  auto t = [&](int a, int b) -> float { return active ? T[(int64_t)a * N + b] : 0.f; };
+
+  // col[j] = M~[j][c], c = gl + 1; index UV is the augmented coordinate.
+  const int c = gl + 1;
+  const bool cu = c < UV && c < U, ca = c == UV;
+  float2 col[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const bool ju = j < UV && j < U, ja = j == UV;
+    float2 v = make_float2(0.f, 0.f);
+    if (ju && cu) v = make_float2(t(j, c), t(U + j, c));
+    else if (ju && ca) v = make_float2(t(j, 2 * U), t(U + j, 2 * U));
+    else if (ja && cu) v = make_float2(t(c, 2 * U), -t(U + c, 2 * U));
+    else if (ja && ca) v = make_float2(t(2 * U, 2 * U), 0.f);
+    col[j] = v;
+  }
+  for (int i = gl; i < VB; i += G) {
+    xb[i] = make_float2(0.f, 0.f);
+    wb[i] = make_float2(0.f, 0.f);
+  }
+  if (gl == 0) db[0] = U >= 1 ? t(0, 0) : 0.f;
+  __syncwarp();
+
+  static_for_blocks<UV>([&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    constexpr int KE = (KB + KBLK < UV - 1) ? KB + KBLK : UV - 1;   // k in [KB, KE)
+#pragma unroll 1
+    for (int k = KB; k < KE; ++k) {
+      // Publish x = column k below the diagonal: x_j = M[j][k] = conj(M[k][j]), j > k.
+      float2 ck = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = KB; r < KE; ++r) ck = (r == k) ? col[r] : ck;
+      xb[c] = (c > k) ? make_float2(ck.x, -ck.y) : make_float2(0.f, 0.f);
+      if (c == k) db[k] = ck.x;
+      __syncwarp();
+      float2 x[VB];
+#pragma unroll
+      for (int j2 = (KB + 1) & ~1; j2 < VB; j2 += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(xb + j2);
+        x[j2] = make_float2(q.x, q.y);
+        x[j2 + 1] = make_float2(q.z, q.w);
+      }
+      const float2 x1 = xb[k + 1];
+      float sig2 = 0.f;
+#pragma unroll
+      for (int j = KB + 1; j < NP; ++j) sig2 = fmaf(x[j].x, x[j].x, fmaf(x[j].y, x[j].y, sig2));
+      const float sig = sqrtf(sig2);
+      const float ax1 = sqrtf(fmaf(x1.x, x1.x, x1.y * x1.y));
+      const float2 ph = ax1 > 0.f ? make_float2(x1.x / ax1, x1.y / ax1) : make_float2(1.f, 0.f);
+      const float2 al = make_float2(-ph.x * sig, -ph.y * sig);       // alpha = -e^{i theta} sigma
+      const float2 v1 = make_float2(ph.x * (ax1 + sig), ph.y * (ax1 + sig));
+      const float vv2 = 2.f * sig * (sig + ax1);
+      const float beta = vv2 > 0.f ? 2.f / vv2 : 0.f;
+      // p_c = beta (sum_j conj(M[j][c]) v_j), v = x except v_{k+1} = x_{k+1} - alpha.
+      float2 acc = make_float2(0.f, 0.f), ck1 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int j = KB + 1; j < NP; ++j) {
+        const float2 m = cmul_conj(col[j], x[j]);
+        acc.x += m.x;
+        acc.y += m.y;
+      }
+#pragma unroll
+      for (int r = KB + 1; r <= KE && r < NP; ++r) ck1 = (r == k + 1) ? col[r] : ck1;
+      const float2 corr = cmul_conj(ck1, make_float2(-al.x, -al.y));
+      const bool live = c > k;
+      const float2 p = live ? make_float2(beta * (acc.x + corr.x), beta * (acc.y + corr.y)) : make_float2(0.f, 0.f);
+      const float2 vc = !live ? make_float2(0.f, 0.f) : (c == k + 1 ? v1 : xb[c]);
+      float kk = fmaf(vc.x, p.x, vc.y * p.y);                       // Re(conj(v_c) p_c)
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) kk += __shfl_xor_sync(TASER_FULL_MASK, kk, o);
+      kk *= 0.5f * beta;
+      const float2 w = make_float2(fmaf(-kk, vc.x, p.x), fmaf(-kk, vc.y, p.y));
+      wb[c] = w;
+      if (c == k + 1) eb2[k] = sig2;                               // |alpha|^2
+      __syncwarp();
+      float2 wv[VB];
+#pragma unroll
+      for (int j2 = (KB + 1) & ~1; j2 < VB; j2 += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(wb + j2);
+        wv[j2] = make_float2(q.x, q.y);
+        wv[j2 + 1] = make_float2(q.z, q.w);
+      }
+      // M[j][c] -= v_j conj(w_c) + w_j conj(v_c)
+#pragma unroll
+      for (int j = KB + 1; j < NP; ++j) {
+        col[j].x -= fmaf(x[j].x, w.x, fmaf(x[j].y, w.y, fmaf(wv[j].x, vc.x, wv[j].y * vc.y)));
+        col[j].y -= fmaf(x[j].y, w.x, fmaf(-x[j].x, w.y, fmaf(wv[j].y, vc.x, -wv[j].x * vc.y)));
+      }
+      // v_{k+1} = x_{k+1} - alpha: add alpha conj(w_c) to row k+1
+#pragma unroll
+      for (int r = KB + 1; r <= KE && r < NP; ++r) {
+        if (r == k + 1) {
+          col[r].x += fmaf(al.x, w.x, al.y * w.y);
+          col[r].y += fmaf(al.y, w.x, -al.x * w.y);
+        }
+      }
+      __syncwarp();
+    }
+  });
+  // Trailing 2 x 2 block.
+  if (c == UV - 1) {
+    db[UV - 1] = col[UV - 1].x;
+    eb2[UV - 1] = fmaf(col[UV].x, col[UV].x, col[UV].y * col[UV].y);
+  }
+  if (c == UV) db[UV] = col[UV].x;
+  __syncwarp();
+  float d[NP], e2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    d[j] = db[j];
+    e2[j] = j < UV ? eb2[j] : 0.f;
+  }
+  // One-sided multisection for lambda_max (M~ is positive semidefinite), G + 1 parts.
+  float lo = -3.0e38f, hi = -3.0e38f;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const float r = (j > 0 ? sqrtf(e2[j - 1]) : 0.f) + sqrtf(e2[j]);
+    lo = fmaxf(lo, d[j]);
+    hi = fmaxf(hi, d[j] + r);
+  }
+  const float inv_parts = 1.f / (float)(G + 1);
+  const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
+#pragma unroll 1
+  for (int round = 0; round < C::ROUNDS; ++round) {
+    const float step = (hi - lo) * inv_parts;
+    const float sigma = fmaf(step, (float)(gl + 1), lo);
+    const int cnt = sturm_count<NP>(d, e2, 1.f, sigma);
+    const unsigned ball = __ballot_sync(TASER_FULL_MASK, cnt == NP);
+    const unsigned mine = (ball >> (grp * G)) & gmask;
+    if (mine == 0u) {
+      lo = fmaf(step, (float)G, lo);
+    } else {
+      const int f = __ffs(mine) - 1;
+      const float nhi = fmaf(step, (float)(f + 1), lo);
+      const float nlo = f == 0 ? lo : fmaf(step, (float)f, lo);
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  const float nrm = 0.5f * (lo + hi);
+  if (active && gl == 0) {
+    tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
+    if (nrm_out != nullptr) nrm_out[inst] = nrm;
+  }
+}
+
+template <int UV>
+static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
+                               cudaStream_t st) {
+  const int64_t blocks = (batch + HermCfg<UV>::IPC - 1) / HermCfg<UV>::IPC;
+  spectral_herm_kernel<UV><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
   return cudaGetLastError();
 }
 
-cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, float* tau, float* nrm,
+// ||T~||_2 of QPSK matrices (N = 2U + 1) through the complex form; U <= 32.
+cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
+                          cudaStream_t st) {
+  if (U + 1 <= 9) return launch_herm<8>(batch, U, Tt, alpha, tau, nrm, st);
+  if (U + 1 <= 17) return launch_herm<16>(batch, U, Tt, alpha, tau, nrm, st);
+  return launch_herm<32>(batch, U, Tt, alpha, tau, nrm, st);
+}
+
+template <int NV>
+static cudaError_t launch_spectral(int64_t batch, int N, const float* Tt, float alpha, int hint, float* tau,
+                                   float* nrm, cudaStream_t st) {
+  const int64_t blocks = (batch + SpecCfg<NV>::WARPS - 1) / SpecCfg<NV>::WARPS;
+  spectral_kernel<NV><<<(unsigned)blocks, 32 * SpecCfg<NV>::WARPS, 0, st>>>(batch, N, Tt, alpha, hint, tau, nrm);
+  return cudaGetLastError();
+}
+
+cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, int hint, float* tau, float* nrm,
                      cudaStream_t st) {
   switch (bucket_of(N)) {
-    case 8: return launch_spectral<8>(batch, N, Tt, alpha, tau, nrm, st);
-    case 16: return launch_spectral<16>(batch, N, Tt, alpha, tau, nrm, st);
-    case 32: return launch_spectral<32>(batch, N, Tt, alpha, tau, nrm, st);
-    default: return launch_spectral<64>(batch, N, Tt, alpha, tau, nrm, st);
+    case 8: return launch_spectral<8>(batch, N, Tt, alpha, hint, tau, nrm, st);
+    case 16: return launch_spectral<16>(batch, N, Tt, alpha, hint, tau, nrm, st);
+    case 32: return launch_spectral<32>(batch, N, Tt, alpha, hint, tau, nrm, st);
+    default: return launch_spectral<64>(batch, N, Tt, alpha, hint, tau, nrm, st);
   }
 }
 

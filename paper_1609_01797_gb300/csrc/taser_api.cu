@@ -8,7 +8,10 @@
 namespace taser {
 cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X, const void* y, float* Tt,
                     float* D, uint32_t* flags, cudaStream_t st);
-cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, float* tau, float* nrm, cudaStream_t st);
+cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, int hint, float* tau, float* nrm,
+                     cudaStream_t st);
+cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
+                          cudaStream_t st);
 cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                         int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
 cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
@@ -108,7 +111,12 @@ taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const voi
   cudaError_t e = taser::build_T(kind, batch, B, P, N, H_or_Y, y, T_tilde, D, flags, st);
   if (e == cudaErrorNotSupported) return fail(TASER_ERR_UNSUPPORTED, "no build kernel for %d columns", P + 1);
   if (e != cudaSuccess) return from_cuda(e, "build_T");
-  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, tau, spec_norm, st), "spectral");
+  // QPSK: ||T~||_2 equals the norm of its (U+1) x (U+1) complex Hermitian form.
+  if (kind == TASER_MIMO_QPSK) {
+    return from_cuda(taser::spectral_qpsk(batch, U_or_K, T_tilde, alpha, tau, spec_norm, st), "spectral_qpsk");
+  }
+  // T = A^T A is positive semidefinite (MIMO), T = -A^T A negative semidefinite (JED).
+  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, jed ? -1 : 1, tau, spec_norm, st), "spectral");
 }
 
 taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, float alpha, float* tau, float* spec_norm,
@@ -120,7 +128,7 @@ taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, float a
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(tau, "tau");
   if (spec_norm != nullptr) TASER_REQUIRE(aligned16(spec_norm), "spec_norm must be 16-byte aligned");
-  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, tau, spec_norm, static_cast<cudaStream_t>(stream)),
+  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, 0, tau, spec_norm, static_cast<cudaStream_t>(stream)),
                    "spectral");
 }
 
