@@ -3,8 +3,8 @@
 path vs FP32 path at equal BER, on one or more GPUs (one process per GPU).
 
 A step is one pass of the whole detector over one batch of synthetic instances that
-are already resident in HBM: taser_build_T (T~, D, tau from H, y) followed by
-taser_detect (Algorithm 1 and the decisions).  The batch is 65,536 instances per GPU
+are already resident in HBM: taser_build_T (T~ and D from H, y), taser_step_size
+(tau = alpha / ||T~||_2) and taser_detect (Algorithm 1 and the decisions).  The batch is 65,536 instances per GPU
 with the SNR cycling over 0, 2, ..., 20 dB (the SNR sweep of the workload); its inputs
 (1.14 GB) are larger than the 129 MB L2, so no flush is needed between steps.
 
@@ -39,7 +39,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["taser", "reference"], default="taser")
     ap.add_argument("--instances", type=int, default=65536, help="instances per GPU per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=8192, help="instances timed on the CPU oracle")
+    ap.add_argument("--cpu-sample", type=int, default=32768, help="instances timed on the CPU oracle")
     return ap.parse_args()
 
 
@@ -52,9 +52,39 @@ def flops_per_detection(n, t_max):
 
 
 def build_bytes_per_instance(b, u, n):
-    """Algorithmic HBM bytes of taser_build_T per instance: read H (B x U complex64) and y
-    (B complex64), write T~ (N x N fp32), D (N) and tau; the step-size kernel reads T~."""
-    return 8 * b * u + 8 * b + 4 * n * n + 4 * n + 4 + 4 * n * n
+    """Algorithmic HBM bytes of the build kernel per instance: read H (B x U complex64)
+    and y (B complex64), write T~ (N x N fp32) and D (N fp32)."""
+    return 8 * b * u + 8 * b + 4 * n * n + 4 * n
+
+
+def spectral_flops_per_instance(u):
+    """Complex Hermitian tridiagonalisation of order n = U + 1 (16/3 n^3 real flops) plus
+    the Sturm multisection (6 rounds x 16 points x n steps x 4 flops)."""
+    n = u + 1
+    return 16 * n ** 3 // 3 + 6 * 16 * n * 4
+
+
+KERNEL_SOURCES = {"build": "build_T.cu", "spectral": "spectral.cu", "detect_tc": "detect_tc.cu",
+                  "detect_fp32": "detect_fp32.cu"}
+
+
+def measured_traffic():
+    """DRAM bytes per instance per kernel from the committed ncu summary, kept only while
+    the kernel's source is unchanged since the counters were taken (sha1 match)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    out = {}
+    if not os.path.exists(path):
+        return out
+    for line in open(path):
+        p = line.split()
+        if len(p) != 3 or line.startswith("#"):
+            continue
+        key, per_inst, sha = p[0], float(p[1]), p[2]
+        src = os.path.join(ROOT, "paper_1609_01797_gb300", "csrc", KERNEL_SOURCES.get(key, ""))
+        if os.path.isfile(src) and hashlib.sha1(open(src, "rb").read()).hexdigest() == sha:
+            out[key] = per_inst
+    return out
 
 
 def make_workload(n, seed):
@@ -210,37 +240,48 @@ def main():
     bufs = {"T_tilde": torch.empty((n, N, N), device=dev), "D": torch.empty((n, N), device=dev),
             "tau": torch.empty((n,), device=dev), "flags": torch.zeros((n,), device=dev, dtype=torch.int32)}
     s_hat = torch.empty((n, N - 1), device=dev, dtype=torch.int8)
+    nrm_buf = torch.empty((n,), device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def barrier():
         if world > 1:
             dist.barrier()
 
+    def one_step(precision, ev=None):
+        # taser_build_T (T~, D) -> taser_step_size (tau, QPSK structure) -> taser_detect
+        if ev is not None:
+            ev[0].record(stream)
+        taser.build_T("mimo_qpsk", H, y, ALPHA, out=bufs, with_tau=False)
+        if ev is not None:
+            ev[1].record(stream)
+        taser.step_size(bufs["T_tilde"], ALPHA, structure="mimo_qpsk", tau=bufs["tau"], spec_norm=nrm_buf)
+        if ev is not None:
+            ev[2].record(stream)
+        taser.detect(bufs["T_tilde"], bufs["D"], bufs["tau"], T_MAX, precision, want_L=False,
+                     flags=bufs["flags"], out_s=s_hat)
+        if ev is not None:
+            ev[3].record(stream)
+
     def run_path(precision, steps, warmup):
         for _ in range(warmup):
-            taser.build_T("mimo_qpsk", H, y, ALPHA, out=bufs)
-            taser.detect(bufs["T_tilde"], bufs["D"], bufs["tau"], T_MAX, precision, want_L=False,
-                         flags=bufs["flags"], out_s=s_hat)
-        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+            one_step(precision)
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
         start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize(dev)
         start.record(stream)
         for i in range(steps):
-            ev[i][0].record(stream)
-            taser.build_T("mimo_qpsk", H, y, ALPHA, out=bufs)
-            ev[i][1].record(stream)
-            taser.detect(bufs["T_tilde"], bufs["D"], bufs["tau"], T_MAX, precision, want_L=False,
-                         flags=bufs["flags"], out_s=s_hat)
-            ev[i][2].record(stream)
+            one_step(precision, ev[i])
         end.record(stream)
         torch.cuda.synchronize(dev)
         barrier()
         ms = start.elapsed_time(end) / steps
         build_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / steps
-        detect_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        spectral_ms = sum(e[1].elapsed_time(e[2]) for e in ev) / steps
+        detect_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / steps
         errs = int((s_hat.cpu().numpy() != bits).sum())
-        return {"ms_per_step": ms, "build_ms": build_ms, "detect_ms": detect_ms, "bit_errors": errs}
+        return {"ms_per_step": ms, "build_ms": build_ms, "spectral_ms": spectral_ms, "detect_ms": detect_ms,
+                "bit_errors": errs}
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -273,6 +314,7 @@ def main():
     for p in paths.values():
         p["ms_per_step"] = max_over_ranks(p["ms_per_step"], world)
         p["build_ms"] = max_over_ranks(p["build_ms"], world)
+        p["spectral_ms"] = max_over_ranks(p["spectral_ms"], world)
         p["detect_ms"] = max_over_ranks(p["detect_ms"], world)
         p["bit_errors"] = sum_over_ranks(p["bit_errors"], world)
         p["det_per_s"] = total / (p["ms_per_step"] * 1e-3)
@@ -296,18 +338,34 @@ def main():
     bf16_peak = _peak(peaks, "bf16_tflops", "bf16_dense_tflops") or 1900.0
     hbm_peak = _peak(peaks, "hbm_gbs", "hbm_GBps", "copy_gbs") or 6800.0
     fl = flops_per_detection(N, T_MAX)
+    traffic = measured_traffic()
+
+    def tr(key):
+        return traffic[key] * n if key in traffic else None
+
     det_tc = n / (head["detect_ms"] * 1e-3) / 1e12 * fl                      # TFLOP/s per GPU
     build_gbs = n * build_bytes_per_instance(B, U, N) / (head["build_ms"] * 1e-3) / 1e9
-    roof_detect = {"kernel": "detect_tc_kernel<32,bf16> (mma.sync m16n8k16)", "bound": "tensor",
-                   "achieved": det_tc, "peak": bf16_peak, "unit": "TFLOP/s", "frac": det_tc / bf16_peak,
-                   "traffic": None, "peak_source": peak_src,
-                   "algorithmic_flops_per_launch": fl * n,
-                   "fp32_pipe_frac": det_tc / fp32_peak}
-    roof_build = {"kernel": "build_T_kernel<17> + spectral_kernel<32>", "bound": "hbm", "achieved": build_gbs,
-                  "peak": hbm_peak, "unit": "GB/s", "frac": build_gbs / hbm_peak, "traffic": None,
-                  "peak_source": peak_src,
-                  "algorithmic_bytes_per_launch": n * build_bytes_per_instance(B, U, N)}
-    dominant, other = (roof_detect, roof_build) if head["detect_ms"] >= head["build_ms"] else (roof_build, roof_detect)
+    spec_tf = n * spectral_flops_per_instance(U) / (head["spectral_ms"] * 1e-3) / 1e12
+    roofs = {
+        "detect": (head["detect_ms"], {
+            "kernel": "detect_tc_kernel<32,bf16> (mma.sync m16n8k16)", "bound": "tensor", "achieved": det_tc,
+            "peak": bf16_peak, "unit": "TFLOP/s", "frac": det_tc / bf16_peak, "traffic": tr("detect_tc"),
+            "peak_source": peak_src, "algorithmic_flops_per_launch": fl * n, "ms_per_launch": head["detect_ms"],
+            "fp32_pipe_frac": det_tc / fp32_peak}),
+        "build": (head["build_ms"], {
+            "kernel": "build_T_kernel<17> (3xTF32 mma.sync Gram)", "bound": "hbm", "achieved": build_gbs,
+            "peak": hbm_peak, "unit": "GB/s", "frac": build_gbs / hbm_peak, "traffic": tr("build"),
+            "peak_source": peak_src, "algorithmic_bytes_per_launch": n * build_bytes_per_instance(B, U, N),
+            "ms_per_launch": head["build_ms"]}),
+        "spectral": (head["spectral_ms"], {
+            "kernel": "spectral_herm_kernel<16> (Householder + Sturm)", "bound": "alu", "achieved": spec_tf,
+            "peak": fp32_peak, "unit": "TFLOP/s", "frac": spec_tf / fp32_peak, "traffic": tr("spectral"),
+            "peak_source": "derived FP32 pipe", "algorithmic_flops_per_launch": n * spectral_flops_per_instance(U),
+            "ms_per_launch": head["spectral_ms"]}),
+    }
+    order = sorted(roofs, key=lambda k: -roofs[k][0])
+    dominant = roofs[order[0]][1]
+    others = {k: roofs[k][1] for k in order[1:]}
     fp32 = paths["fp32"]
     det_fp32 = n / (fp32["detect_ms"] * 1e-3) / 1e12 * fl
     out = {
@@ -328,14 +386,16 @@ def main():
                    "l2": "inputs (%.2f GB per GPU) larger than L2; no flush" % (n * (8 * B * U + 8 * B) / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "paths": {k: {"det_per_s": v["det_per_s"], "detect_only_det_per_s": v["detect_only_det_per_s"],
-                      "ms_per_step": v["ms_per_step"], "build_ms": v["build_ms"], "detect_ms": v["detect_ms"],
-                      "ber": v["ber"], "ber_ci95": v["ber_ci95"]} for k, v in paths.items()},
+                      "ms_per_step": v["ms_per_step"], "build_ms": v["build_ms"], "spectral_ms": v["spectral_ms"],
+                      "detect_ms": v["detect_ms"], "ber": v["ber"], "ber_ci95": v["ber_ci95"]}
+                  for k, v in paths.items()},
         "equal_ber": equal_ber,
         "speedup_bf16_vs_fp32": fp32["ms_per_step"] / head["ms_per_step"],
         "roofline": dominant,
-        "roofline_other": other,
+        "roofline_other": others,
         "roofline_fp32_path": {"kernel": "detect_fp32_kernel<32>", "bound": "alu", "achieved": det_fp32,
                                "peak": fp32_peak, "unit": "TFLOP/s", "frac": det_fp32 / fp32_peak,
+                               "traffic": tr("detect_fp32"),
                                "peak_source": "derived: %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
                                               % (props.multi_processor_count, smax)},
         "clocks": clocks,

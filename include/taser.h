@@ -96,7 +96,8 @@ const char* taser_last_error(void);
  *   alpha     step-size factor, 0 < alpha < 1 (the paper leaves its value open).
  *   T_tilde   out, float [batch][N][N], full symmetric matrix.
  *   D         out, float [batch][N], D_kk = sqrt(|T_kk|) (1 where T_kk == 0).
- *   tau       out, float [batch].
+ *   tau       out, float [batch]; NULL skips the step size (then call
+ *             taser_step_size with structure = kind).
  *   spec_norm out, float [batch] = ||T~||_2, or NULL.
  *   flags     out, uint32 [batch] (overwritten with ZERO_DIAG / NONFINITE bits), or NULL.
  *
@@ -112,13 +113,24 @@ taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K,
                            float* T_tilde, float* D, float* tau, float* spec_norm,
                            uint32_t* flags, void* stream);
 
+/* Structure of T~ known to taser_step_size (a problem kind, or this value). */
+#define TASER_GENERIC_SYMMETRIC (-1)
+
 /*
- * taser_step_size -- tau = alpha / ||T~||_2 for caller-provided symmetric T~
- * (Sec. III-B; Algorithm 1 inputs).  T_tilde float [batch][N][N] (full), N in [2, 65];
- * tau out float [batch]; spec_norm out float [batch] or NULL.
+ * taser_step_size -- tau = alpha / ||T~||_2 for symmetric T~ (Sec. III-B; Algorithm 1
+ * inputs), ||T~||_2 = largest |eigenvalue|.
+ *   T_tilde   float [batch][N][N] (full), N in [2, 65].
+ *   structure what is known about T~, which selects a cheaper exact method:
+ *               TASER_MIMO_BPSK      positive semidefinite;
+ *               TASER_SIMO_JED_BPSK  negative semidefinite;
+ *               TASER_MIMO_QPSK      the real form of a complex Hermitian (U+1) x (U+1)
+ *                                    matrix with Im(last) deleted (N = 2U + 1), as built by
+ *                                    taser_build_T; ||T~|| is computed on that matrix;
+ *               TASER_GENERIC_SYMMETRIC  nothing known.
+ *   tau       out float [batch]; spec_norm out float [batch] or NULL.
  */
-taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, float alpha,
-                             float* tau, float* spec_norm, void* stream);
+taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int structure,
+                             float alpha, float* tau, float* spec_norm, void* stream);
 
 /*
  * taser_detect -- Algorithm 1 (TASER) for every instance:

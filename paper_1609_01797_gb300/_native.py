@@ -13,7 +13,7 @@ SIGNATURES = {
     "taser_status_string": (ctypes.c_char_p, [_c_i32]),
     "taser_last_error": (ctypes.c_char_p, []),
     "taser_build_T": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _vp, _vp, _vp, _vp, _vp, _vp]),
-    "taser_step_size": (_c_i32, [_c_i64, _c_i32, _vp, _c_f32, _vp, _vp, _vp]),
+    "taser_step_size": (_c_i32, [_c_i64, _c_i32, _vp, _c_i32, _c_f32, _vp, _vp, _vp]),
     "taser_detect": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _c_i32, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
     "taser_host_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i64, _c_i32, _c_i32]),
     "taser_run_host": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32, _vp,

@@ -35,9 +35,10 @@ def problem_size(kind, U_or_K):
     return lib().taser_problem_size(KINDS[kind], int(U_or_K))
 
 
-def build_T(kind, H_or_Y, y=None, alpha=0.5, out=None, stream=None):
+def build_T(kind, H_or_Y, y=None, alpha=0.5, out=None, stream=None, with_tau=True):
     """T~, D, tau (and ||T~||_2, flags) per instance from complex64 H [n,B,U] and
-    y [n,B] (MIMO) or Y [n,B,K] (JED).  Returns a dict of device tensors."""
+    y [n,B] (MIMO) or Y [n,B,K] (JED).  Returns a dict of device tensors.  With
+    with_tau=False the step size is skipped (see step_size)."""
     k = KINDS[kind]
     X = _dev(H_or_Y, torch.complex64, "H_or_Y")
     n, B, M = X.shape
@@ -54,18 +55,24 @@ def build_T(kind, H_or_Y, y=None, alpha=0.5, out=None, stream=None):
                "spec_norm": torch.empty((n,), device=dev, dtype=torch.float32),
                "flags": torch.zeros((n,), device=dev, dtype=torch.int32)}
     st = lib().taser_build_T(k, n, B, M, _ptr(X), _ptr(y if k != JED_BPSK else None), float(alpha),
-                             _ptr(out["T_tilde"]), _ptr(out["D"]), _ptr(out["tau"]),
+                             _ptr(out["T_tilde"]), _ptr(out["D"]), _ptr(out["tau"] if with_tau else None),
                              _ptr(out.get("spec_norm")), _ptr(out.get("flags")), _stream(stream))
     check(st, "taser_build_T")
     return out
 
 
-def step_size(T_tilde, alpha=0.5, stream=None):
+GENERIC = -1
+
+
+def step_size(T_tilde, alpha=0.5, structure=GENERIC, tau=None, spec_norm=None, stream=None):
+    """tau = alpha / ||T~||_2.  `structure`: a problem kind (what taser_build_T produced)
+    or GENERIC.  Returns (tau, spec_norm)."""
     T = _dev(T_tilde, torch.float32, "T_tilde")
     n, N, _ = T.shape
-    tau = torch.empty((n,), device=T.device, dtype=torch.float32)
-    nrm = torch.empty((n,), device=T.device, dtype=torch.float32)
-    check(lib().taser_step_size(n, N, _ptr(T), float(alpha), _ptr(tau), _ptr(nrm), _stream(stream)),
+    tau = tau if tau is not None else torch.empty((n,), device=T.device, dtype=torch.float32)
+    nrm = spec_norm if spec_norm is not None else torch.empty((n,), device=T.device, dtype=torch.float32)
+    s = KINDS[structure] if structure != GENERIC else GENERIC
+    check(lib().taser_step_size(n, N, _ptr(T), s, float(alpha), _ptr(tau), _ptr(nrm), _stream(stream)),
           "taser_step_size")
     return tau, nrm
 

@@ -63,46 +63,6 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Real index a of T -> (complex column of X, part): part 0 = real, 1 = imaginary,
-// 2 = the augmented column.
-__device__ __forceinline__ void t_index(int kind, int a, int P, int MP, int& col, int& part) {
-  if (kind == TASER_MIMO_QPSK && a >= P && a < 2 * P) {
-    col = a - P;
-    part = 1;
-  } else if (a < P) {
-    col = a;
-    part = 0;
-  } else {
-    col = MP - 1;
-    part = 2;
-  }
-}
-
-// T_ab = cr * Re(Gamma[col_a][col_b]) + ci * Im(Gamma[col_a][col_b]).
-//   QPSK (effective channel H / sqrt2, c = 1/sqrt2):
-//     user-user  [[Re G, -Im G], [Im G, Re G]] / 2;  user-aug -c [Re z; Im z];  aug-aug ||y||^2
-//   BPSK: Re G, -Re z, ||y||^2.   JED: -Re Gamma.
-__device__ __forceinline__ void t_coef(int kind, int pa, int pb, float& cr, float& ci) {
-  const float c = 0.70710678118654752f;
-  cr = 0.f;
-  ci = 0.f;
-  if (kind == TASER_SIMO_JED_BPSK) {
-    cr = -1.f;
-  } else if (kind == TASER_MIMO_BPSK) {
-    cr = ((pa == 2) == (pb == 2)) ? 1.f : -1.f;
-  } else if (pa == 2 && pb == 2) {
-    cr = 1.f;
-  } else if (pa == 2) {          // Gamma[aug][user] = conj(z_user)
-    if (pb == 0) cr = -c; else ci = c;
-  } else if (pb == 2) {          // Gamma[user][aug] = z_user
-    if (pa == 0) cr = -c; else ci = -c;
-  } else if (pa == pb) {
-    cr = 0.5f;
-  } else {
-    ci = pa == 0 ? -0.5f : 0.5f;
-  }
-}
-
 template <int MP>
 __global__ void __launch_bounds__(128)
 build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __restrict__ X,
@@ -118,7 +78,7 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   float* Ws = smem + warp * C::WARP_FLOATS;
 
   // Padding columns (2P .. 2MP-3 and >= 2MP) stay zero for the whole Gram phase.
-  for (int i = lane; i < C::WARP_FLOATS; i += 32) Ws[i] = 0.f;
+  for (int i = lane; i < C::WARP_FLOATS / 4; i += 32) reinterpret_cast<float4*>(Ws)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
   const bool jed = kind == TASER_SIMO_JED_BPSK;
   const int src_cols = jed ? P + 1 : P;                 // complex columns per antenna row
@@ -213,9 +173,9 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
 
   // Gamma_pq (p <= q) from the accumulators: lane (g, tq) holds rows 16i + g (+8) and
   // columns 8j + 2tq, +1 of G', i.e. complex column q = 4j + tq; rows 2p and 2p+1 of
-  // complex row p sit in lanes g and g + 1.  Each (p, q) with p <= q lies in exactly one
-  // computed tile, so Gamma is written once per entry (and mirrored).
-  float2* Gf = reinterpret_cast<float2*>(Ws);   // MP x MP complex, reuses the buffers
+  // complex row p sit in lanes g and g + 1 (even g combines).  Each (p, q) with p <= q
+  // lies in exactly one computed tile.
+  float gre[MT][NT][2], gim[MT][NT][2];
 #pragma unroll
   for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -224,82 +184,112 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
       float o[4];
 #pragma unroll
       for (int e = 0; e < 4; ++e) o[e] = __shfl_xor_sync(TASER_FULL_MASK, acc[i][j][e], 4);
-      if ((g & 1) == 0) {
-        const int q = 4 * j + tq;
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int p = 8 * i + 4 * h + (g >> 1);
-          if (p <= q && q < MP) {
-            const float re = acc[i][j][2 * h] + o[2 * h + 1];
-            const float im = p == q ? 0.f : acc[i][j][2 * h + 1] - o[2 * h];
-            Gf[p * MP + q] = make_float2(re, im);
-            Gf[q * MP + p] = make_float2(re, -im);
+      for (int h = 0; h < 2; ++h) {
+        gre[i][j][h] = acc[i][j][2 * h] + o[2 * h + 1];
+        gim[i][j][h] = acc[i][j][2 * h + 1] - o[2 * h];
+      }
+    }
+  const bool holder = (g & 1) == 0;
+  // Complex column p -> real indices of T: (ire, iim, kind of column) with the augmented
+  // column last.  QPSK user p: real p and U + p; BPSK / JED data column p: real p.
+  const bool qpsk = kind == TASER_MIMO_QPSK;
+  float* Dc = Ws + C::WARP_FLOATS - 2 * 72;   // D per complex column
+  float* rDc = Dc + 72;                       // 1 / D per complex column
+  float* Ts = Ws;                             // N x N staging of T~ (reuses the buffers)
+  __syncwarp();
+  // Diagonal: D and the flags.
+  uint32_t fl = 0;
+#pragma unroll
+  for (int i = 0; i < MT; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      if (!C::tile(i, j)) continue;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
+        if (holder && p == q && (p < P || p == MP - 1)) {
+          const bool aug = p == MP - 1;
+          const float taa = fabsf(gre[i][j][h]) * (qpsk && !aug ? 0.5f : 1.f);
+          if (!isfinite(gre[i][j][h])) fl |= TASER_FLAG_NONFINITE;
+          float da = sqrtf(taa);
+          if (taa == 0.f) {
+            da = 1.f;
+            fl |= TASER_FLAG_ZERO_DIAG;
           }
+          Dc[p] = da;
+          rDc[p] = 1.f / da;
         }
       }
     }
-  __syncwarp();
-
-  // D_a = sqrt|T_aa| (1 where T_aa == 0) and the flags.
-  float* Tdg = Ws + 2 * MP * MP;   // T_aa
-  float* rDsm = Tdg + 72;          // 1 / D_a
-  uint32_t fl = 0;
-  for (int a = lane; a < N; a += 32) {
-    int ca, pa;
-    t_index(kind, a, P, MP, ca, pa);
-    float dcr, dci;
-    t_coef(kind, pa, pa, dcr, dci);
-    const float taa = dcr * Gf[ca * MP + ca].x;
-    if (!isfinite(taa)) fl |= TASER_FLAG_NONFINITE;
-    float da = sqrtf(fabsf(taa));
-    if (taa == 0.f) {
-      da = 1.f;
-      fl |= TASER_FLAG_ZERO_DIAG;
-    }
-    Tdg[a] = taa;
-    rDsm[a] = 1.f / da;
-    Dout[inst * N + a] = da;
-  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
   if (lane == 0 && flags != nullptr) flags[inst] = fl;
   __syncwarp();
-
-  // T~_ab = T_ab / (D_a D_b); the diagonal is exactly sign(T_aa).  Per lane the
-  // coefficients of its columns b are precomputed for the three parts of row a.
-  const int nslot = (N + 31) >> 5;
-  int cb[3];
-  float rdb[3], cr[3][3], ci[3][3];
+  // Off-diagonal and diagonal entries of T~ into the staging tile.
+  const int NU = P;                   // users / data columns
+  const int Nr = N;
+  const float dsg = kind == TASER_SIMO_JED_BPSK ? -1.f : 1.f;   // sign of T_aa
 #pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int b = lane + 32 * k;
-    int pb;
-    t_index(kind, b < N ? b : 0, P, MP, cb[k], pb);
-    rdb[k] = b < N ? rDsm[b] : 0.f;
+  for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int pa = 0; pa < 3; ++pa) t_coef(kind, pa, pb, cr[k][pa], ci[k][pa]);
-  }
-  float* To = Tt + inst * (int64_t)N * N;
-  for (int a = 0; a < N; ++a) {
-    int ca, pa;
-    t_index(kind, a, P, MP, ca, pa);
-    const float ra = rDsm[a];
-    const float taa = Tdg[a];
-    const float sgn = taa > 0.f ? 1.f : (taa < 0.f ? -1.f : 0.f);
-    const float2* grow = Gf + ca * MP;
-    float* trow = To + (int64_t)a * N;
+    for (int j = 0; j < NT; ++j) {
+      if (!C::tile(i, j)) continue;
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-      if (k >= nslot) break;
-      const int b = lane + 32 * k;
-      if (b < N) {
-        const float c0 = pa == 0 ? cr[k][0] : (pa == 1 ? cr[k][1] : cr[k][2]);
-        const float c1 = pa == 0 ? ci[k][0] : (pa == 1 ? ci[k][1] : ci[k][2]);
-        const float2 gv = grow[cb[k]];
-        const float tab = fmaf(c0, gv.x, c1 * gv.y);
-        trow[b] = (a == b) ? sgn : tab * ra * rdb[k];
+      for (int h = 0; h < 2; ++h) {
+        const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
+        const bool pv = p < NU, qv = q < NU, qa = q == MP - 1, pa = p == MP - 1;
+        if (!holder || p > q || !(pv || pa) || !(qv || qa)) continue;
+        const float re = gre[i][j][h], im = gim[i][j][h];
+        const float sc = rDc[p] * rDc[q];
+        const int ap = pa ? Nr - 1 : p, aq = qa ? Nr - 1 : q;     // real index of the Re part
+        if (p == q) {
+          const float dv = re == 0.f ? 0.f : dsg;
+          Ts[ap * Nr + ap] = dv;
+          if (qpsk && !pa) {
+            Ts[(NU + p) * Nr + (NU + p)] = dv;
+            Ts[p * Nr + (NU + p)] = 0.f;
+            Ts[(NU + p) * Nr + p] = 0.f;
+          }
+          continue;
+        }
+        if (kind == TASER_SIMO_JED_BPSK) {
+          const float v = -re * sc;
+          Ts[ap * Nr + aq] = v;
+          Ts[aq * Nr + ap] = v;
+        } else if (kind == TASER_MIMO_BPSK) {
+          const float v = (qa ? -re : re) * sc;
+          Ts[ap * Nr + aq] = v;
+          Ts[aq * Nr + ap] = v;
+        } else if (qa) {
+          // user p with the augmented column: -c [Re z; Im z]
+          const float c = 0.70710678118654752f;
+          const float vr = -c * re * sc, vi = -c * im * sc;
+          Ts[p * Nr + aq] = vr;
+          Ts[aq * Nr + p] = vr;
+          Ts[(NU + p) * Nr + aq] = vi;
+          Ts[aq * Nr + (NU + p)] = vi;
+        } else {
+          // users p < q: [[Re G, -Im G], [Im G, Re G]] / 2
+          const float vr = 0.5f * re * sc, vi = 0.5f * im * sc;
+          Ts[p * Nr + q] = vr;
+          Ts[q * Nr + p] = vr;
+          Ts[(NU + p) * Nr + (NU + q)] = vr;
+          Ts[(NU + q) * Nr + (NU + p)] = vr;
+          Ts[p * Nr + (NU + q)] = -vi;
+          Ts[(NU + q) * Nr + p] = -vi;
+          Ts[(NU + p) * Nr + q] = vi;
+          Ts[q * Nr + (NU + p)] = vi;
+        }
       }
     }
+  __syncwarp();
+  // Coalesced copy of T~ and D to global memory.
+  float* To = Tt + inst * (int64_t)Nr * Nr;
+  for (int e = lane; e < Nr * Nr; e += 32) To[e] = Ts[e];
+  for (int a = lane; a < Nr; a += 32) {
+    const int p = a == Nr - 1 ? MP - 1 : (qpsk && a >= NU ? a - NU : a);
+    Dout[inst * Nr + a] = Dc[p];
   }
 }
 
@@ -307,7 +297,7 @@ template <int MP>
 static cudaError_t launch_build(int kind, int64_t batch, int B, int P, int N, const float2* X, const float2* y,
                                 float* Tt, float* D, uint32_t* flags, cudaStream_t st) {
   using C = BuildCfg<MP>;
-  static_assert(2 * MP * MP + 144 <= C::WARP_FLOATS, "epilogue scratch must fit the staging buffers");
+  static_assert((2 * MP - 1) * (2 * MP - 1) + 144 <= C::WARP_FLOATS, "epilogue scratch must fit the staging buffers");
   if (C::SMEM_BYTES > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(build_T_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM_BYTES);

@@ -103,7 +103,7 @@ taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const voi
   if (!jed) TASER_REQUIRE_PTR(y, "y");
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(D, "D");
-  TASER_REQUIRE_PTR(tau, "tau");
+  if (tau != nullptr) TASER_REQUIRE(aligned16(tau), "tau must be 16-byte aligned");
   if (spec_norm != nullptr) TASER_REQUIRE(aligned16(spec_norm), "spec_norm must be 16-byte aligned");
   if (flags != nullptr) TASER_REQUIRE(aligned16(flags), "flags must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -111,25 +111,31 @@ taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const voi
   cudaError_t e = taser::build_T(kind, batch, B, P, N, H_or_Y, y, T_tilde, D, flags, st);
   if (e == cudaErrorNotSupported) return fail(TASER_ERR_UNSUPPORTED, "no build kernel for %d columns", P + 1);
   if (e != cudaSuccess) return from_cuda(e, "build_T");
-  // QPSK: ||T~||_2 equals the norm of its (U+1) x (U+1) complex Hermitian form.
-  if (kind == TASER_MIMO_QPSK) {
-    return from_cuda(taser::spectral_qpsk(batch, U_or_K, T_tilde, alpha, tau, spec_norm, st), "spectral_qpsk");
-  }
-  // T = A^T A is positive semidefinite (MIMO), T = -A^T A negative semidefinite (JED).
-  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, jed ? -1 : 1, tau, spec_norm, st), "spectral");
+  if (tau == nullptr) return ok();
+  return taser_step_size(batch, N, T_tilde, kind, alpha, tau, spec_norm, stream);
 }
 
-taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, float alpha, float* tau, float* spec_norm,
-                             void* stream) {
+taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int structure, float alpha, float* tau,
+                             float* spec_norm, void* stream) {
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
   TASER_REQUIRE(alpha > 0.f && alpha < 1.f, "alpha must lie in (0, 1) (got %g)", (double)alpha);
+  TASER_REQUIRE(structure == TASER_GENERIC_SYMMETRIC || structure == TASER_MIMO_BPSK ||
+                    structure == TASER_MIMO_QPSK || structure == TASER_SIMO_JED_BPSK,
+                "unknown structure %d", structure);
+  TASER_REQUIRE(structure != TASER_MIMO_QPSK || N % 2 == 1, "QPSK structure needs odd N = 2U + 1 (got %d)", N);
   if (batch == 0) return ok();
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(tau, "tau");
   if (spec_norm != nullptr) TASER_REQUIRE(aligned16(spec_norm), "spec_norm must be 16-byte aligned");
-  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, 0, tau, spec_norm, static_cast<cudaStream_t>(stream)),
-                   "spectral");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (structure == TASER_MIMO_QPSK) {
+    // ||T~||_2 equals the norm of its (U+1) x (U+1) complex Hermitian form.
+    return from_cuda(taser::spectral_qpsk(batch, (N - 1) / 2, T_tilde, alpha, tau, spec_norm, st), "spectral_qpsk");
+  }
+  // T = A^T A is positive semidefinite (MIMO), T = -A^T A negative semidefinite (JED).
+  const int hint = structure == TASER_MIMO_BPSK ? 1 : (structure == TASER_SIMO_JED_BPSK ? -1 : 0);
+  return from_cuda(taser::spectral(batch, N, T_tilde, alpha, hint, tau, spec_norm, st), "spectral");
 }
 
 taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const float* D, const float* tau, int t_max,

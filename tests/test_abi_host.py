@@ -91,7 +91,9 @@ def test_build_empty_batch_is_noop(lib):
 
 
 def test_step_size_rejects_invalid_arguments(lib):
-    assert lib.taser_step_size(4, 1, P16, 0.5, P16, None, None) == 1
-    assert lib.taser_step_size(4, 33, P16, 1.5, P16, None, None) == 1
-    assert lib.taser_step_size(4, 33, None, 0.5, P16, None, None) == 1
-    assert lib.taser_step_size(0, 33, None, 0.5, None, None, None) == 0
+    assert lib.taser_step_size(4, 1, P16, -1, 0.5, P16, None, None) == 1
+    assert lib.taser_step_size(4, 33, P16, -1, 1.5, P16, None, None) == 1
+    assert lib.taser_step_size(4, 33, None, -1, 0.5, P16, None, None) == 1
+    assert lib.taser_step_size(4, 33, P16, 7, 0.5, P16, None, None) == 1
+    assert lib.taser_step_size(4, 32, P16, 1, 0.5, P16, None, None) == 1   # QPSK needs odd N
+    assert lib.taser_step_size(0, 33, None, -1, 0.5, None, None, None) == 0

@@ -156,6 +156,24 @@ def test_step_size_matches_oracle(T, N):
     np.testing.assert_allclose(nrm.cpu().numpy(), O.spectral_norm(M.astype(np.float64)), rtol=1e-5)
 
 
+@pytest.mark.parametrize("kind,B,M", [("mimo_qpsk", 128, 16), ("mimo_qpsk", 20, 3), ("mimo_qpsk", 256, 32),
+                                      ("mimo_bpsk", 64, 24), ("jed_bpsk", 16, 32), ("jed_bpsk", 16, 16)])
+def test_step_size_with_structure_hint(T, kind, B, M):
+    """The structure-aware methods (complex Hermitian form for QPSK, one-sided search for
+    semidefinite T~) agree with the oracle's eigensolver on T~ built by the oracle."""
+    n = 41
+    if kind == "jed_bpsk":
+        w = make_jed(n, B, M, 3.0, seed=M)
+        r = O.detect(kind, w["Y"], None, ALPHA, 1)
+    else:
+        w = make_mimo(n, B, M, 3.0, kind[5:], seed=M)
+        r = O.detect(kind, w["H"], w["y"], ALPHA, 1)
+    Tt = r["T_tilde"].astype(np.float32)
+    for structure in (kind, T.GENERIC):
+        tau, nrm = T.step_size(to_dev(Tt)[0], ALPHA, structure=structure)
+        np.testing.assert_allclose(nrm.cpu().numpy(), O.spectral_norm(Tt.astype(np.float64)), rtol=1e-5)
+
+
 @pytest.mark.parametrize("kind,B,M,t_max,precision", [
     ("mimo_bpsk", 32, 8, 10, "fp32"), ("mimo_qpsk", 128, 16, 20, "fp32"), ("jed_bpsk", 16, 16, 20, "fp32"),
     ("jed_bpsk", 16, 32, 20, "fp32"), ("mimo_qpsk", 64, 8, 20, "fp32"), ("mimo_qpsk", 256, 32, 10, "fp32"),
