@@ -251,3 +251,38 @@ def test_full_size_qpsk_128x16_sampled(T, precision):
     cn = torch.linalg.vector_norm(Lg, dim=1)
     assert torch.allclose(cn, out["D"], rtol=1e-4)
     assert torch.all(s.abs() == 1)
+
+
+@pytest.mark.parametrize("kind,B,M,t_max,precision", [("mimo_qpsk", 128, 16, 20, "bf16_tc"),
+                                                      ("mimo_bpsk", 32, 8, 10, "fp32"),
+                                                      ("jed_bpsk", 16, 16, 20, "fp32")])
+def test_run_host_matches_device_path(T, kind, B, M, t_max, precision):
+    """taser_run_host (host buffers in and out, caller-owned device workspace) gives the
+    same decisions and flags as the device-resident calls, and its decisions agree with
+    the oracle where they are confident."""
+    n = 517
+    if kind == "jed_bpsk":
+        w = make_jed(n, B, M, np.linspace(0, 12, n), seed=9)
+        X, y = w["Y"], None
+    else:
+        w = make_mimo(n, B, M, np.linspace(0, 20, n), kind[5:], seed=9)
+        X, y = w["H"], w["y"]
+    N = T.problem_size(kind, M)
+    ws = torch.empty(T.host_workspace_bytes(kind, n, B, M), device="cuda", dtype=torch.uint8)
+    Xh = torch.from_numpy(X).pin_memory()
+    yh = torch.from_numpy(y).pin_memory() if y is not None else None
+    s_host = torch.empty((n, N - 1), dtype=torch.int8).pin_memory()
+    f_host = torch.empty((n,), dtype=torch.int32).pin_memory()
+    for _ in range(2):                                    # the workspace is reused as scratch
+        s_host.fill_(0)
+        T.run_host(kind, Xh, yh, ALPHA, t_max, precision, ws, s_host, flags=f_host)
+        torch.cuda.synchronize()
+        out = T.build_T(kind, *to_dev(X), None if y is None else to_dev(y)[0], alpha=ALPHA)
+        s, _, flags = T.detect(out["T_tilde"], out["D"], out["tau"], t_max, precision, want_L=False,
+                               flags=out["flags"])
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(s_host.numpy(), s.cpu().numpy())
+        np.testing.assert_array_equal(f_host.numpy(), flags.cpu().numpy())
+    r = O.detect(kind, X, y, ALPHA, t_max)
+    m = confident(r["L"], 1e-3 if precision == "fp32" else 5e-2)
+    np.testing.assert_array_equal(s_host.numpy()[m], r["s_hat"][m])
