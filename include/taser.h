@@ -179,6 +179,34 @@ taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const vo
                             void* workspace, size_t workspace_bytes, int8_t* s_hat,
                             uint32_t* flags, void* stream);
 
+/*
+ * taser_run_host_static -- taser_run_host without a caller-provided workspace.
+ *
+ * The paper has no counterpart: this entry point exists for callers that cannot
+ * allocate device memory.  Examples are baseband pipelines that reserve every buffer at
+ * start-up and must not call cudaMalloc inside a slot (it can synchronise the device and
+ * stall a real-time deadline), and plug-ins whose host framework owns the whole device
+ * memory pool and hands them none.  Such callers pass only their inputs and outputs.
+ *
+ * The scratch (device copies of H and y or Y, T~, D, tau, the decisions and flags) lives
+ * in one file-scope device array of TASER_STATIC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.  A batch whose
+ * taser_host_workspace_bytes(kind, batch, B, U_or_K) exceeds that size is rejected with
+ * TASER_ERR_INVALID_ARG (split it into smaller calls).  Nothing in the scratch has to
+ * start at zero: every intermediate is written before it is read.  The array keeps the
+ * last call's contents, and all calls share it: calls whose GPU work overlaps (on
+ * different streams, or from several threads) race on it and must be serialised by the
+ * caller.  The first call on a device looks up the array's device address for that
+ * device (cudaGetSymbolAddress, with that device current); make that first call before
+ * any stream capture.  Arguments and outputs are as in taser_run_host.
+ */
+#define TASER_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
+
+taser_status taser_run_host_static(int kind, int64_t batch, int B, int U_or_K,
+                                   const void* H_or_Y, const void* y, float alpha, int t_max,
+                                   int precision, int lnn_mode, int8_t* s_hat,
+                                   uint32_t* flags, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

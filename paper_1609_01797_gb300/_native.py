@@ -18,7 +18,12 @@ SIGNATURES = {
     "taser_host_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i64, _c_i32, _c_i32]),
     "taser_run_host": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32, _vp,
                                 ctypes.c_size_t, _vp, _vp, _vp]),
+    "taser_run_host_static": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32,
+                                       _vp, _vp, _vp]),
 }
+
+# Capacity of the library's static device scratch (include/taser.h).
+STATIC_SCRATCH_BYTES = 64 << 20
 
 _lib = None
 

@@ -113,3 +113,17 @@ def run_host(kind, H_or_Y, y, alpha, t_max, precision, workspace, s_hat, flags=N
                               int(t_max), PRECISIONS[precision], LNN_MODES[lnn_mode], _ptr(workspace),
                               workspace.numel(), _ptr(s_hat), _ptr(flags), _stream(stream))
     check(st, "taser_run_host")
+
+
+def run_host_static(kind, H_or_Y, y, alpha, t_max, precision, s_hat, flags=None, lnn_mode="fixed", stream=None):
+    """run_host for callers that cannot allocate device memory: the workspace is the
+    library's static device scratch (a batch must fit in it; see include/taser.h)."""
+    k = KINDS[kind]
+    n, B, M = H_or_Y.shape
+    for name, t in (("H_or_Y", H_or_Y), ("s_hat", s_hat)) + ((("y", y),) if k != JED_BPSK else ()):
+        if t.is_cuda or not t.is_contiguous():
+            raise ValueError("%s must be a contiguous host tensor" % name)
+    st = lib().taser_run_host_static(k, n, B, M, _ptr(H_or_Y), _ptr(y if k != JED_BPSK else None), float(alpha),
+                                     int(t_max), PRECISIONS[precision], LNN_MODES[lnn_mode], _ptr(s_hat),
+                                     _ptr(flags), _stream(stream))
+    check(st, "taser_run_host_static")

@@ -242,3 +242,8 @@ taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const vo
 }
 
 }  // extern "C"
+
+namespace taser {
+// Records `msg` as the thread's last error (taser_last_error) and returns `st`.
+taser_status report(taser_status st, const char* msg) { return fail(st, "%s", msg); }
+}  // namespace taser
