@@ -180,6 +180,40 @@ taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const vo
                             uint32_t* flags, void* stream);
 
 /*
+ * taser_unfolded_forward -- unfolded TASER: Algorithm 1 with one step size per
+ * iteration, tau_t = alpha_t / ||T~||_2, learnable alpha_t shared by all instances
+ * (mode TASER_LNN_FIXED, FP32).  Forward pass of the training path.
+ *   T_tilde, D  as in taser_detect; N in [2, 33].
+ *   inv_norm    float [batch] = 1 / ||T~||_2 (from spec_norm of taser_build_T).
+ *   alpha_t     float [t_max].
+ *   c           checkpoint spacing, 1 <= c <= t_max (ceil(sqrt(t_max)) balances memory
+ *               and recomputation).
+ *   ckpt        out float [batch][ceil(t_max / c)][N][N]: L~(k c) for k = 0, 1, ..., or
+ *               NULL when no backward pass follows.
+ *   soft        out float [batch][N-1]: x_k = L~(t_max)_{N,k} / D_k, the last row of the
+ *               unit-column factor L = L~ D^-1 (Sec. III-C), in [-1, 1].
+ *   s_hat       out int8 [batch][N-1] = sign(x_k), or NULL.
+ */
+taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, const float* D,
+                                    const float* inv_norm, const float* alpha_t, int t_max, int c,
+                                    float* ckpt, float* soft, int8_t* s_hat, void* stream);
+
+/*
+ * taser_unfolded_backward -- adjoint of taser_unfolded_forward.  Given grad_soft =
+ * dloss/dsoft (float [batch][N-1]), writes grad_tau (float [batch][t_max]) =
+ * dloss/dtau_t per instance and, if grad_alpha is not NULL, grad_alpha (float [t_max]) =
+ * sum_n grad_tau[n][t] inv_norm[n] in a fixed reduction order.  Each segment of c
+ * iterations is recomputed from ckpt (same arguments as the forward call) and
+ * differentiated in reverse; the gradient flows through the soft last row only.
+ * Needs 4 (c + 2) (NB + 1)(NB + 4) floats of shared memory per block, NB the bucket of N
+ * (c <= 10 at N = 33); larger c is rejected.
+ */
+taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde, const float* D,
+                                     const float* inv_norm, const float* alpha_t, int t_max, int c,
+                                     const float* ckpt, const float* grad_soft, float* grad_tau,
+                                     float* grad_alpha, void* stream);
+
+/*
  * taser_run_host_static -- taser_run_host without a caller-provided workspace.
  *
  * The paper has no counterpart: this entry point exists for callers that cannot

@@ -4,4 +4,5 @@ The Python layer only marshals device pointers and the current CUDA stream into 
 C ABI declared in include/taser.h; every step of the detector runs in CUDA kernels.
 """
 from .api import (BPSK, GENERIC, JED_BPSK, QPSK, PRECISIONS, build_T, detect, problem_size,  # noqa: F401
-                  step_size, host_workspace_bytes, run_host, run_host_static)
+                  step_size, host_workspace_bytes, run_host, run_host_static,
+                  unfolded_forward, unfolded_backward, UnfoldedTASER)

@@ -20,6 +20,9 @@ SIGNATURES = {
                                 ctypes.c_size_t, _vp, _vp, _vp]),
     "taser_run_host_static": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32,
                                        _vp, _vp, _vp]),
+    "taser_unfolded_forward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
+    "taser_unfolded_backward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp,
+                                         _vp]),
 }
 
 # Capacity of the library's static device scratch (include/taser.h).

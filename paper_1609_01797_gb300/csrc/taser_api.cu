@@ -12,6 +12,10 @@ cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, int hin
                      cudaStream_t st);
 cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
                           cudaStream_t st);
+cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,
+                     const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
+                     const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st);
+size_t unfolded_backward_smem(int N, int c);
 cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                         int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
 cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
@@ -247,3 +251,53 @@ namespace taser {
 // Records `msg` as the thread's last error (taser_last_error) and returns `st`.
 taser_status report(taser_status st, const char* msg) { return fail(st, "%s", msg); }
 }  // namespace taser
+
+extern "C" {
+
+taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, const float* D, const float* inv_norm,
+                                    const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
+                                    void* stream) {
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(N >= 2 && N <= 33, "unfolded TASER supports 2 <= N <= 33 (got %d)", N);
+  TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
+  TASER_REQUIRE(c >= 1 && c <= t_max, "checkpoint spacing c must lie in [1, t_max] (got %d)", c);
+  if (batch == 0) return ok();
+  TASER_REQUIRE_PTR(T_tilde, "T_tilde");
+  TASER_REQUIRE_PTR(D, "D");
+  TASER_REQUIRE_PTR(inv_norm, "inv_norm");
+  TASER_REQUIRE_PTR(alpha_t, "alpha_t");
+  TASER_REQUIRE_PTR(soft, "soft");
+  if (ckpt != nullptr) TASER_REQUIRE(aligned16(ckpt), "ckpt must be 16-byte aligned");
+  if (s_hat != nullptr) TASER_REQUIRE(aligned16(s_hat), "s_hat must be 16-byte aligned");
+  return from_cuda(taser::unfolded(false, batch, N, T_tilde, D, inv_norm, alpha_t, t_max, c, ckpt, soft, s_hat,
+                                   nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream)),
+                   "unfolded_forward");
+}
+
+taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde, const float* D,
+                                     const float* inv_norm, const float* alpha_t, int t_max, int c,
+                                     const float* ckpt, const float* grad_soft, float* grad_tau, float* grad_alpha,
+                                     void* stream) {
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(N >= 2 && N <= 33, "unfolded TASER supports 2 <= N <= 33 (got %d)", N);
+  TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
+  TASER_REQUIRE(c >= 1 && c <= t_max, "checkpoint spacing c must lie in [1, t_max] (got %d)", c);
+  TASER_REQUIRE(taser::unfolded_backward_smem(N, c) <= 227 * 1024,
+                "checkpoint spacing c = %d needs %zu bytes of shared memory per block (limit 232448)", c,
+                taser::unfolded_backward_smem(N, c));
+  if (batch == 0) return ok();
+  TASER_REQUIRE_PTR(T_tilde, "T_tilde");
+  TASER_REQUIRE_PTR(D, "D");
+  TASER_REQUIRE_PTR(inv_norm, "inv_norm");
+  TASER_REQUIRE_PTR(alpha_t, "alpha_t");
+  TASER_REQUIRE_PTR(ckpt, "ckpt");
+  TASER_REQUIRE_PTR(grad_soft, "grad_soft");
+  TASER_REQUIRE_PTR(grad_tau, "grad_tau");
+  if (grad_alpha != nullptr) TASER_REQUIRE(aligned16(grad_alpha), "grad_alpha must be 16-byte aligned");
+  return from_cuda(taser::unfolded(true, batch, N, T_tilde, D, inv_norm, alpha_t, t_max, c, const_cast<float*>(ckpt),
+                                   nullptr, nullptr, grad_soft, grad_tau, grad_alpha,
+                                   static_cast<cudaStream_t>(stream)),
+                   "unfolded_backward");
+}
+
+}  // extern "C"

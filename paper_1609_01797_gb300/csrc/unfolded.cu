@@ -1,0 +1,308 @@
+// Unfolded TASER: Algorithm 1 with a learnable step per iteration, tau_t = alpha_t /
+// ||T~||_2, its FP32 forward with checkpoints, and the hand-written adjoint.
+//
+// Forward (mode "fixed", L~_NN = D_NN):  V_t = L~(t-1) - tau_t tril(2 L~(t-1) T~),
+// L~(t) = prox(V_t); soft output x_k = L~(t_max)_{N,k} / D_k (the last row of the
+// unit-column factor L = L~ D^-1).  L~(kc) is saved every c iterations.
+//
+// Adjoint of one step, given Lbar = dloss/dL~(t):
+//   G = tril(2 L~(t-1) T~),  u_k = V_{.k} / ||V_{.k}||,
+//   Vbar_{.k} = (D_k / ||V_{.k}||) (Lbar_{.k} - u_k (u_k . Lbar_{.k}))  for k < N-1, Vbar_{.N} = 0,
+//   taubar_t = - sum_{i >= j} Vbar_ij G_ij,
+//   dloss/dL~(t-1) = tril(Vbar - tau_t Vbar (2 T~)).
+// Each segment of c iterations is recomputed from its checkpoint and kept in shared
+// memory while it is differentiated in reverse.
+//
+// Mapping as in the FP32 detector: one warp per instance, lane j owns column j of L~, V,
+// G, Vbar and Lbar; the column j of T~ stays in registers; rows of L~ and Vbar are
+// broadcast from shared memory, so both products keep the triangular skip.
+#include "common.cuh"
+
+namespace taser {
+
+template <int NB>
+struct UfCfg {
+  static constexpr int S = NB + 4;                  // smem row stride (floats)
+  static constexpr int MAT = (NB + 1) * S;          // one bucket matrix in smem
+  static constexpr int WARPS = 4;
+};
+
+// acc_i = sum_{k <= i} R[i][k] t[k] for the rows i of a lower-triangular smem matrix R.
+template <int NB>
+__device__ __forceinline__ float tri_row(const float* R, int i, const float (&t)[NB + 1]) {
+  float acc = 0.f;
+  const float* row = R + i * UfCfg<NB>::S;
+#pragma unroll
+  for (int k4 = 0; k4 <= NB; k4 += 4) {
+    if (k4 > i) break;
+    const float4 q = *reinterpret_cast<const float4*>(row + k4);
+    acc = fmaf(q.x, t[k4], acc);
+    if (k4 + 1 <= i) acc = fmaf(q.y, t[k4 + 1], acc);
+    if (k4 + 2 <= i) acc = fmaf(q.z, t[k4 + 2], acc);
+    if (k4 + 3 <= i) acc = fmaf(q.w, t[k4 + 3], acc);
+  }
+  return acc;
+}
+
+// One forward step on the smem iterate Lin -> Lout (column j of the result also
+// returned in l[]).  Returns nothing; l holds L~(t) column j on exit.
+template <int NB>
+__device__ __forceinline__ void forward_step(const float* Lin, float* Lout, float (&l)[NB + 1],
+                                             const float (&tcol)[NB + 1], float tau, float Dj, int j) {
+  float v[NB + 1];
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) {
+    const float g = 2.f * tri_row<NB>(Lin, i, tcol);
+    v[i] = (i >= j) ? fmaf(-tau, g, Lin[i * UfCfg<NB>::S + j]) : 0.f;
+  }
+  float n2 = 0.f;
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) n2 = fmaf(v[i], v[i], n2);
+  const float sc = n2 > 0.f ? Dj * rsqrtf(n2) : 0.f;
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) {
+    l[i] = v[i] * sc;
+    Lout[i * UfCfg<NB>::S + j] = l[i];
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void load_tcol(float (&tcol)[NB + 1], const float* T, int N, int jr) {
+#pragma unroll
+  for (int k = 0; k <= NB; ++k) {
+    const int kr = bucket_to_real(k, N, NB);
+    tcol[k] = (jr >= 0 && kr >= 0) ? T[(int64_t)kr * N + jr] : 0.f;
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void init_diag(float* L, int j, float Dj, float DN, int lane) {
+  for (int idx = lane; idx < UfCfg<NB>::MAT; idx += 32) L[idx] = 0.f;
+  __syncwarp();
+  if (j < NB) L[j * UfCfg<NB>::S + j] = Dj;
+  if (lane == 0) L[NB * UfCfg<NB>::S + NB] = DN;
+  __syncwarp();
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128)
+unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
+                        const float* __restrict__ inv_norm, const float* __restrict__ alpha_t, int t_max, int c,
+                        float* __restrict__ ckpt, float* __restrict__ soft, int8_t* __restrict__ s_hat) {
+  using C = UfCfg<NB>;
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
+  if (inst >= batch) return;
+  float* buf0 = smem + warp * 2 * C::MAT;
+  float* buf1 = buf0 + C::MAT;
+  const int j = lane;                                  // lanes >= NB carry zero columns
+  const int jr = j < N - 1 ? j : -1;
+  const float* T = Tt + inst * (int64_t)N * N;
+  float tcol[NB + 1];
+  load_tcol<NB>(tcol, T, N, jr);
+  const float Dj = jr >= 0 ? Dg[inst * N + jr] : 0.f;
+  const float DN = Dg[inst * N + N - 1];
+  const float inv = inv_norm[inst];
+  const int n_ckpt = (t_max + c - 1) / c;
+  init_diag<NB>(buf0, j < NB ? j : NB, j < NB ? Dj : 0.f, DN, lane);
+  float l[NB + 1];
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) l[i] = (i == j) ? Dj : 0.f;
+  float* cur = buf0;
+  float* nxt = buf1;
+  for (int idx = lane; idx < C::MAT; idx += 32) nxt[idx] = cur[idx];  // keeps L~_NN in both buffers
+  __syncwarp();
+  for (int t = 0; t < t_max; ++t) {
+    if (t % c == 0 && ckpt != nullptr) {
+      // checkpoint L~(t) in real indices, full N x N with zeros above the diagonal
+      float* out = ckpt + (inst * n_ckpt + t / c) * (int64_t)N * N;
+      for (int e = lane; e < N * N; e += 32) {
+        const int r = e / N, cc = e % N;
+        const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
+        out[e] = cur[br * C::S + bc];
+      }
+    }
+    const float tau = alpha_t[t] * inv;
+    if (j < NB) forward_step<NB>(cur, nxt, l, tcol, tau, Dj, j);
+    __syncwarp();
+    float* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  }
+  if (jr >= 0) {
+    soft[inst * (N - 1) + jr] = Dj > 0.f ? l[NB] / Dj : 0.f;
+    if (s_hat != nullptr) s_hat[inst * (N - 1) + jr] = l[NB] >= 0.f ? int8_t(1) : int8_t(-1);
+  }
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128)
+unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
+                         const float* __restrict__ inv_norm, const float* __restrict__ alpha_t, int t_max, int c,
+                         const float* __restrict__ ckpt, const float* __restrict__ grad_soft,
+                         float* __restrict__ grad_tau) {
+  using C = UfCfg<NB>;
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
+  if (inst >= batch) return;
+  // per warp: c + 1 iterates of the segment and the Vbar rows
+  float* seg = smem + (int64_t)warp * (c + 2) * C::MAT;
+  float* vb = seg + (c + 1) * C::MAT;
+  const int j = lane;
+  const int jr = j < N - 1 ? j : -1;
+  const float* T = Tt + inst * (int64_t)N * N;
+  float tcol[NB + 1];
+  load_tcol<NB>(tcol, T, N, jr);
+  const float Dj = jr >= 0 ? Dg[inst * N + jr] : 0.f;
+  const float inv = inv_norm[inst];
+  const int n_ckpt = (t_max + c - 1) / c;
+  // Lbar(t_max): only the last row, dloss/dL~_{N,k} = dloss/dx_k / D_k
+  float lbar[NB + 1];
+#pragma unroll
+  for (int i = 0; i <= NB; ++i) lbar[i] = 0.f;
+  if (jr >= 0 && Dj > 0.f) lbar[NB] = grad_soft[inst * (N - 1) + jr] / Dj;
+
+  for (int kc = n_ckpt - 1; kc >= 0; --kc) {
+    const int t0 = kc * c, t1 = min(t0 + c, t_max);
+    // L~(t0) from the checkpoint into seg[0] (bucket layout)
+    {
+      const float* in = ckpt + (inst * n_ckpt + kc) * (int64_t)N * N;
+      for (int idx = lane; idx < C::MAT; idx += 32) seg[idx] = 0.f;
+      __syncwarp();
+      for (int e = lane; e < N * N; e += 32) {
+        const int r = e / N, cc = e % N;
+        const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
+        seg[br * C::S + bc] = in[e];
+      }
+      __syncwarp();
+    }
+    // recompute L~(t0+1) .. L~(t1-1) into seg[1..]
+    float l[NB + 1];
+    for (int s = t0 + 1; s < t1; ++s) {
+      float* Lin = seg + (s - 1 - t0) * C::MAT;
+      float* Lout = seg + (s - t0) * C::MAT;
+      for (int idx = lane; idx < C::MAT; idx += 32) Lout[idx] = Lin[idx];  // zeros and L~_NN
+      __syncwarp();
+      if (j < NB) forward_step<NB>(Lin, Lout, l, tcol, alpha_t[s - 1] * inv, Dj, j);
+      __syncwarp();
+    }
+    // reverse through steps t1 .. t0+1 (step s maps L~(s-1) -> L~(s), uses tau_{s})
+    for (int s = t1; s > t0; --s) {
+      const float* Lin = seg + (s - 1 - t0) * C::MAT;
+      const float tau = alpha_t[s - 1] * inv;
+      float g[NB + 1], v[NB + 1], vbar[NB + 1];
+#pragma unroll
+      for (int i = 0; i <= NB; ++i) {
+        g[i] = (j < NB) ? 2.f * tri_row<NB>(Lin, i, tcol) : 0.f;
+        v[i] = (i >= j && j < NB) ? fmaf(-tau, g[i], Lin[i * C::S + (j < NB ? j : 0)]) : 0.f;
+      }
+      float n2 = 0.f;
+#pragma unroll
+      for (int i = 0; i <= NB; ++i) n2 = fmaf(v[i], v[i], n2);
+      float proj = 0.f;
+      const float rn = (n2 > 0.f && jr >= 0) ? rsqrtf(n2) : 0.f;
+#pragma unroll
+      for (int i = 0; i <= NB; ++i) proj = fmaf(v[i] * rn, lbar[i], proj);
+      const float f = Dj * rn;
+      float tb = 0.f;
+#pragma unroll
+      for (int i = 0; i <= NB; ++i) {
+        vbar[i] = (i >= j) ? f * fmaf(-v[i] * rn, proj, lbar[i]) : 0.f;
+        tb = fmaf(vbar[i], g[i], tb);
+      }
+      tb = -warp_sum(tb);
+      if (lane == 0) grad_tau[inst * t_max + (s - 1)] = tb;
+      // Lbar(s-1) = tril(Vbar - tau Vbar (2 T~)): rows of Vbar through shared memory
+#pragma unroll
+      for (int i = 0; i <= NB; ++i)
+        if (j < NB) vb[i * C::S + j] = vbar[i];
+      if (lane == 0) vb[NB * C::S + NB] = 0.f;   // column N of Vbar is zero
+      __syncwarp();
+#pragma unroll
+      for (int i = 0; i <= NB; ++i) {
+        const float p = 2.f * tri_row<NB>(vb, i, tcol);
+        lbar[i] = (i >= j && j < NB) ? fmaf(-tau, p, vbar[i]) : 0.f;
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// grad_alpha[t] = sum_n grad_tau[n][t] * inv_norm[n], one block per t, fixed-order tree.
+__global__ void reduce_alpha_kernel(int64_t batch, int t_max, const float* __restrict__ grad_tau,
+                                     const float* __restrict__ inv_norm, float* __restrict__ grad_alpha) {
+  __shared__ float part[256];
+  const int t = blockIdx.x;
+  float acc = 0.f;
+  for (int64_t n = threadIdx.x; n < batch; n += blockDim.x) acc = fmaf(grad_tau[n * t_max + t], inv_norm[n], acc);
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) part[threadIdx.x] += part[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) grad_alpha[t] = part[0];
+}
+
+template <int NB>
+static cudaError_t launch_unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D,
+                                   const float* inv_norm, const float* alpha_t, int t_max, int c, float* ckpt,
+                                   float* soft, int8_t* s_hat, const float* grad_soft, float* grad_tau,
+                                   cudaStream_t st) {
+  using C = UfCfg<NB>;
+  const int64_t blocks = (batch + C::WARPS - 1) / C::WARPS;
+  if (!backward) {
+    const size_t smem = (size_t)C::WARPS * 2 * C::MAT * sizeof(float);
+    if (smem > 48 * 1024) {
+      cudaError_t e = cudaFuncSetAttribute(unfolded_forward_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                           (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    unfolded_forward_kernel<NB><<<(unsigned)blocks, 128, smem, st>>>(batch, N, Tt, D, inv_norm, alpha_t, t_max, c,
+                                                                     ckpt, soft, s_hat);
+  } else {
+    const size_t smem = (size_t)C::WARPS * (c + 2) * C::MAT * sizeof(float);
+    if (smem > 227 * 1024) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(unfolded_backward_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    unfolded_backward_kernel<NB><<<(unsigned)blocks, 128, smem, st>>>(batch, N, Tt, D, inv_norm, alpha_t, t_max, c,
+                                                                      ckpt, grad_soft, grad_tau);
+  }
+  return cudaGetLastError();
+}
+
+// Shared memory the backward kernel needs for checkpoint spacing c at size N (bytes).
+size_t unfolded_backward_smem(int N, int c) {
+  const int NB = bucket_of(N);
+  return (size_t)4 * (c + 2) * (NB + 1) * (NB + 4) * sizeof(float);
+}
+
+cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,
+                     const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
+                     const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st) {
+  cudaError_t e;
+  switch (bucket_of(N)) {
+    case 8:
+      e = launch_unfolded<8>(backward, batch, N, Tt, D, inv_norm, alpha_t, t_max, c, ckpt, soft, s_hat, grad_soft,
+                             grad_tau, st);
+      break;
+    case 16:
+      e = launch_unfolded<16>(backward, batch, N, Tt, D, inv_norm, alpha_t, t_max, c, ckpt, soft, s_hat, grad_soft,
+                              grad_tau, st);
+      break;
+    case 32:
+      e = launch_unfolded<32>(backward, batch, N, Tt, D, inv_norm, alpha_t, t_max, c, ckpt, soft, s_hat, grad_soft,
+                              grad_tau, st);
+      break;
+    default:
+      return cudaErrorNotSupported;
+  }
+  if (e != cudaSuccess || !backward || grad_alpha == nullptr) return e;
+  reduce_alpha_kernel<<<t_max, 256, 0, st>>>(batch, t_max, grad_tau, inv_norm, grad_alpha);
+  return cudaGetLastError();
+}
+
+}  // namespace taser

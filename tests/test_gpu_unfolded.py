@@ -1,0 +1,118 @@
+"""Unfolded TASER on the GPU (learnable per-iteration steps): forward, checkpoints and the
+hand-written adjoint against the FP64 oracle (whose adjoint is pinned by finite
+differences and the dot-product test on the CPU).
+
+Tolerances: soft outputs and checkpoints within 1e-5 (FP32 iterations, as for the
+detector); dloss/dtau_t within 2e-3 of the largest entry per instance (the adjoint chains
+t_max FP32 steps of prox Jacobians); dloss/dalpha_t within 1e-5 relative of the FP64 sum
+of the GPU's own per-instance gradients.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import taser_oracle as O
+from synth import make_mimo
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_01797_gb300 as taser
+    return taser
+
+
+def setup(n, B, U, const, t_max, seed):
+    w = make_mimo(n, B, U, np.linspace(2.0, 14.0, n), const, seed=seed)
+    kind = "mimo_" + const
+    r = O.detect(kind, w["H"], w["y"], 0.5, 1)
+    Tt = r["T_tilde"].astype(np.float32)
+    D = r["D"].astype(np.float32)
+    inv = (1.0 / O.spectral_norm(r["T_tilde"])).astype(np.float32)
+    rng = np.random.default_rng(seed)
+    alpha = rng.uniform(0.3, 0.7, size=t_max).astype(np.float32)
+    truth = w["bits_re"] if const == "bpsk" else np.concatenate([w["bits_re"], w["bits_im"]], 1)
+    return Tt, D, inv, alpha, truth.astype(np.float64)
+
+
+def dev(*a):
+    return [torch.from_numpy(np.ascontiguousarray(x)).cuda() for x in a]
+
+
+CASES = [(96, 32, 4, "qpsk", 10, 4), (64, 16, 16, "bpsk", 7, 3), (128, 128, 16, "qpsk", 10, 4),
+         (40, 24, 8, "qpsk", 20, 5), (33, 12, 5, "bpsk", 5, 5)]
+
+
+@pytest.mark.parametrize("n,B,U,const,t_max,c", CASES)
+def test_unfolded_forward_and_checkpoints(T, n, B, U, const, t_max, c):
+    Tt, D, inv, alpha, _ = setup(n, B, U, const, t_max, seed=U)
+    tau_t = alpha[None, :].astype(np.float64) * inv[:, None].astype(np.float64)
+    L, Ls = O.unfolded_forward(Tt.astype(np.float64), D.astype(np.float64), tau_t)
+    soft_o = O.soft_output(L, D.astype(np.float64))
+    soft, s_hat, ckpt = T.unfolded_forward(*dev(Tt, D, inv, alpha), c)
+    torch.cuda.synchronize()
+    assert np.abs(soft.cpu().numpy() - soft_o).max() <= 1e-5
+    np.testing.assert_array_equal(s_hat.cpu().numpy(), np.where(L[:, -1, :-1] >= 0, 1, -1)[:, :])
+    ck = ckpt.cpu().numpy().astype(np.float64)
+    for k in range(ck.shape[1]):
+        ref = Ls[k * c]
+        err = np.linalg.norm(ck[:, k] - ref, axis=(1, 2)) / np.linalg.norm(ref, axis=(1, 2))
+        assert err.max() <= 1e-5, (k, err.max())
+
+
+@pytest.mark.parametrize("n,B,U,const,t_max,c", CASES)
+def test_unfolded_backward_matches_oracle(T, n, B, U, const, t_max, c):
+    Tt, D, inv, alpha, truth = setup(n, B, U, const, t_max, seed=100 + U)
+    dT, dD, dinv, dalpha = dev(Tt, D, inv, alpha)
+    soft, _, ckpt = T.unfolded_forward(dT, dD, dinv, dalpha, c)
+    x = soft.cpu().numpy().astype(np.float64)
+    g_soft = (2.0 * (x - truth) / x.size).astype(np.float32)       # MSE loss gradient
+    grad_tau, grad_alpha = T.unfolded_backward(dT, dD, dinv, dalpha, c, ckpt, dev(g_soft)[0])
+    torch.cuda.synchronize()
+    tau_t = alpha[None, :].astype(np.float64) * inv[:, None].astype(np.float64)
+    _, Ls = O.unfolded_forward(Tt.astype(np.float64), D.astype(np.float64), tau_t)
+    g_o = O.unfolded_backward(Tt.astype(np.float64), D.astype(np.float64), tau_t, Ls, g_soft.astype(np.float64))
+    g = grad_tau.cpu().numpy().astype(np.float64)
+    scale = np.abs(g_o).max(axis=1, keepdims=True) + 1e-30
+    assert (np.abs(g - g_o) / scale).max() <= 2e-3, (np.abs(g - g_o) / scale).max()
+    ga = (g * inv[:, None].astype(np.float64)).sum(axis=0)
+    np.testing.assert_allclose(grad_alpha.cpu().numpy(), ga, rtol=1e-5, atol=1e-7 * np.abs(ga).max())
+
+
+def test_checkpoint_spacing_does_not_change_the_gradient(T):
+    Tt, D, inv, alpha, truth = setup(72, 64, 8, "qpsk", 12, seed=5)
+    dT, dD, dinv, dalpha = dev(Tt, D, inv, alpha)
+    g_soft = dev((np.random.default_rng(1).standard_normal((72, 16)) * 1e-3).astype(np.float32))[0]
+    ref = None
+    for c in (1, 3, 4, 12):
+        soft, _, ckpt = T.unfolded_forward(dT, dD, dinv, dalpha, c)
+        gt, _ = T.unfolded_backward(dT, dD, dinv, dalpha, c, ckpt, g_soft)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = gt.clone()
+        assert torch.equal(gt, ref), c
+
+
+def test_unfolded_training_lowers_the_loss(T):
+    """A few Adam steps on alpha_t with fresh seeded QPSK 128x16 batches (N = 33,
+    t_max = 10, c = 4) lower the MSE between the soft last row and the symbols."""
+    t_max, c = 10, 4
+    alpha = torch.full((t_max,), 0.5, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([alpha], lr=0.05)
+    losses = []
+    for step in range(12):
+        w = make_mimo(1024, 128, 16, np.random.default_rng(step).uniform(4, 14, 1024), "qpsk", seed=700 + step)
+        out = T.build_T("mimo_qpsk", *dev(w["H"], w["y"]), alpha=0.5)
+        inv = 1.0 / out["spec_norm"]
+        truth = dev(np.concatenate([w["bits_re"], w["bits_im"]], 1).astype(np.float32))[0]
+        soft = T.UnfoldedTASER.apply(alpha, out["T_tilde"], out["D"], inv, c)
+        loss = torch.mean((soft - truth) ** 2)
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert alpha.grad is not None and torch.isfinite(alpha.grad).all()
+    assert np.mean(losses[-3:]) < losses[0]
