@@ -68,6 +68,8 @@ typedef enum {
 #define TASER_FLAG_ZERO_COLUMN (1u << 2) /* a column of V had zero norm in the prox      */
 #define TASER_FLAG_LNN_SIGN    (1u << 3) /* V_NN <= 0 was seen in some iteration         */
 
+#define TASER_FLAG_BAD_ITEM    (1u << 4) /* uneven batch: item with N or t_max out of range */
+
 /* Largest N supported by the detection kernels. */
 #define TASER_MAX_N 65
 
@@ -212,6 +214,50 @@ taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde,
                                      const float* inv_norm, const float* alpha_t, int t_max, int c,
                                      const float* ckpt, const float* grad_soft, float* grad_tau,
                                      float* grad_alpha, void* stream);
+
+/*
+ * Uneven batches.  One item per detection problem; the items share pooled buffers.
+ */
+typedef struct {
+    int32_t N;       /* problem size, 2..65 */
+    int32_t t_max;   /* iterations, >= 1 */
+    int64_t t_off;   /* offset (in floats) of the item's T~ (N x N) in T_pool */
+    int64_t d_off;   /* offset (in floats) of its D (N) in D_pool */
+    int64_t s_off;   /* offset (in bytes) of its decisions (N - 1) in s_pool */
+    int64_t l_off;   /* offset (in floats) of its L~ (N x N) in L_pool, or -1 for none */
+} taser_item;
+
+/* Per-bucket launch tuning of taser_detect_uneven (buckets N <= 9, 17, 33, 65). */
+typedef struct {
+    int32_t blocks_per_sm[4];   /* persistent blocks per SM, 0 = as many as fit */
+    int32_t pop[4];             /* items a warp takes per queue pop, 0 = 1 */
+} taser_uneven_tuning;
+
+/* Device workspace (bytes) taser_detect_uneven needs for n_items items. */
+size_t taser_uneven_workspace_bytes(int64_t n_items);
+
+/*
+ * taser_detect_uneven -- Algorithm 1 on a batch of problems of different sizes and
+ * iteration counts (N = 2..65, any t_max >= 1 per item), in one stream-ordered sequence
+ * without host synchronisation (capturable in a CUDA graph and replayed with one launch):
+ * a counting-sort kernel builds a size-bucketed work queue in `workspace` (items grouped
+ * by bucket N <= 9 / 17 / 33 / 65, then by t_max), and one persistent kernel per bucket
+ * pulls items from its queue with an atomic counter.  Precisions as in taser_detect
+ * (tensor cores for 10 <= N <= 33, FP32 otherwise).
+ *   items     device array of n_items taser_item.
+ *   T_pool, D_pool, tau (float [n_items]), L_pool (may be NULL), s_pool: device pools
+ *             addressed by the items' offsets.
+ *   flags     uint32 [n_items] or NULL: OR-ed flag bits; items with N or t_max out of range
+ *             are skipped and get TASER_FLAG_BAD_ITEM.
+ *   workspace device buffer of taser_uneven_workspace_bytes(n_items) bytes, 256-byte aligned.
+ *   tuning    per-bucket launch parameters (from the autotuner), or NULL for defaults.
+ * Items are independent: their results do not depend on the queue order.
+ */
+taser_status taser_detect_uneven(int64_t n_items, const taser_item* items, const float* T_pool,
+                                 const float* D_pool, const float* tau, int precision,
+                                 int lnn_mode, float* L_pool, int8_t* s_pool, uint32_t* flags,
+                                 void* workspace, size_t workspace_bytes,
+                                 const taser_uneven_tuning* tuning, void* stream);
 
 /*
  * taser_run_host_static -- taser_run_host without a caller-provided workspace.

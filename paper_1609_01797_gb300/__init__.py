@@ -5,4 +5,5 @@ C ABI declared in include/taser.h; every step of the detector runs in CUDA kerne
 """
 from .api import (BPSK, GENERIC, JED_BPSK, QPSK, PRECISIONS, build_T, detect, problem_size,  # noqa: F401
                   step_size, host_workspace_bytes, run_host, run_host_static,
-                  unfolded_forward, unfolded_backward, UnfoldedTASER)
+                  unfolded_forward, unfolded_backward, UnfoldedTASER, ITEM_DTYPE, make_items,
+                  uneven_workspace_bytes, tuning, detect_uneven)

@@ -23,7 +23,15 @@ SIGNATURES = {
     "taser_unfolded_forward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
     "taser_unfolded_backward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp,
                                          _vp]),
+    "taser_uneven_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
+    "taser_detect_uneven": (_c_i32, [_c_i64, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
+                                     _vp, _vp]),
 }
+
+
+class UnevenTuning(ctypes.Structure):
+    """taser_uneven_tuning of include/taser.h."""
+    _fields_ = [("blocks_per_sm", ctypes.c_int32 * 4), ("pop", ctypes.c_int32 * 4)]
 
 # Capacity of the library's static device scratch (include/taser.h).
 STATIC_SCRATCH_BYTES = 64 << 20

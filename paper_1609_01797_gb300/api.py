@@ -3,7 +3,9 @@ import ctypes
 
 import torch
 
-from ._native import check, lib
+import numpy as np
+
+from ._native import UnevenTuning, check, lib
 
 BPSK, QPSK, JED_BPSK = 0, 1, 2
 KINDS = {"mimo_bpsk": BPSK, "mimo_qpsk": QPSK, "jed_bpsk": JED_BPSK, BPSK: BPSK, QPSK: QPSK,
@@ -177,3 +179,46 @@ class UnfoldedTASER(torch.autograd.Function):
         a, T_tilde, D, inv_norm, ckpt = ctx.saved_tensors
         _, grad_alpha = unfolded_backward(T_tilde, D, inv_norm, a, ctx.c, ckpt, grad_soft)
         return grad_alpha, None, None, None, None
+
+
+# taser_item of include/taser.h (40 bytes, naturally aligned).
+ITEM_DTYPE = np.dtype([("N", "<i4"), ("t_max", "<i4"), ("t_off", "<i8"), ("d_off", "<i8"), ("s_off", "<i8"),
+                       ("l_off", "<i8")])
+
+
+def make_items(N, t_max, t_off, d_off, s_off, l_off=None):
+    """Host array of taser_item from per-item arrays (l_off None -> no L output)."""
+    n = len(N)
+    it = np.zeros(n, dtype=ITEM_DTYPE)
+    it["N"], it["t_max"], it["t_off"], it["d_off"], it["s_off"] = N, t_max, t_off, d_off, s_off
+    it["l_off"] = -1 if l_off is None else l_off
+    return it
+
+
+def uneven_workspace_bytes(n_items):
+    return int(lib().taser_uneven_workspace_bytes(int(n_items)))
+
+
+def tuning(blocks_per_sm=(0, 0, 0, 0), pop=(1, 1, 1, 1)):
+    t = UnevenTuning()
+    for b in range(4):
+        t.blocks_per_sm[b] = int(blocks_per_sm[b])
+        t.pop[b] = int(pop[b])
+    return t
+
+
+def detect_uneven(items, T_pool, D_pool, tau, s_pool, workspace, precision="fp32", lnn_mode="fixed", L_pool=None,
+                  flags=None, tune=None, stream=None):
+    """Algorithm 1 on an uneven batch.  `items` is a CUDA uint8 tensor holding taser_item
+    records (see make_items); pools are CUDA tensors addressed by the items' offsets."""
+    n = items.numel() // ITEM_DTYPE.itemsize
+    _dev(items, torch.uint8, "items")
+    for name, t in (("T_pool", T_pool), ("D_pool", D_pool), ("tau", tau)):
+        _dev(t, torch.float32, name)
+    _dev(s_pool, torch.int8, "s_pool")
+    _dev(workspace, torch.uint8, "workspace")
+    st = lib().taser_detect_uneven(n, _ptr(items), _ptr(T_pool), _ptr(D_pool), _ptr(tau), PRECISIONS[precision],
+                                   LNN_MODES[lnn_mode], _ptr(L_pool), _ptr(s_pool), _ptr(flags), _ptr(workspace),
+                                   workspace.numel(), ctypes.byref(tune) if tune is not None else None,
+                                   _stream(stream))
+    check(st, "taser_detect_uneven")

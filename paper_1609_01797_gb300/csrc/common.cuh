@@ -25,6 +25,58 @@ __device__ __forceinline__ int bucket_to_real(int i, int N, int NB) {
   return i < N - 1 ? i : (i == NB ? N - 1 : -1);
 }
 
+// One detection problem as the iteration kernels see it.
+struct Job {
+  const float* T;      // T~, N x N row-major
+  const float* D;      // D, N
+  const float* tau;    // step size (one float)
+  float* L;            // L~ output (N x N) or nullptr
+  int8_t* s;           // decisions (N - 1)
+  uint32_t* flag;      // flag word or nullptr
+  int N;
+  int t_max;
+};
+
+__device__ __forceinline__ Job dense_job(int64_t inst, int N, int t_max, const float* Tt, const float* Dg,
+                                         const float* tau, float* L, int8_t* s, uint32_t* flags) {
+  Job j;
+  j.T = Tt + inst * (int64_t)N * N;
+  j.D = Dg + inst * (int64_t)N;
+  j.tau = tau + inst;
+  j.L = L != nullptr ? L + inst * (int64_t)N * N : nullptr;
+  j.s = s + inst * (int64_t)(N - 1);
+  j.flag = flags != nullptr ? flags + inst : nullptr;
+  j.N = N;
+  j.t_max = t_max;
+  return j;
+}
+
+__device__ __forceinline__ Job item_job(const taser_item& it, int64_t idx, const float* T_pool, const float* D_pool,
+                                        const float* tau, float* L_pool, int8_t* s_pool, uint32_t* flags) {
+  Job j;
+  j.T = T_pool + it.t_off;
+  j.D = D_pool + it.d_off;
+  j.tau = tau + idx;
+  j.L = (L_pool != nullptr && it.l_off >= 0) ? L_pool + it.l_off : nullptr;
+  j.s = s_pool + it.s_off;
+  j.flag = flags != nullptr ? flags + idx : nullptr;
+  j.N = it.N;
+  j.t_max = it.t_max;
+  return j;
+}
+
+// Work queue of one size bucket, filled on the device: item indices
+// list[meta[b] .. meta[b] + meta[4 + b]), popped through the atomic counter meta[8 + b].
+struct Queue {
+  const taser_item* items;
+  const int* list;
+  int* meta;
+  int b;
+  __device__ __forceinline__ int count() const { return *((volatile const int*)meta + 4 + b); }
+  __device__ __forceinline__ int pop(int k) const { return atomicAdd(meta + 8 + b, k); }
+  __device__ __forceinline__ int item_at(int pos) const { return list[meta[b] + pos]; }
+};
+
 __device__ __forceinline__ float warp_sum(float v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(TASER_FULL_MASK, v, o);

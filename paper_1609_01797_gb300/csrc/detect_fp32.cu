@@ -7,6 +7,10 @@
 // Buckets: NB = 8 / 16 -> 4 / 2 instances per warp, NB = 32 -> one instance per warp,
 // NB = 64 -> two warps per instance (the second warp skips rows < 32, all above its
 // columns).  L~ never leaves the SM between iterations.
+//
+// The per-instance body (fp32_run) serves the dense kernel (instances at a fixed stride)
+// and the queue-fed persistent kernel of uneven batches; the instances sharing a warp
+// may have different t_max, so each emits its outputs at its own last iteration.
 #include "common.cuh"
 
 namespace taser {
@@ -32,32 +36,19 @@ __device__ __forceinline__ void sync_instance(int bar_id) {
   }
 }
 
-template <int NB>
-__global__ void __launch_bounds__(128)
-detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
-                   const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
-                   int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags) {
+// Runs Algorithm 1 for `jb` (inactive lanes compute on zeros and write nothing).
+// t_loop: iterations the warp executes (the largest t_max among its instances).  MIXED:
+// instances sharing the warp may have different t_max, so outputs are emitted inside the
+// loop at each instance's own last iteration; otherwise once after the loop.
+template <int NB, bool MIXED>
+__device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop, float* Ls, float* xs, int j,
+                                         int lane, int warp, int bar_id, int literal) {
   using C = Fp32Cfg<NB>;
-  extern __shared__ __align__(16) float smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  int local_inst, j;
-  if constexpr (NB <= 32) {
-    local_inst = warp * C::IPW + lane / C::G;
-    j = lane % C::G;
-  } else {
-    local_inst = warp / C::WPI;
-    j = (warp % C::WPI) * 32 + lane;
-  }
   const int colbase = NB > 32 ? (warp % C::WPI) * 32 : 0;  // warp-uniform
-  const int64_t inst = (int64_t)blockIdx.x * C::IPC + local_inst;
-  const bool active = inst < batch;
-  float* Ls = smem + local_inst * C::INST_FLOATS;
-  float* xs = Ls + (NB + 1) * C::S;                         // cross-warp partial sums
-  const int bar_id = 1 + local_inst;
-
-  const int jr = j < N - 1 ? j : -1;                        // real column (variable)
-  const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
-  const float tau = active ? tau_g[inst] : 0.f;
+  const unsigned gmask = C::G == 32 ? TASER_FULL_MASK : (((1u << C::G) - 1u) << ((lane / C::G) * C::G));
+  const int N = active ? jb.N : NB + 1;
+  const int jr = j < N - 1 ? j : -1;                         // real column (variable)
+  const float tau = active ? *jb.tau : 0.f;
   const float m2tau = -2.f * tau;
 
   // Column j of T^ = -2 tau T~ (T~ symmetric: T~[k][j] read row by row, coalesced).
@@ -66,12 +57,12 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
   for (int k = 0; k <= NB; ++k) {
     const int kr = bucket_to_real(k, N, NB);
     float v = 0.f;
-    if (active && jr >= 0 && kr >= 0) v = T[(int64_t)kr * N + jr];
+    if (active && jr >= 0 && kr >= 0) v = jb.T[(int64_t)kr * N + jr];
     tn[k] = m2tau * v;
   }
-  const float Dj = (active && jr >= 0) ? Dg[inst * N + jr] : 0.f;
-  const float DN = active ? Dg[inst * N + N - 1] : 0.f;
-  const float tnNN = m2tau * (active ? T[(int64_t)(N - 1) * N + (N - 1)] : 0.f);
+  const float Dj = (active && jr >= 0) ? jb.D[jr] : 0.f;
+  const float DN = active ? jb.D[N - 1] : 0.f;
+  const float tnNN = m2tau * (active ? jb.T[(int64_t)(N - 1) * N + (N - 1)] : 0.f);
 
   // L~(0) = D (Algorithm 1 initialisation).
   for (int idx = j; idx < C::INST_FLOATS; idx += (NB <= 32 ? C::G : 64)) Ls[idx] = 0.f;
@@ -85,7 +76,36 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
   uint32_t fl = 0;
   sync_instance<NB>(bar_id);
 
-  for (int t = 0; t < t_max; ++t) {
+  // Outputs of this instance (its lanes call this together).
+  auto emit = [&]() {
+    uint32_t f = fl;
+    if constexpr (NB <= 32) {
+#pragma unroll
+      for (int o = C::G / 2; o > 0; o >>= 1) f |= __shfl_xor_sync(gmask, f, o);
+      if (j == 0 && jb.flag != nullptr && f) *jb.flag |= f;
+    } else {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) f |= __shfl_xor_sync(TASER_FULL_MASK, f, o);
+      if (lane == 0 && jb.flag != nullptr && f) atomicOr(jb.flag, f);
+    }
+    // Decisions s_k = sign(L~_{N,k}) (sign(0) = +1), times sign(L~_NN) in literal mode.
+    if (jr >= 0) {
+      float r = l[NB];
+      if (literal && LNN < 0.f) r = -r;
+      jb.s[jr] = (r >= 0.f) ? int8_t(1) : int8_t(-1);
+    }
+    if (jb.L != nullptr) {
+#pragma unroll
+      for (int i = 0; i <= NB; ++i) {
+        const int ir = bucket_to_real(i, N, NB);
+        if (ir < 0) continue;
+        if (jr >= 0) jb.L[(int64_t)ir * N + jr] = l[i];
+        if (j == 0) jb.L[(int64_t)ir * N + (N - 1)] = (ir == N - 1) ? LNN : 0.f;
+      }
+    }
+  };
+
+  for (int t = 0; t < t_loop; ++t) {
     // Partial of V_NN = L~_NN (1 - 2 tau T~_NN) - 2 tau sum_k L~_Nk T~_kN from L~(t-1).
     float part = l[NB] * tn[NB];
 #pragma unroll
@@ -140,39 +160,83 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
     }
     if (literal && j == 0) Ls[NB * C::S + NB] = LNN;
     sync_instance<NB>(bar_id);
-  }
 
-  // OR the flags of the instance's lanes (all lanes still present for the shuffles).
+    if constexpr (MIXED) {
+      if (t + 1 == (active ? jb.t_max : -1)) emit();
+    }
+  }
+  if constexpr (!MIXED) {
+    if (active) emit();
+  }
+}
+
+template <int NB>
+__device__ __forceinline__ void fp32_lane_layout(int warp, int lane, int& local_inst, int& j) {
+  using C = Fp32Cfg<NB>;
   if constexpr (NB <= 32) {
-#pragma unroll
-    for (int o = C::G / 2; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
+    local_inst = warp * C::IPW + lane / C::G;
+    j = lane % C::G;
   } else {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
+    local_inst = warp / C::WPI;
+    j = (warp % C::WPI) * 32 + lane;
   }
-  if (!active) return;
-  if (flags != nullptr && fl) {
+}
+
+template <int NB>
+__global__ void __launch_bounds__(128, NB == 32 ? 4 : 1)
+detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
+                   const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
+                   int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags) {
+  using C = Fp32Cfg<NB>;
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int local_inst, j;
+  fp32_lane_layout<NB>(warp, lane, local_inst, j);
+  const int64_t inst = (int64_t)blockIdx.x * C::IPC + local_inst;
+  const bool active = inst < batch;
+  float* Ls = smem + local_inst * C::INST_FLOATS;
+  const Job jb = dense_job(active ? inst : 0, N, t_max, Tt, Dg, tau_g, Lout, s_hat, flags);
+  fp32_run<NB, false>(jb, active, t_max, Ls, Ls + (NB + 1) * C::S, j, lane, warp, 1 + local_inst, literal);
+}
+
+// Persistent, queue-fed: each warp (each warp pair for NB = 64) pops the next items of
+// its bucket until the queue is empty.
+template <int NB>
+__global__ void __launch_bounds__(128, NB == 32 ? 4 : 1)
+detect_fp32_queue_kernel(Queue q, const float* __restrict__ T_pool, const float* __restrict__ D_pool,
+                         const float* __restrict__ tau, int literal, float* __restrict__ L_pool,
+                         int8_t* __restrict__ s_pool, uint32_t* __restrict__ flags) {
+  using C = Fp32Cfg<NB>;
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int local_inst, j;
+  fp32_lane_layout<NB>(warp, lane, local_inst, j);
+  float* Ls = smem + local_inst * C::INST_FLOATS;
+  float* xs = Ls + (NB + 1) * C::S;
+  int* pop_slot = reinterpret_cast<int*>(xs + 2);
+  const int count = q.count();
+  for (;;) {
+    int base;
     if constexpr (NB <= 32) {
-      if (j == 0) flags[inst] |= fl;
+      base = 0;
+      if (lane == 0) base = q.pop(C::IPW);
+      base = __shfl_sync(TASER_FULL_MASK, base, 0);
     } else {
-      if (lane == 0) atomicOr(&flags[inst], fl);
+      if ((warp % C::WPI) == 0 && lane == 0) *pop_slot = q.pop(1);
+      sync_instance<NB>(1 + local_inst);
+      base = *pop_slot;
+      sync_instance<NB>(1 + local_inst);
     }
-  }
-  // Decisions s_k = sign(L~_{N,k}) (sign(0) = +1), times sign(L~_NN) in literal mode.
-  if (jr >= 0) {
-    float r = l[NB];
-    if (literal && LNN < 0.f) r = -r;
-    s_hat[inst * (N - 1) + jr] = (r >= 0.f) ? int8_t(1) : int8_t(-1);
-  }
-  if (Lout != nullptr) {
-    float* Lo = Lout + inst * (int64_t)N * N;
-#pragma unroll
-    for (int i = 0; i <= NB; ++i) {
-      const int ir = bucket_to_real(i, N, NB);
-      if (ir < 0) continue;
-      if (jr >= 0) Lo[(int64_t)ir * N + jr] = l[i];
-      if (j == 0) Lo[(int64_t)ir * N + (N - 1)] = (ir == N - 1) ? LNN : 0.f;
-    }
+    if (base >= count) break;                                   // uniform per warp (pair)
+    const int pos = NB <= 32 ? base + (lane / C::G) : base;
+    const bool active = pos < count;
+    const int idx = active ? q.item_at(pos) : 0;
+    const taser_item it = q.items[idx];
+    const Job jb = item_job(it, idx, T_pool, D_pool, tau, L_pool, s_pool, flags);
+    int t_loop = active ? jb.t_max : 0;
+    if constexpr (NB <= 32) t_loop = __reduce_max_sync(TASER_FULL_MASK, t_loop);
+    fp32_run<NB, (Fp32Cfg<NB>::IPW > 1)>(jb, active, t_loop, Ls, xs, j, lane, warp, 1 + local_inst, literal);
+    sync_instance<NB>(1 + local_inst);
   }
 }
 
@@ -199,6 +263,40 @@ cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, c
     case 16: return launch_fp32<16>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
     case 32: return launch_fp32<32>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
     default: return launch_fp32<64>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
+  }
+}
+
+// Queue-fed launch for bucket NB with `blocks` persistent blocks.
+template <int NB>
+static cudaError_t launch_fp32_queue(const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
+                                     const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
+                                     cudaStream_t st) {
+  using C = Fp32Cfg<NB>;
+  const size_t smem = C::SMEM_BYTES;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(detect_fp32_queue_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  int dev = 0, sms = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_fp32_queue_kernel<NB>, 128, smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
+  detect_fp32_queue_kernel<NB><<<sms * per_sm, 128, smem, st>>>(q, T_pool, D_pool, tau, literal, L_pool, s_pool,
+                                                               flags);
+  return cudaGetLastError();
+}
+
+cudaError_t detect_fp32_queue(int nb, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
+                              const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
+                              cudaStream_t st) {
+  switch (nb) {
+    case 8: return launch_fp32_queue<8>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    case 16: return launch_fp32_queue<16>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    case 32: return launch_fp32_queue<32>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    default: return launch_fp32_queue<64>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
   }
 }
 

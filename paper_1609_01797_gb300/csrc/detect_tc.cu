@@ -67,37 +67,94 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
-// Stage T~ (N x N), D (N) and tau of one instance into the warp's shared slot.
-__device__ __forceinline__ void stage_instance(float* slot, const float* Tt, const float* Dg, const float* tau_g,
-                                               int64_t inst, int N, int lane) {
-  const int nn = N * N;
-  const float* T = Tt + inst * (int64_t)nn;
-  for (int i = lane; i < nn; i += 32) cp_async4(slot + i, T + i);
-  for (int i = lane; i < N; i += 32) cp_async4(slot + nn + i, Dg + inst * (int64_t)N + i);
-  if (lane == 0) cp_async4(slot + nn + N, tau_g + inst);
+// Stage T~ (N x N), D (N) and tau of one job into the warp's shared slot.
+__device__ __forceinline__ void stage_job(float* slot, const Job& jb, int lane) {
+  const int N = jb.N, nn = N * N;
+  for (int i = lane; i < nn; i += 32) cp_async4(slot + i, jb.T + i);
+  for (int i = lane; i < N; i += 32) cp_async4(slot + nn + i, jb.D + i);
+  if (lane == 0) cp_async4(slot + nn + N, jb.tau);
   asm volatile("cp.async.commit_group;" ::: "memory");
 }
 
-// Persistent: each warp walks instances inst, inst + stride, ... and prefetches the next
-// instance's inputs with cp.async while it iterates on the current one.
-template <int NB, bool FP16>
+// Instances at a fixed stride (the dense batch of taser_detect).
+struct DenseSource {
+  int64_t batch, stride;
+  int N, t_max;
+  const float *Tt, *Dg, *tau;
+  float* L;
+  int8_t* s;
+  uint32_t* flags;
+  __device__ __forceinline__ bool get(int64_t k, Job& jb) const {  // k-th instance of this warp
+    const int64_t inst = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5) + k * stride;
+    if (inst >= batch) return false;
+    jb = dense_job(inst, N, t_max, Tt, Dg, tau, L, s, flags);
+    return true;
+  }
+};
+
+// Items of one bucket's queue, popped `pop` at a time per warp.
+struct QueueSource {
+  Queue q;
+  int pop;
+  const float *T_pool, *D_pool, *tau;
+  float* L_pool;
+  int8_t* s_pool;
+  uint32_t* flags;
+};
+
+template <class Src>
+struct Cursor;
+
+template <>
+struct Cursor<DenseSource> {
+  int64_t k = 0;
+  __device__ __forceinline__ bool next(const DenseSource& src, Job& jb, int) { return src.get(k++, jb); }
+};
+
+template <>
+struct Cursor<QueueSource> {
+  int base = 0, left = 0;
+  __device__ __forceinline__ bool next(const QueueSource& src, Job& jb, int lane) {
+    if (left == 0) {
+      int b = 0;
+      if (lane == 0) b = src.q.pop(src.pop);
+      base = __shfl_sync(TASER_FULL_MASK, b, 0);
+      left = src.pop;
+    }
+    const int pos = base++;
+    --left;
+    if (pos >= src.q.count()) {
+      left = 0;
+      base = 1 << 30;
+      return false;
+    }
+    const int idx = src.q.item_at(pos);
+    const taser_item it = src.q.items[idx];
+    jb = item_job(it, idx, src.T_pool, src.D_pool, src.tau, src.L_pool, src.s_pool, src.flags);
+    return true;
+  }
+};
+
+// Persistent: each warp takes jobs from its source (a fixed stride, or a bucket queue) and
+// prefetches the next job's inputs with cp.async while it iterates on the current one.
+template <int NB, bool FP16, class Src>
 __global__ void __launch_bounds__(128, 4)
-detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
-                 const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
-                 int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags, int slot_floats) {
+detect_tc_kernel(Src src, int literal, int slot_floats) {
   using C = TcCfg<NB>;
   constexpr int KT = C::KT, NT = C::NT, MT = C::MT;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
   float* slot = smem + warp * slot_floats;
-  const int64_t stride = (int64_t)gridDim.x * C::WARPS;
-  int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
-  if (inst < batch) stage_instance(slot, Tt, Dg, tau_g, inst, N, lane);
+  Cursor<Src> cursor;
+  Job cur;
+  bool have = cursor.next(src, cur, lane);
+  if (have) stage_job(slot, cur, lane);
 
-  for (; inst < batch; inst += stride) {
+  while (have) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
+    const int N = cur.N, t_max = cur.t_max;
     const float* T = slot;
     const float* Di = slot + N * N;
     const float m2tau = -2.f * slot[N * N + N];
@@ -142,10 +199,9 @@ detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float
           acc[M][n][e] = (M < MT - 1 && r == c && r < N - 1) ? Di[r] : 0.f;
         }
     __syncwarp();  // every lane has read the slot
-    {
-      const int64_t next = inst + stride;
-      if (next < batch) stage_instance(slot, Tt, Dg, tau_g, next, N, lane);
-    }
+    Job nxt;
+    const bool have_next = cursor.next(src, nxt, lane);
+    if (have_next) stage_job(slot, nxt, lane);
     float LNN = DN;
     uint32_t fl = 0;
 
@@ -265,7 +321,7 @@ detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float
 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
-    if (lane == 0 && flags != nullptr && fl) flags[inst] |= fl;
+    if (lane == 0 && cur.flag != nullptr && fl) *cur.flag |= fl;
 
     // Decisions from row N (lanes g == 0).
     if (g == 0) {
@@ -277,12 +333,12 @@ detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float
           if (c < N - 1) {
             float r = acc[MT - 1][n][p];
             if (literal && LNN < 0.f) r = -r;
-            s_hat[inst * (N - 1) + c] = r >= 0.f ? int8_t(1) : int8_t(-1);
+            cur.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
           }
         }
     }
-    if (Lout != nullptr) {
-      float* Lo = Lout + inst * (int64_t)N * N;
+    if (cur.L != nullptr) {
+      float* Lo = cur.L;
 #pragma unroll
       for (int M = 0; M < MT; ++M)
 #pragma unroll
@@ -297,7 +353,28 @@ detect_tc_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float
           }
       for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
     }
+    cur = nxt;
+    have = have_next;
   }
+}
+
+template <int NB, bool FP16, class Src>
+static cudaError_t launch_tc_src(const Src& src, int64_t jobs, int blocks_per_sm, int literal, int slot_floats,
+                                 cudaStream_t st) {
+  using C = TcCfg<NB>;
+  const size_t smem = (size_t)C::WARPS * slot_floats * sizeof(float);
+  int dev = 0, sms = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, Src>, 32 * C::WARPS, smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
+  const int64_t need = (jobs + C::WARPS - 1) / C::WARPS;
+  const int64_t resident = (int64_t)sms * per_sm;
+  const int64_t blocks = jobs >= 0 && need < resident ? need : resident;
+  detect_tc_kernel<NB, FP16, Src><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(src, literal, slot_floats);
+  return cudaGetLastError();
 }
 
 template <int NB, bool FP16>
@@ -305,19 +382,27 @@ static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float*
                              int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
   using C = TcCfg<NB>;
   const int slot_floats = ((N * N + N + 1) + 3) & ~3;
-  const size_t smem = (size_t)C::WARPS * slot_floats * sizeof(float);
-  int dev = 0, sms = 0, per_sm = 0;
+  int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, detect_tc_kernel<NB, FP16>, 32 * C::WARPS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, DenseSource>, 32 * C::WARPS,
+                                                      (size_t)C::WARPS * slot_floats * sizeof(float));
   if (e != cudaSuccess) return e;
   const int64_t need = (batch + C::WARPS - 1) / C::WARPS;
-  const int64_t resident = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
-  const int64_t blocks = need < resident ? need : resident;
-  detect_tc_kernel<NB, FP16><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(batch, N, Tt, D, tau, t_max, literal, L,
-                                                                          s, flags, slot_floats);
-  return cudaGetLastError();
+  const int64_t resident = (int64_t)sms * (fit > 0 ? fit : 1);
+  DenseSource src;
+  src.batch = batch;
+  src.stride = (need < resident ? need : resident) * C::WARPS;
+  src.N = N;
+  src.t_max = t_max;
+  src.Tt = Tt;
+  src.Dg = D;
+  src.tau = tau;
+  src.L = L;
+  src.s = s;
+  src.flags = flags;
+  return launch_tc_src<NB, FP16>(src, batch, fit, literal, slot_floats, st);
 }
 
 // Returns cudaErrorNotSupported when the bucket has no tensor-core kernel.
@@ -330,6 +415,32 @@ cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, con
     case 32:
       return fp16 ? launch_tc<32, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st)
                   : launch_tc<32, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
+// Queue-fed launch for bucket nb (16 or 32) of an uneven batch.
+cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm, int pop, const float* T_pool,
+                            const float* D_pool, const float* tau, int literal, float* L_pool, int8_t* s_pool,
+                            uint32_t* flags, cudaStream_t st) {
+  QueueSource src;
+  src.q = q;
+  src.pop = pop > 0 ? pop : 1;
+  src.T_pool = T_pool;
+  src.D_pool = D_pool;
+  src.tau = tau;
+  src.L_pool = L_pool;
+  src.s_pool = s_pool;
+  src.flags = flags;
+  const int slot_floats = (((nb + 1) * (nb + 1) + (nb + 1) + 1) + 3) & ~3;
+  switch (nb) {
+    case 16:
+      return fp16 ? launch_tc_src<16, true>(src, -1, blocks_per_sm, literal, slot_floats, st)
+                  : launch_tc_src<16, false>(src, -1, blocks_per_sm, literal, slot_floats, st);
+    case 32:
+      return fp16 ? launch_tc_src<32, true>(src, -1, blocks_per_sm, literal, slot_floats, st)
+                  : launch_tc_src<32, false>(src, -1, blocks_per_sm, literal, slot_floats, st);
     default:
       return cudaErrorNotSupported;
   }

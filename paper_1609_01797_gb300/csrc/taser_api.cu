@@ -16,6 +16,10 @@ cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const
                      const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
                      const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st);
 size_t unfolded_backward_smem(int N, int c);
+size_t uneven_workspace_bytes(int64_t n_items);
+cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float* T_pool, const float* D_pool,
+                          const float* tau, int precision, int literal, float* L_pool, int8_t* s_pool,
+                          uint32_t* flags, void* workspace, const taser_uneven_tuning* tuning, cudaStream_t st);
 cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                         int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
 cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
@@ -298,6 +302,42 @@ taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde,
                                    nullptr, nullptr, grad_soft, grad_tau, grad_alpha,
                                    static_cast<cudaStream_t>(stream)),
                    "unfolded_backward");
+}
+
+}  // extern "C"
+
+extern "C" {
+
+size_t taser_uneven_workspace_bytes(int64_t n_items) {
+  if (n_items < 0 || n_items > 0x7fffffff) return 0;
+  return taser::uneven_workspace_bytes(n_items);
+}
+
+taser_status taser_detect_uneven(int64_t n_items, const taser_item* items, const float* T_pool, const float* D_pool,
+                                 const float* tau, int precision, int lnn_mode, float* L_pool, int8_t* s_pool,
+                                 uint32_t* flags, void* workspace, size_t workspace_bytes,
+                                 const taser_uneven_tuning* tuning, void* stream) {
+  TASER_REQUIRE(n_items >= 0 && n_items <= 0x7fffffff, "n_items must lie in [0, 2^31) (got %lld)",
+                (long long)n_items);
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC,
+                "unknown precision %d", precision);
+  TASER_REQUIRE(lnn_mode == TASER_LNN_FIXED || lnn_mode == TASER_LNN_LITERAL, "unknown lnn_mode %d", lnn_mode);
+  if (n_items == 0) return ok();
+  TASER_REQUIRE(items != nullptr && (reinterpret_cast<uintptr_t>(items) & 7u) == 0, "items must be 8-byte aligned");
+  TASER_REQUIRE(T_pool != nullptr && D_pool != nullptr && tau != nullptr && s_pool != nullptr,
+                "T_pool, D_pool, tau and s_pool must not be NULL");
+  TASER_REQUIRE(workspace != nullptr && (reinterpret_cast<uintptr_t>(workspace) & 255u) == 0,
+                "workspace must be a 256-byte aligned device pointer");
+  TASER_REQUIRE(workspace_bytes >= taser::uneven_workspace_bytes(n_items), "workspace too small: %zu < %zu bytes",
+                workspace_bytes, taser::uneven_workspace_bytes(n_items));
+  if (tuning != nullptr) {
+    for (int b = 0; b < 4; ++b)
+      TASER_REQUIRE(tuning->blocks_per_sm[b] >= 0 && tuning->pop[b] >= 0 && tuning->pop[b] <= 64,
+                    "tuning entry %d out of range", b);
+  }
+  return from_cuda(taser::detect_uneven(n_items, items, T_pool, D_pool, tau, precision, lnn_mode == TASER_LNN_LITERAL,
+                                        L_pool, s_pool, flags, workspace, tuning, static_cast<cudaStream_t>(stream)),
+                   "detect_uneven");
 }
 
 }  // extern "C"
