@@ -40,6 +40,8 @@ def parse_args():
     ap.add_argument("--instances", type=int, default=65536, help="instances per GPU per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=32768, help="instances timed on the CPU oracle")
+    ap.add_argument("--workload", choices=["qpsk128x16", "uneven"], default="qpsk128x16",
+                    help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20} (not the headline)")
     return ap.parse_args()
 
 
@@ -213,10 +215,99 @@ def run_reference(args):
     return 0
 
 
+def run_uneven(args):
+    """Uneven QPSK batch: taser_detect_uneven replayed from a CUDA graph vs the same work as
+    dense taser_detect calls per (shape, t_max) group (the scheduling overhead)."""
+    import torch
+    import paper_1609_01797_gb300 as taser
+    from synth import make_uneven
+    dev = torch.device("cuda", 0)
+    n = 200000
+    w = make_uneven(n, seed=3)
+    shapes = w["shapes"]
+    Ns = np.array([2 * u + 1 for _, u in shapes])[w["shape_idx"]]
+    tm = w["t_max"]
+    # T~, D, tau per shape (dense builds), pooled in shape order
+    groups, T_parts, D_parts, tau_parts = [], [], [], []
+    t_base = d_base = 0
+    t_off = np.zeros(n, np.int64)
+    d_off = np.zeros(n, np.int64)
+    for si, ps in enumerate(w["per_shape"]):
+        B_, U_ = shapes[si]
+        N_ = 2 * U_ + 1
+        out = taser.build_T("mimo_qpsk", torch.from_numpy(ps["H"]).to(dev), torch.from_numpy(ps["y"]).to(dev), ALPHA)
+        sel = ps["items"]
+        t_off[sel] = t_base + np.arange(len(sel)) * N_ * N_
+        d_off[sel] = d_base + np.arange(len(sel)) * N_
+        t_base += len(sel) * N_ * N_
+        d_base += len(sel) * N_
+        T_parts.append(out["T_tilde"].reshape(-1))
+        D_parts.append(out["D"].reshape(-1))
+        tau_parts.append((si, sel, out["tau"]))
+        groups.append((N_, sel, out))
+    T_pool = torch.cat(T_parts)
+    D_pool = torch.cat(D_parts)
+    tau = torch.empty(n, device=dev)
+    for si, sel, tv in tau_parts:
+        tau[torch.from_numpy(sel).to(dev)] = tv
+    s_off = np.concatenate([[0], np.cumsum(Ns - 1)[:-1]])
+    items = torch.from_numpy(taser.make_items(Ns, tm, t_off, d_off, s_off).view(np.uint8).copy()).to(dev)
+    s_pool = torch.empty(int((Ns - 1).sum()), dtype=torch.int8, device=dev)
+    ws = torch.empty(taser.uneven_workspace_bytes(n), dtype=torch.uint8, device=dev)
+    result = {}
+    for precision in ("bf16_tc", "fp32"):
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            taser.detect_uneven(items, T_pool, D_pool, tau, s_pool, ws, precision=precision)
+        torch.cuda.current_stream().wait_stream(side)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            taser.detect_uneven(items, T_pool, D_pool, tau, s_pool, ws, precision=precision)
+        for _ in range(args.warmup):
+            g.replay()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        un_ms = e0.elapsed_time(e1) / args.steps
+        # the same work as dense calls per (shape, t_max) group
+        dense = []
+        for N_, sel, out in groups:
+            for t in (10, 20):
+                m = torch.from_numpy(tm[sel] == t).to(dev)
+                dense.append((N_, t, out["T_tilde"][m].contiguous(), out["D"][m].contiguous(),
+                              out["tau"][m].contiguous()))
+        for _ in range(args.warmup):
+            for N_, t, Tg, Dg, tg in dense:
+                taser.detect(Tg, Dg, tg, t, precision, want_L=False)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            for N_, t, Tg, Dg, tg in dense:
+                taser.detect(Tg, Dg, tg, t, precision, want_L=False)
+        e1.record()
+        torch.cuda.synchronize()
+        dn_ms = e0.elapsed_time(e1) / args.steps
+        result[precision] = {"uneven_ms": un_ms, "dense_ms": dn_ms, "det_per_s": n / (un_ms * 1e-3),
+                             "overhead_vs_dense": un_ms / dn_ms - 1.0}
+    print(json.dumps({"metric": "TASER detections/s, uneven QPSK batch (N = 9, 17, 33, 65; t_max 10/20), "
+                                "detection only, CUDA-graph replay", "value": result["bf16_tc"]["det_per_s"],
+                      "unit": "detections/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+                      "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "config": {"workload": "uneven_qpsk_200000_N9-65_tmax10-20", "items": n}, "paths": result}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "uneven":
+        return run_uneven(args)
 
     import torch
     import torch.distributed as dist

@@ -145,16 +145,35 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
-  float* slot = smem + warp * slot_floats;
+  float* slot = smem + warp * (slot_floats + 16);
+  // Output pointers and sizes of the current and the next job live in shared memory
+  // (two records per warp), not in registers across the iteration loop.
+  struct JobOut {
+    float* L;
+    int8_t* s;
+    uint32_t* flag;
+    int N, t_max;
+  };
+  JobOut* outs = reinterpret_cast<JobOut*>(slot + slot_floats);   // 16 floats = 2 records
+  auto park = [&](const Job& jb, int which) {
+    if (lane == 0) outs[which] = JobOut{jb.L, jb.s, jb.flag, jb.N, jb.t_max};
+  };
   Cursor<Src> cursor;
-  Job cur;
-  bool have = cursor.next(src, cur, lane);
-  if (have) stage_job(slot, cur, lane);
+  int cur_m = 0;
+  bool have;
+  {
+    Job first;
+    have = cursor.next(src, first, lane);
+    if (have) {
+      stage_job(slot, first, lane);
+      park(first, 0);
+    }
+  }
 
   while (have) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
-    const int N = cur.N, t_max = cur.t_max;
+    const int N = outs[cur_m].N, t_max = outs[cur_m].t_max;
     const float* T = slot;
     const float* Di = slot + N * N;
     const float m2tau = -2.f * slot[N * N + N];
@@ -199,9 +218,15 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           acc[M][n][e] = (M < MT - 1 && r == c && r < N - 1) ? Di[r] : 0.f;
         }
     __syncwarp();  // every lane has read the slot
-    Job nxt;
-    const bool have_next = cursor.next(src, nxt, lane);
-    if (have_next) stage_job(slot, nxt, lane);
+    bool have_next;
+    {
+      Job nxt;
+      have_next = cursor.next(src, nxt, lane);
+      if (have_next) {
+        stage_job(slot, nxt, lane);
+        park(nxt, cur_m ^ 1);
+      }
+    }
     float LNN = DN;
     uint32_t fl = 0;
 
@@ -321,7 +346,8 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
-    if (lane == 0 && cur.flag != nullptr && fl) *cur.flag |= fl;
+    const JobOut o = outs[cur_m];
+    if (lane == 0 && o.flag != nullptr && fl) *o.flag |= fl;
 
     // Decisions from row N (lanes g == 0).
     if (g == 0) {
@@ -333,12 +359,12 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           if (c < N - 1) {
             float r = acc[MT - 1][n][p];
             if (literal && LNN < 0.f) r = -r;
-            cur.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
+            o.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
           }
         }
     }
-    if (cur.L != nullptr) {
-      float* Lo = cur.L;
+    if (o.L != nullptr) {
+      float* Lo = o.L;
 #pragma unroll
       for (int M = 0; M < MT; ++M)
 #pragma unroll
@@ -353,7 +379,8 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           }
       for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
     }
-    cur = nxt;
+    __syncwarp();  // the record of this job is consumed before it is reused
+    cur_m ^= 1;
     have = have_next;
   }
 }
@@ -362,7 +389,7 @@ template <int NB, bool FP16, class Src>
 static cudaError_t launch_tc_src(const Src& src, int64_t jobs, int blocks_per_sm, int literal, int slot_floats,
                                  cudaStream_t st) {
   using C = TcCfg<NB>;
-  const size_t smem = (size_t)C::WARPS * slot_floats * sizeof(float);
+  const size_t smem = (size_t)C::WARPS * (slot_floats + 16) * sizeof(float);
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -387,7 +414,7 @@ static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float*
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, DenseSource>, 32 * C::WARPS,
-                                                      (size_t)C::WARPS * slot_floats * sizeof(float));
+                                                      (size_t)C::WARPS * (slot_floats + 16) * sizeof(float));
   if (e != cudaSuccess) return e;
   const int64_t need = (batch + C::WARPS - 1) / C::WARPS;
   const int64_t resident = (int64_t)sms * (fit > 0 ? fit : 1);
