@@ -146,9 +146,8 @@ taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int str
  *   D         float [batch][N], positive scaling (D_kk of Sec. III-C).
  *   tau       float [batch], step size.
  *   t_max     iterations, >= 1.
- *   precision taser_precision.  Tensor-core precisions run for 10 <= N <= 33; outside
- *             that range the FP32 kernel runs (below it the product has no dense tile
- *             worth a tensor core; above it no tensor-core kernel is built yet).
+ *   precision taser_precision.  Tensor-core precisions run for N >= 10; below that the
+ *             FP32 kernel runs (the product has no dense tile worth a tensor core).
  *   lnn_mode  taser_lnn_mode.
  *   L         out, float [batch][N][N] = L~(t_max) with zeros above the diagonal, or NULL.
  *   s_hat     out, int8 [batch][N-1], values +1 / -1.
@@ -243,7 +242,7 @@ size_t taser_uneven_workspace_bytes(int64_t n_items);
  * a counting-sort kernel builds a size-bucketed work queue in `workspace` (items grouped
  * by bucket N <= 9 / 17 / 33 / 65, then by t_max), and one persistent kernel per bucket
  * pulls items from its queue with an atomic counter.  Precisions as in taser_detect
- * (tensor cores for 10 <= N <= 33, FP32 otherwise).
+ * (tensor cores for N >= 10, FP32 below).
  *   items     device array of n_items taser_item.
  *   T_pool, D_pool, tau (float [n_items]), L_pool (may be NULL), s_pool: device pools
  *             addressed by the items' offsets.

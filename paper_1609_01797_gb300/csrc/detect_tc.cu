@@ -432,10 +432,18 @@ static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float*
   return launch_tc_src<NB, FP16>(src, batch, fit, literal, slot_floats, st);
 }
 
+cudaError_t detect_tc64(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                        int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
+cudaError_t detect_tc64_queue(bool fp16, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
+                              const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
+                              cudaStream_t st);
+
 // Returns cudaErrorNotSupported when the bucket has no tensor-core kernel.
 cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                       int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
   switch (bucket_of(N)) {
+    case 64:
+      return detect_tc64(batch, N, Tt, D, tau, t_max, literal, fp16, L, s, flags, st);
     case 16:
       return fp16 ? launch_tc<16, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st)
                   : launch_tc<16, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
@@ -462,6 +470,8 @@ cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm
   src.flags = flags;
   const int slot_floats = (((nb + 1) * (nb + 1) + (nb + 1) + 1) + 3) & ~3;
   switch (nb) {
+    case 64:
+      return detect_tc64_queue(fp16, q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
     case 16:
       return fp16 ? launch_tc_src<16, true>(src, -1, blocks_per_sm, literal, slot_floats, st)
                   : launch_tc_src<16, false>(src, -1, blocks_per_sm, literal, slot_floats, st);

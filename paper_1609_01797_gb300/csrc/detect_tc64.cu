@@ -1,0 +1,372 @@
+// Tensor-core TASER iterations for 34 <= N <= 65 (bucket of 64 variable columns).
+//
+// Same arithmetic as detect_tc.cu (mma.m16n8k16 with BF16/FP16 operands and FP32
+// accumulation, FP32 master L~ in the accumulator layout, FP32 prox) with two warps per
+// instance.  Row blocks of 16 are split for balance: warp 0 owns blocks 0 and 3, warp 1
+// blocks 1 and 2 (2 + 32 and 8 + 18 mma per iteration), and each warp owns half of the
+// augmented row 64 (n-tiles 0..3 or 4..7, 16 mma each).  Per iteration the warps exchange
+// through shared memory (double-buffered by iteration parity, two pair barriers):
+//   1. their half of row 64 as packed A-operand pairs (the row-64 tile needs all k-tiles),
+//      and their part of V_NN's partial sum;
+//   2. their partial column sums of squares.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace taser {
+
+template <bool FP16>
+__device__ __forceinline__ uint32_t pack2_64(float lo, float hi) {
+  if constexpr (FP16) {
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&h);
+  } else {
+    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t*>(&b);
+  }
+}
+
+template <bool FP16>
+__device__ __forceinline__ void mma64(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  if constexpr (FP16) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  } else {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+}
+
+// Shared exchange area of one instance (floats): [parity][ row64 A pairs (32 u32) |
+// V_NN partial (1) | pad | column partial sums [2 warps][64] ].
+constexpr int X64_ROW = 0, X64_VNN = 32, X64_COL = 36, X64_PAR = 36 + 128;
+constexpr int X64_INST = 2 * X64_PAR + 8;   // + pop slot
+
+__device__ __forceinline__ void pair_bar(int id) { asm volatile("bar.sync %0, 64;" ::"r"(id) : "memory"); }
+
+// ROLE 0: row blocks 0 and 3, row-64 n-tiles 0..3.  ROLE 1: blocks 1 and 2, n-tiles 4..7.
+template <bool FP16, int ROLE>
+__device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int bar, int literal) {
+  constexpr int MLO = ROLE ? 1 : 0, MHI = ROLE ? 2 : 3;
+  constexpr int NLO = 2 * MLO + 2, NHI = 2 * MHI + 2;   // n-tiles of the two row blocks
+  constexpr int RN0 = 4 * ROLE;                          // first n-tile of this warp's row-64 half
+  constexpr int NB = 64;
+  const int g = lane >> 2, tq = lane & 3;
+  const int N = jb.N;
+  const float* T = jb.T;
+  const float m2tau = -2.f * (*jb.tau);
+  auto tval = [&](int k, int n) -> float { return (k < N - 1 && n < N - 1) ? m2tau * T[(int64_t)k * N + n] : 0.f; };
+  auto needB = [](int kt, int n) -> bool {
+    return (kt <= MLO && n < NLO) || (kt <= MHI && n < NHI) || (n >= RN0 && n < RN0 + 4);
+  };
+  uint32_t bf[4][8][2];
+#pragma unroll
+  for (int kt = 0; kt < 4; ++kt)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      if (!needB(kt, nt)) continue;
+      const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
+      bf[kt][nt][0] = pack2_64<FP16>(tval(k0, n), tval(k0 + 1, n));
+      bf[kt][nt][1] = pack2_64<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
+    }
+  // Row N of T^ at this warp's row-64 columns c = 8 (RN0 + n) + 2tq + p.
+  float tN[4][2];
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int c = 8 * (RN0 + n) + 2 * tq + p;
+      tN[n][p] = (g == 0 && c < N - 1) ? m2tau * T[(int64_t)(N - 1) * N + c] : 0.f;
+    }
+  const float tnNN = m2tau * T[(int64_t)(N - 1) * N + (N - 1)];
+  const float DN = jb.D[N - 1];
+  // Column scales are owned per lane for columns 8g + 2tq + p (after the reduction).
+  float Down[2];
+#pragma unroll
+  for (int p = 0; p < 2; ++p) {
+    const int c = 8 * g + 2 * tq + p;
+    Down[p] = c < N - 1 ? jb.D[c] : 0.f;
+  }
+  float lo[NLO][4], hi[NHI][4], rw[4][4];
+#pragma unroll
+  for (int n = 0; n < NLO; ++n)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 16 * MLO + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+      lo[n][e] = (r == c && r < N - 1) ? jb.D[r] : 0.f;
+    }
+#pragma unroll
+  for (int n = 0; n < NHI; ++n)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int r = 16 * MHI + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+      hi[n][e] = (r == c && r < N - 1) ? jb.D[r] : 0.f;
+    }
+#pragma unroll
+  for (int n = 0; n < 4; ++n)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) rw[n][e] = 0.f;   // L~(0) row N: zeros (and L~_NN = D_N)
+  float LNN = DN;
+  uint32_t fl = 0;
+
+  for (int t = 0; t < jb.t_max; ++t) {
+    float* XP = X + (t & 1) * X64_PAR;
+    // --- exchange 1: this warp's half of row 64 (A pairs, lanes g == 0) and V_NN partial
+    float part = 0.f;
+#pragma unroll
+    for (int n = 0; n < 4; ++n) part = fmaf(rw[n][0], tN[n][0], fmaf(rw[n][1], tN[n][1], part));
+    part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
+    part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
+    uint32_t* rowA = reinterpret_cast<uint32_t*>(XP + X64_ROW);
+    if (g == 0) {
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {          // this warp's k-tiles 2 ROLE + kk
+        const int kt = 2 * ROLE + kk;
+        rowA[(kt * 4 + tq) * 2 + 0] = pack2_64<FP16>(rw[2 * kk][0], rw[2 * kk][1]);
+        rowA[(kt * 4 + tq) * 2 + 1] = pack2_64<FP16>(rw[2 * kk + 1][0], rw[2 * kk + 1][1]);
+      }
+      if (tq == 0) XP[X64_VNN + ROLE * 2] = part;
+    }
+    pair_bar(bar);
+    const float vpart = XP[X64_VNN] + XP[X64_VNN + 2];
+    // --- products: V = L~ - L~ T^ for the owned row blocks and the row-64 half
+    auto block_mma = [&](auto& acc, auto mtag) {
+      constexpr int M = decltype(mtag)::value;
+      constexpr int NT = 2 * M + 2;
+      uint32_t a[4][4];
+#pragma unroll
+      for (int kt = 0; kt <= M; ++kt) {
+        a[kt][0] = pack2_64<FP16>(acc[2 * kt][0], acc[2 * kt][1]);
+        a[kt][1] = pack2_64<FP16>(acc[2 * kt][2], acc[2 * kt][3]);
+        a[kt][2] = pack2_64<FP16>(acc[2 * kt + 1][0], acc[2 * kt + 1][1]);
+        a[kt][3] = pack2_64<FP16>(acc[2 * kt + 1][2], acc[2 * kt + 1][3]);
+      }
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int kt = 0; kt <= M; ++kt) mma64<FP16>(acc[n], a[kt], bf[kt][n]);
+#pragma unroll
+      for (int n = 2 * M; n <= 2 * M + 1; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+          if (c > r) acc[n][e] = 0.f;
+        }
+    };
+    block_mma(lo, std::integral_constant<int, MLO>{});
+    block_mma(hi, std::integral_constant<int, MHI>{});
+    {
+      uint32_t a[4][4];
+#pragma unroll
+      for (int kt = 0; kt < 4; ++kt) {
+        a[kt][0] = g == 0 ? rowA[(kt * 4 + tq) * 2 + 0] : 0u;
+        a[kt][2] = g == 0 ? rowA[(kt * 4 + tq) * 2 + 1] : 0u;
+        a[kt][1] = 0u;
+        a[kt][3] = 0u;
+      }
+#pragma unroll
+      for (int n = 0; n < 4; ++n) {
+        rw[n][0] = fmaf(LNN, tN[n][0], rw[n][0]);   // k = N term in FP32 (tN is 0 for g != 0)
+        rw[n][1] = fmaf(LNN, tN[n][1], rw[n][1]);
+#pragma unroll
+        for (int kt = 0; kt < 4; ++kt) mma64<FP16>(rw[n], a[kt], bf[kt][RN0 + n]);
+      }
+    }
+    const float vnn = fmaf(LNN, tnNN, LNN) + vpart;
+    if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
+    if (literal) LNN = vnn >= 0.f ? DN : -DN;
+    // --- column sums of squares: 16 partials per lane (n-tile, parity) over owned rows
+    float s[16];
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        float v = 0.f;
+        if (n < NLO) v = fmaf(lo[n][p], lo[n][p], fmaf(lo[n][2 + p], lo[n][2 + p], v));
+        if (n < NHI) v = fmaf(hi[n][p], hi[n][p], fmaf(hi[n][2 + p], hi[n][2 + p], v));
+        if (n >= RN0 && n < RN0 + 4) v = fmaf(rw[n - RN0][p], rw[n - RN0][p], v);
+        s[2 * n + p] = v;
+      }
+    // transpose-reduce over g: lane ends with columns 8g + 2tq + {0, 1}
+#pragma unroll
+    for (int step = 0; step < 3; ++step) {
+      const int m = 16 >> step;
+      const int h = 8 >> step;
+      const bool up = (lane & m) != 0;
+#pragma unroll
+      for (int i = 0; i < h; ++i) {
+        const float send = up ? s[i] : s[i + h];
+        const float keep = up ? s[i + h] : s[i];
+        s[i] = keep + __shfl_xor_sync(TASER_FULL_MASK, send, m);
+      }
+    }
+    float* col = XP + X64_COL;
+#pragma unroll
+    for (int p = 0; p < 2; ++p) col[ROLE * 64 + 8 * g + 2 * tq + p] = s[p];
+    pair_bar(bar);
+    float sc_own[2];
+#pragma unroll
+    for (int p = 0; p < 2; ++p) {
+      const int c = 8 * g + 2 * tq + p;
+      const float tot = col[c] + col[64 + c];
+      sc_own[p] = 0.f;
+      if (tot > 0.f) {
+        sc_own[p] = Down[p] * rsqrtf(tot);
+      } else if (c < N - 1) {
+        fl |= TASER_FLAG_ZERO_COLUMN;
+      }
+    }
+#pragma unroll
+    for (int n = 0; n < 8; ++n)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const float sc = __shfl_sync(TASER_FULL_MASK, sc_own[p], 4 * n + tq);
+        if (n < NLO) {
+          lo[n][p] *= sc;
+          lo[n][2 + p] *= sc;
+        }
+        if (n < NHI) {
+          hi[n][p] *= sc;
+          hi[n][2 + p] *= sc;
+        }
+        if (n >= RN0 && n < RN0 + 4) rw[n - RN0][p] *= sc;
+      }
+  }
+
+  // Outputs.
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
+  if (lane == 0 && jb.flag != nullptr && fl) atomicOr(jb.flag, fl);
+  if (g == 0) {
+#pragma unroll
+    for (int n = 0; n < 4; ++n)
+#pragma unroll
+      for (int p = 0; p < 2; ++p) {
+        const int c = 8 * (RN0 + n) + 2 * tq + p;
+        if (c < N - 1) {
+          float r = rw[n][p];
+          if (literal && LNN < 0.f) r = -r;
+          jb.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
+        }
+      }
+  }
+  if (jb.L != nullptr) {
+    float* Lo = jb.L;
+    auto put = [&](auto& acc, auto mtag, int nmax) {
+      constexpr int M = decltype(mtag)::value;
+#pragma unroll
+      for (int n = 0; n < 8; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+          if (r >= N - 1 || c >= N - 1) continue;
+          Lo[(int64_t)r * N + c] = n < nmax ? acc[n < nmax ? n : 0][e] : 0.f;
+        }
+    };
+    put(lo, std::integral_constant<int, MLO>{}, NLO);
+    put(hi, std::integral_constant<int, MHI>{}, NHI);
+    if (g == 0) {
+#pragma unroll
+      for (int n = 0; n < 4; ++n)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+          const int c = 8 * (RN0 + n) + 2 * tq + p;
+          if (c < N - 1) Lo[(int64_t)(N - 1) * N + c] = rw[n][p];
+        }
+    }
+    if (ROLE == 0)
+      for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+  }
+}
+
+// Two warps per instance, two instances per block.  The pair's first warp takes the job
+// (fixed stride or queue pop) and shares it through shared memory.
+template <bool FP16, bool QUEUE>
+__global__ void __launch_bounds__(128)
+detect_tc64_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
+                   const float* __restrict__ tau, int t_max, float* __restrict__ L, int8_t* __restrict__ s,
+                   uint32_t* __restrict__ flags, Queue q, const float* __restrict__ T_pool,
+                   const float* __restrict__ D_pool, float* __restrict__ L_pool, int8_t* __restrict__ s_pool,
+                   int literal) {
+  __shared__ __align__(16) float xsm[2 * X64_INST];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int pair = warp >> 1, role = warp & 1;
+  float* X = xsm + pair * X64_INST;
+  int* slot = reinterpret_cast<int*>(X + 2 * X64_PAR);
+  const int bar = 1 + pair;
+  const int64_t stride = (int64_t)gridDim.x * 2;
+  int64_t k = 0;
+  for (;;) {
+    int64_t idx;
+    if constexpr (QUEUE) {
+      if (role == 0 && lane == 0) *slot = q.pop(1);
+      pair_bar(bar);
+      const int pos = *slot;
+      pair_bar(bar);
+      if (pos >= q.count()) break;
+      idx = q.item_at(pos);
+    } else {
+      idx = (int64_t)blockIdx.x * 2 + pair + k * stride;
+      ++k;
+      if (idx >= batch) break;
+    }
+    Job jb;
+    if constexpr (QUEUE) {
+      const taser_item it = q.items[idx];
+      jb = item_job(it, idx, T_pool, D_pool, tau, L_pool, s_pool, flags);
+    } else {
+      jb = dense_job(idx, N, t_max, Tt, Dg, tau, L, s, flags);
+    }
+    if (role == 0) tc64_run<FP16, 0>(jb, X, lane, bar, literal);
+    else tc64_run<FP16, 1>(jb, X, lane, bar, literal);
+    pair_bar(bar);
+  }
+}
+
+template <bool FP16, bool QUEUE>
+static cudaError_t launch_tc64(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                               int literal, float* L, int8_t* s, uint32_t* flags, const Queue& q, int blocks_per_sm,
+                               const float* T_pool, const float* D_pool, float* L_pool, int8_t* s_pool,
+                               cudaStream_t st) {
+  int dev = 0, sms = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc64_kernel<FP16, QUEUE>, 128, 0);
+  if (e != cudaSuccess) return e;
+  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
+  int64_t blocks = (int64_t)sms * per_sm;
+  if (!QUEUE) {
+    const int64_t need = (batch + 1) / 2;
+    if (need < blocks) blocks = need;
+  }
+  detect_tc64_kernel<FP16, QUEUE><<<(unsigned)blocks, 128, 0, st>>>(batch, N, Tt, D, tau, t_max, L, s, flags, q,
+                                                                   T_pool, D_pool, L_pool, s_pool, literal);
+  return cudaGetLastError();
+}
+
+cudaError_t detect_tc64(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                        int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
+  Queue q{};
+  return fp16 ? launch_tc64<true, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, q, 0, nullptr, nullptr,
+                                         nullptr, nullptr, st)
+              : launch_tc64<false, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, q, 0, nullptr, nullptr,
+                                          nullptr, nullptr, st);
+}
+
+cudaError_t detect_tc64_queue(bool fp16, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
+                              const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
+                              cudaStream_t st) {
+  return fp16 ? launch_tc64<true, true>(0, 0, nullptr, nullptr, tau, 0, literal, nullptr, nullptr, flags, q,
+                                        blocks_per_sm, T_pool, D_pool, L_pool, s_pool, st)
+              : launch_tc64<false, true>(0, 0, nullptr, nullptr, tau, 0, literal, nullptr, nullptr, flags, q,
+                                         blocks_per_sm, T_pool, D_pool, L_pool, s_pool, st);
+}
+
+}  // namespace taser

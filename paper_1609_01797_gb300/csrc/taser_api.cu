@@ -163,7 +163,7 @@ taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const floa
   if (flags != nullptr) TASER_REQUIRE(aligned16(flags), "flags must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int literal = lnn_mode == TASER_LNN_LITERAL;
-  if (precision != TASER_FP32 && taser::bucket_of(N) >= 16 && taser::bucket_of(N) <= 32) {
+  if (precision != TASER_FP32 && taser::bucket_of(N) >= 16) {
     return from_cuda(taser::detect_tc(batch, N, T_tilde, D, tau, t_max, literal, precision == TASER_FP16_TC, L,
                                       s_hat, flags, st),
                      "detect_tc");

@@ -91,7 +91,7 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
     q.b = b;
     const int bps = tuning != nullptr ? tuning->blocks_per_sm[b] : 0;
     const int pop = tuning != nullptr ? tuning->pop[b] : 1;
-    if (precision != TASER_FP32 && (nb == 16 || nb == 32)) {
+    if (precision != TASER_FP32 && nb >= 16) {
       e = detect_tc_queue(nb, precision == TASER_FP16_TC, q, bps, pop, T_pool, D_pool, tau, literal, L_pool, s_pool,
                           flags, st);
     } else {

@@ -73,7 +73,7 @@ def test_detect_fp32_matches_oracle(T, N, t_max, mode):
     np.testing.assert_array_equal(got & O.FLAG_ZERO_COLUMN, fo & O.FLAG_ZERO_COLUMN)
 
 
-@pytest.mark.parametrize("N", [10, 16, 17, 24, 32, 33])
+@pytest.mark.parametrize("N", [10, 16, 17, 24, 32, 33, 34, 47, 64, 65])
 @pytest.mark.parametrize("precision", ["bf16_tc", "fp16_tc"])
 @pytest.mark.parametrize("t_max", [1, 20])
 def test_detect_tensor_core_matches_oracle(T, N, precision, t_max):
@@ -91,6 +91,25 @@ def test_detect_tensor_core_matches_oracle(T, N, precision, t_max):
     np.testing.assert_allclose(np.linalg.norm(L[:, :, :-1], axis=1), D[:, :-1], rtol=1e-5)
     m = confident(Lo, 5e-2)
     np.testing.assert_array_equal(s.cpu().numpy()[m], so[m])
+
+
+@pytest.mark.parametrize("N", [17, 33, 40, 65])
+def test_detect_tensor_core_literal_mode(T, N):
+    """Literal L~_NN handling (sign of V_NN kept, decisions flipped with it) on the
+    tensor-core kernels, against the oracle in literal mode at 0 dB."""
+    Tt, D, tau = oracle_inputs(N, 97, seed=4000 + N, snr=0.0)
+    Lo, fo = O.taser(Tt.astype(np.float64), D.astype(np.float64), tau.astype(np.float64), 20, "literal")
+    so = O.decisions(Lo, "literal")
+    dT, dD, dtau = to_dev(Tt, D, tau)
+    s, L, flags = T.detect(dT, dD, dtau, 20, "bf16_tc", "literal")
+    torch.cuda.synchronize()
+    L = L.cpu().numpy().astype(np.float64)
+    assert rel_frob(L, Lo).max() <= 3e-2
+    assert np.all(np.triu(L, 1) == 0)
+    m = confident(Lo, 5e-2)
+    np.testing.assert_array_equal(s.cpu().numpy()[m], so[m])
+    got = flags.cpu().numpy().astype(np.uint32)
+    np.testing.assert_array_equal(got & O.FLAG_ZERO_COLUMN, fo & O.FLAG_ZERO_COLUMN)
 
 
 def test_tensor_core_falls_back_to_fp32_below_10(T):
@@ -177,7 +196,8 @@ def test_step_size_with_structure_hint(T, kind, B, M):
 @pytest.mark.parametrize("kind,B,M,t_max,precision", [
     ("mimo_bpsk", 32, 8, 10, "fp32"), ("mimo_qpsk", 128, 16, 20, "fp32"), ("jed_bpsk", 16, 16, 20, "fp32"),
     ("jed_bpsk", 16, 32, 20, "fp32"), ("mimo_qpsk", 64, 8, 20, "fp32"), ("mimo_qpsk", 256, 32, 10, "fp32"),
-    ("mimo_qpsk", 128, 16, 20, "bf16_tc"), ("mimo_qpsk", 128, 16, 20, "fp16_tc"), ("jed_bpsk", 16, 32, 20, "bf16_tc")])
+    ("mimo_qpsk", 128, 16, 20, "bf16_tc"), ("mimo_qpsk", 128, 16, 20, "fp16_tc"), ("jed_bpsk", 16, 32, 20, "bf16_tc"),
+    ("mimo_qpsk", 256, 32, 20, "bf16_tc")])
 def test_end_to_end_matches_oracle(T, kind, B, M, t_max, precision):
     n = 203
     snr = np.linspace(0.0, 20.0, n)
