@@ -48,12 +48,26 @@ typedef enum {
     TASER_SIMO_JED_BPSK = 2  /* N = K,      Y complex64 [batch][B][K], slot 0 = +1 pilot */
 } taser_problem;
 
-/* Arithmetic of the triangular product L~ T^ inside the iterations.  The prox
- * (column norms and rescaling) and the master copy of L~ are always FP32. */
+/* Arithmetic of the iterations.  For the first three the triangular product L~ T^
+ * runs at the named precision while the prox (column norms and rescaling) and the
+ * master copy of L~ stay FP32.  TASER_FIXED14 is the 14-bit fixed-point datapath of
+ * the paper's VLSI designs (Sec. IV-B operation modes, Sec. IV-D fixed-point
+ * parameters and inverse square-root LUT), computed exactly in integer arithmetic:
+ *   - L~ and V carry 8 fraction bits, 7 in row N; L~_NN is a constant register with 5
+ *     (so only TASER_LNN_FIXED exists; TASER_LNN_LITERAL returns TASER_ERR_UNSUPPORTED);
+ *   - T^ = 2 tau T~ has 12 fraction bits, quantised from the FP32 product fl(2 tau) T~_ij;
+ *     D_j has 8, D_N 5;
+ *   - every format saturates to [-2^13, 2^13 - 1] (TASER_FLAG_SATURATED) and rounds
+ *     half up; the MAC and the squared column norms are exact;
+ *   - 1/||v_j|| comes from a 2^11-entry LUT (13 fraction bits) indexed by the top 11
+ *     bits of the normalised squared norm, LUT[i] = round(2^13 / sqrt((i + 1/2)/512)).
+ * The results (L~ codes scaled to floats, decisions, flags) are bit-exact and do not
+ * depend on the GPU or the launch shape. */
 typedef enum {
     TASER_FP32 = 0,      /* FP32 FMA pipe                                              */
     TASER_BF16_TC = 1,   /* tensor cores, BF16 operands, FP32 accumulation             */
-    TASER_FP16_TC = 2    /* tensor cores, FP16 operands, FP32 accumulation             */
+    TASER_FP16_TC = 2,   /* tensor cores, FP16 operands, FP32 accumulation             */
+    TASER_FIXED14 = 3    /* 14-bit fixed point of Sec. IV-D, exact integer emulation   */
 } taser_precision;
 
 /* Handling of L~_NN (the prox of Sec. III-C applied to the last column). */
@@ -69,6 +83,7 @@ typedef enum {
 #define TASER_FLAG_LNN_SIGN    (1u << 3) /* V_NN <= 0 was seen in some iteration         */
 
 #define TASER_FLAG_BAD_ITEM    (1u << 4) /* uneven batch: item with N or t_max out of range */
+#define TASER_FLAG_SATURATED   (1u << 5) /* TASER_FIXED14: a value saturated to 14 bits    */
 
 /* Largest N supported by the detection kernels. */
 #define TASER_MAX_N 65

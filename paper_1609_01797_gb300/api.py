@@ -10,7 +10,7 @@ from ._native import UnevenTuning, check, lib
 BPSK, QPSK, JED_BPSK = 0, 1, 2
 KINDS = {"mimo_bpsk": BPSK, "mimo_qpsk": QPSK, "jed_bpsk": JED_BPSK, BPSK: BPSK, QPSK: QPSK,
          JED_BPSK: JED_BPSK}
-PRECISIONS = {"fp32": 0, "bf16_tc": 1, "fp16_tc": 2}
+PRECISIONS = {"fp32": 0, "bf16_tc": 1, "fp16_tc": 2, "fixed14": 3}
 LNN_MODES = {"fixed": 0, "literal": 1}
 
 

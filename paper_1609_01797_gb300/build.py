@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libtaser.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["taser_api.cu", "build_T.cu", "spectral.cu", "detect_fp32.cu", "detect_tc.cu", "detect_tc64.cu", "static_scratch.cu", "unfolded.cu", "uneven.cu"]
+SOURCES = ["taser_api.cu", "build_T.cu", "spectral.cu", "detect_fp32.cu", "detect_tc.cu", "detect_tc64.cu", "detect_fx14.cu", "static_scratch.cu", "unfolded.cu", "uneven.cu"]
 
 
 def _nvcc():

@@ -48,6 +48,35 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
   }
 }
 
+// Packed FP32 pairs (fma/mul/add.rn.f32x2): one instruction for the two columns
+// (2tq, 2tq + 1) an accumulator register pair holds.  Each half is the IEEE result of the
+// scalar operation.
+__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void f2unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// acc[e], acc[e + 1] = f(acc[e], acc[e + 1]) for a packed operation f.
+#define TASER_PAIR_APPLY(arr, e, expr)          \
+  do {                                          \
+    const uint64_t _x = f2pack(arr[e], arr[e + 1]); \
+    const uint64_t _y = (expr);                 \
+    f2unpack(_y, arr[e], arr[e + 1]);           \
+  } while (0)
+
 // Tile bookkeeping for bucket NB (16 or 32).
 template <int NB>
 struct TcCfg {
@@ -199,6 +228,12 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
         const int c = 8 * nt + 2 * tq + p;
         tN[nt][p] = c < N - 1 ? m2tau * T[(N - 1) * N + c] : 0.f;
       }
+    uint64_t tN2[NT], tNg2[NT];   // packed pairs; tNg2 is zero off the lanes holding row N
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      tN2[nt] = f2pack(tN[nt][0], tN[nt][1]);
+      tNg2[nt] = g == 0 ? tN2[nt] : 0ull;
+    }
     const float tnNN = m2tau * T[(N - 1) * N + (N - 1)];
     const float DN = Di[N - 1];
     // After the column-sum reduction this lane owns column cown.
@@ -232,9 +267,12 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
 
     for (int t = 0; t < t_max; ++t) {
       // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
-      float part = 0.f;
+      uint64_t part2 = 0ull;
 #pragma unroll
-      for (int n = 0; n < NT; ++n) part = fmaf(acc[MT - 1][n][0], tN[n][0], fmaf(acc[MT - 1][n][1], tN[n][1], part));
+      for (int n = 0; n < NT; ++n) part2 = f2fma(f2pack(acc[MT - 1][n][0], acc[MT - 1][n][1]), tN2[n], part2);
+      float part, part_hi;
+      f2unpack(part2, part, part_hi);
+      part += part_hi;
       part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
       part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
       part = __shfl_sync(TASER_FULL_MASK, part, 0);
@@ -258,11 +296,9 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
         }
         if (M == MT - 1) {
           // k = N term of row N in FP32: L~_NN T^_{N,c}.
+          const uint64_t lnn2 = f2pack(LNN, LNN);
 #pragma unroll
-          for (int n = 0; n < NT; ++n) {
-            acc[M][n][0] = fmaf(LNN, g == 0 ? tN[n][0] : 0.f, acc[M][n][0]);
-            acc[M][n][1] = fmaf(LNN, g == 0 ? tN[n][1] : 0.f, acc[M][n][1]);
-          }
+          for (int n = 0; n < NT; ++n) TASER_PAIR_APPLY(acc[M][n], 0, f2fma(lnn2, tNg2[n], _x));
         }
 #pragma unroll
         for (int n = 0; n < NT; ++n) {
@@ -289,18 +325,20 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
       // prox: column sums of squares, reduced over the 8 lanes sharing tq.
       float s[C::NV];
 #pragma unroll
-      for (int n = 0; n < NT; ++n)
+      for (int n = 0; n < NT; ++n) {
+        uint64_t v2 = 0ull;
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          float v = 0.f;
-#pragma unroll
-          for (int M = 0; M < MT; ++M) {
-            if (!C::has_tile(M, n)) continue;
-            v = fmaf(acc[M][n][p], acc[M][n][p], v);
-            if (M < MT - 1) v = fmaf(acc[M][n][2 + p], acc[M][n][2 + p], v);
+        for (int M = 0; M < MT; ++M) {
+          if (!C::has_tile(M, n)) continue;
+          const uint64_t x01 = f2pack(acc[M][n][0], acc[M][n][1]);
+          v2 = f2fma(x01, x01, v2);
+          if (M < MT - 1) {
+            const uint64_t x23 = f2pack(acc[M][n][2], acc[M][n][3]);
+            v2 = f2fma(x23, x23, v2);
           }
-          s[2 * n + p] = v;
         }
+        f2unpack(v2, s[2 * n], s[2 * n + 1]);
+      }
       // Transpose-reduce over lane bits 4, 3, 2: each step halves the values a lane keeps.
       {
         int len = C::NV;
@@ -329,19 +367,21 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
         fl |= TASER_FLAG_ZERO_COLUMN;
       }
 #pragma unroll
-      for (int n = 0; n < NT; ++n)
+      for (int n = 0; n < NT; ++n) {
+        float sc[2];
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
           const int idx = 2 * n + p;
-          const int src = 4 * (NT == 4 ? idx : 2 * idx) + tq;
-          const float sc = __shfl_sync(TASER_FULL_MASK, sc_own, src);
-#pragma unroll
-          for (int M = 0; M < MT; ++M) {
-            if (!C::has_tile(M, n)) continue;
-            acc[M][n][p] *= sc;
-            if (M < MT - 1) acc[M][n][2 + p] *= sc;
-          }
+          sc[p] = __shfl_sync(TASER_FULL_MASK, sc_own, 4 * (NT == 4 ? idx : 2 * idx) + tq);
         }
+        const uint64_t sc2 = f2pack(sc[0], sc[1]);
+#pragma unroll
+        for (int M = 0; M < MT; ++M) {
+          if (!C::has_tile(M, n)) continue;
+          TASER_PAIR_APPLY(acc[M][n], 0, f2mul(_x, sc2));
+          if (M < MT - 1) TASER_PAIR_APPLY(acc[M][n], 2, f2mul(_x, sc2));
+        }
+      }
     }
 
 #pragma unroll

@@ -44,6 +44,29 @@ __device__ __forceinline__ void mma64(float (&d)[4], const uint32_t (&a)[4], con
   }
 }
 
+__device__ __forceinline__ uint64_t p2pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void p2unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t p2fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ uint64_t p2mul(uint64_t a, uint64_t b) {
+  uint64_t d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// (v[e], v[e + 1]) *= sc2, as one packed multiply.
+__device__ __forceinline__ void p2scale(float* v, uint64_t sc2) {
+  p2unpack(p2mul(p2pack(v[0], v[1]), sc2), v[0], v[1]);
+}
+
 // Shared exchange area of one instance (floats): [parity][ row64 A pairs (32 u32) |
 // V_NN partial (1) | pad | column partial sums [2 warps][64] ].
 constexpr int X64_ROW = 0, X64_VNN = 32, X64_COL = 36, X64_PAR = 36 + 128;
@@ -85,6 +108,9 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
       const int c = 8 * (RN0 + n) + 2 * tq + p;
       tN[n][p] = (g == 0 && c < N - 1) ? m2tau * T[(int64_t)(N - 1) * N + c] : 0.f;
     }
+  uint64_t tN2[4];
+#pragma unroll
+  for (int n = 0; n < 4; ++n) tN2[n] = p2pack(tN[n][0], tN[n][1]);
   const float tnNN = m2tau * T[(int64_t)(N - 1) * N + (N - 1)];
   const float DN = jb.D[N - 1];
   // Column scales are owned per lane for columns 8g + 2tq + p (after the reduction).
@@ -119,9 +145,12 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
   for (int t = 0; t < jb.t_max; ++t) {
     float* XP = X + (t & 1) * X64_PAR;
     // --- exchange 1: this warp's half of row 64 (A pairs, lanes g == 0) and V_NN partial
-    float part = 0.f;
+    uint64_t part2 = 0ull;
 #pragma unroll
-    for (int n = 0; n < 4; ++n) part = fmaf(rw[n][0], tN[n][0], fmaf(rw[n][1], tN[n][1], part));
+    for (int n = 0; n < 4; ++n) part2 = p2fma(p2pack(rw[n][0], rw[n][1]), tN2[n], part2);
+    float part, part_hi;
+    p2unpack(part2, part, part_hi);
+    part += part_hi;
     part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
     part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
     uint32_t* rowA = reinterpret_cast<uint32_t*>(XP + X64_ROW);
@@ -172,9 +201,10 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
         a[kt][3] = 0u;
       }
 #pragma unroll
+      const uint64_t lnn2 = p2pack(LNN, LNN);
       for (int n = 0; n < 4; ++n) {
-        rw[n][0] = fmaf(LNN, tN[n][0], rw[n][0]);   // k = N term in FP32 (tN is 0 for g != 0)
-        rw[n][1] = fmaf(LNN, tN[n][1], rw[n][1]);
+        // k = N term in FP32 (tN is 0 for g != 0)
+        p2unpack(p2fma(lnn2, tN2[n], p2pack(rw[n][0], rw[n][1])), rw[n][0], rw[n][1]);
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma64<FP16>(rw[n], a[kt], bf[kt][RN0 + n]);
       }
@@ -185,15 +215,23 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
     // --- column sums of squares: 16 partials per lane (n-tile, parity) over owned rows
     float s[16];
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        float v = 0.f;
-        if (n < NLO) v = fmaf(lo[n][p], lo[n][p], fmaf(lo[n][2 + p], lo[n][2 + p], v));
-        if (n < NHI) v = fmaf(hi[n][p], hi[n][p], fmaf(hi[n][2 + p], hi[n][2 + p], v));
-        if (n >= RN0 && n < RN0 + 4) v = fmaf(rw[n - RN0][p], rw[n - RN0][p], v);
-        s[2 * n + p] = v;
+    for (int n = 0; n < 8; ++n) {
+      uint64_t v2 = 0ull;
+      auto sq = [&](float a, float b) {
+        const uint64_t x = p2pack(a, b);
+        v2 = p2fma(x, x, v2);
+      };
+      if (n < NLO) {
+        sq(lo[n][2], lo[n][3]);
+        sq(lo[n][0], lo[n][1]);
       }
+      if (n < NHI) {
+        sq(hi[n][2], hi[n][3]);
+        sq(hi[n][0], hi[n][1]);
+      }
+      if (n >= RN0 && n < RN0 + 4) sq(rw[n - RN0][0], rw[n - RN0][1]);
+      p2unpack(v2, s[2 * n], s[2 * n + 1]);
+    }
     // transpose-reduce over g: lane ends with columns 8g + 2tq + {0, 1}
 #pragma unroll
     for (int step = 0; step < 3; ++step) {
@@ -224,20 +262,19 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
       }
     }
 #pragma unroll
-    for (int n = 0; n < 8; ++n)
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const float sc = __shfl_sync(TASER_FULL_MASK, sc_own[p], 4 * n + tq);
-        if (n < NLO) {
-          lo[n][p] *= sc;
-          lo[n][2 + p] *= sc;
-        }
-        if (n < NHI) {
-          hi[n][p] *= sc;
-          hi[n][2 + p] *= sc;
-        }
-        if (n >= RN0 && n < RN0 + 4) rw[n - RN0][p] *= sc;
+    for (int n = 0; n < 8; ++n) {
+      const uint64_t sc2 = p2pack(__shfl_sync(TASER_FULL_MASK, sc_own[0], 4 * n + tq),
+                                  __shfl_sync(TASER_FULL_MASK, sc_own[1], 4 * n + tq));
+      if (n < NLO) {
+        p2scale(&lo[n][0], sc2);
+        p2scale(&lo[n][2], sc2);
       }
+      if (n < NHI) {
+        p2scale(&hi[n][0], sc2);
+        p2scale(&hi[n][2], sc2);
+      }
+      if (n >= RN0 && n < RN0 + 4) p2scale(&rw[n - RN0][0], sc2);
+    }
   }
 
   // Outputs.

@@ -24,6 +24,8 @@ cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, c
                         int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
 cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                       int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
+cudaError_t detect_fx14(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max, float* L,
+                        int8_t* s, uint32_t* flags, cudaStream_t st);
 }  // namespace taser
 
 namespace {
@@ -151,9 +153,12 @@ taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const floa
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
-  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC,
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC ||
+                    precision == TASER_FIXED14,
                 "unknown precision %d", precision);
   TASER_REQUIRE(lnn_mode == TASER_LNN_FIXED || lnn_mode == TASER_LNN_LITERAL, "unknown lnn_mode %d", lnn_mode);
+  if (precision == TASER_FIXED14 && lnn_mode != TASER_LNN_FIXED)
+    return fail(TASER_ERR_UNSUPPORTED, "TASER_FIXED14 keeps L~_NN constant: only TASER_LNN_FIXED is available");
   if (batch == 0) return ok();
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(D, "D");
@@ -163,6 +168,9 @@ taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const floa
   if (flags != nullptr) TASER_REQUIRE(aligned16(flags), "flags must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int literal = lnn_mode == TASER_LNN_LITERAL;
+  if (precision == TASER_FIXED14) {
+    return from_cuda(taser::detect_fx14(batch, N, T_tilde, D, tau, t_max, L, s_hat, flags, st), "detect_fx14");
+  }
   if (precision != TASER_FP32 && taser::bucket_of(N) >= 16) {
     return from_cuda(taser::detect_tc(batch, N, T_tilde, D, tau, t_max, literal, precision == TASER_FP16_TC, L,
                                       s_hat, flags, st),
@@ -319,9 +327,12 @@ taser_status taser_detect_uneven(int64_t n_items, const taser_item* items, const
                                  const taser_uneven_tuning* tuning, void* stream) {
   TASER_REQUIRE(n_items >= 0 && n_items <= 0x7fffffff, "n_items must lie in [0, 2^31) (got %lld)",
                 (long long)n_items);
-  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC,
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC ||
+                    precision == TASER_FIXED14,
                 "unknown precision %d", precision);
   TASER_REQUIRE(lnn_mode == TASER_LNN_FIXED || lnn_mode == TASER_LNN_LITERAL, "unknown lnn_mode %d", lnn_mode);
+  if (precision == TASER_FIXED14 && lnn_mode != TASER_LNN_FIXED)
+    return fail(TASER_ERR_UNSUPPORTED, "TASER_FIXED14 keeps L~_NN constant: only TASER_LNN_FIXED is available");
   if (n_items == 0) return ok();
   TASER_REQUIRE(items != nullptr && (reinterpret_cast<uintptr_t>(items) & 7u) == 0, "items must be 8-byte aligned");
   TASER_REQUIRE(T_pool != nullptr && D_pool != nullptr && tau != nullptr && s_pool != nullptr,

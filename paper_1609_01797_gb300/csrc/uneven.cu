@@ -71,6 +71,9 @@ size_t uneven_workspace_bytes(int64_t n_items) {
   return list + 256;
 }
 
+cudaError_t detect_fx14_queue(int nb, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
+                              const float* tau, float* L_pool, int8_t* s_pool, uint32_t* flags, cudaStream_t st);
+
 cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float* T_pool, const float* D_pool,
                           const float* tau, int precision, int literal, float* L_pool, int8_t* s_pool,
                           uint32_t* flags, void* workspace, const taser_uneven_tuning* tuning, cudaStream_t st) {
@@ -91,7 +94,9 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
     q.b = b;
     const int bps = tuning != nullptr ? tuning->blocks_per_sm[b] : 0;
     const int pop = tuning != nullptr ? tuning->pop[b] : 1;
-    if (precision != TASER_FP32 && nb >= 16) {
+    if (precision == TASER_FIXED14) {
+      e = detect_fx14_queue(nb, q, bps, T_pool, D_pool, tau, L_pool, s_pool, flags, st);
+    } else if (precision != TASER_FP32 && nb >= 16) {
       e = detect_tc_queue(nb, precision == TASER_FP16_TC, q, bps, pop, T_pool, D_pool, tau, literal, L_pool, s_pool,
                           flags, st);
     } else {

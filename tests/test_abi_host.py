@@ -59,12 +59,17 @@ def _detect(lib, **kw):
                             a["L"], a["s"], a["flags"], None)
 
 
-@pytest.mark.parametrize("kw", [dict(N=1), dict(N=66), dict(t_max=0), dict(batch=-1), dict(prec=3),
+@pytest.mark.parametrize("kw", [dict(N=1), dict(N=66), dict(t_max=0), dict(batch=-1), dict(prec=4),
                                 dict(mode=2), dict(T=None), dict(D=None), dict(tau=None), dict(s=None),
                                 dict(T=P4), dict(L=P4), dict(flags=P4)])
 def test_detect_rejects_invalid_arguments(lib, kw):
     assert _detect(lib, **kw) == 1
     assert lib.taser_last_error()
+
+
+def test_fixed_point_has_no_literal_mode(lib):
+    assert _detect(lib, prec=3, mode=1) == 2                  # TASER_ERR_UNSUPPORTED, before any launch
+    assert b"FIXED14" in lib.taser_last_error()
 
 
 def test_detect_empty_batch_is_noop(lib):
