@@ -21,6 +21,8 @@ Readings taken where the paper is silent or ambiguous (each is listed in DESIGN.
       so that the relaxed vector is exactly in {+-1}^N.
   R2  The augmented "1" coordinate is the last index N; for JED the pilot column
       y_0 s_0 (s_0 = +1) is moved to the end, so N = K when K counts the pilot slot.
+  R16 JED with QPSK: the pilot is s_0 = (1 + j)/sqrt2, the data slots use the effective
+      Y_r / sqrt2 (as R1), and N = 2K - 1 when K counts the pilot slot.
   R3  D_kk = sqrt(|T_kk|) (T_kk < 0 for JED); D_kk = 0 is replaced by 1 and flagged.
   R7  Sign of L~_NN: mode "fixed" (default) keeps L~_NN = D_NN, mode "literal" applies
       the prox to the last column as well, L~_NN = D_NN sign(V_NN), and multiplies
@@ -56,6 +58,8 @@ def problem_size(kind, U_or_K):
         return 2 * U_or_K + 1
     if kind == "jed_bpsk":
         return U_or_K
+    if kind == "jed_qpsk":
+        return 2 * U_or_K - 1
     raise ValueError(kind)
 
 
@@ -113,6 +117,29 @@ def T_jed_bpsk(Y):
     return -np.matmul(np.transpose(A, (0, 2, 1)), A)
 
 
+QPSK_PILOT = (1.0 + 1.0j) / np.sqrt(2.0)
+
+
+def T_jed_qpsk(Y):
+    """SIMO JED with QPSK (Sec. II-B, Eq. 5).
+
+    Y complex [n, B, K]; column 0 is the pilot slot, s_0 = (1 + j)/sqrt2 (reading R16).
+    ybar = [Re(y_0 s_0); Im(y_0 s_0)], Hbar = [[Re Y_r, -Im Y_r], [Im Y_r, Re Y_r]] of the
+    effective Y_r / sqrt2 (reading R1), and
+    T = -[Hbar^T Hbar, Hbar^T ybar; ybar^T Hbar, ybar^T ybar] = -A^T A with A = [Hbar, ybar].
+    N = 2(K - 1) + 1 = 2K - 1 (the paper's 2K + 1 with its K = our K - 1 data slots).
+    """
+    Y = np.asarray(Y, dtype=np.complex128)
+    y0 = Y[:, :, 0] * QPSK_PILOT
+    Yr = Y[:, :, 1:] * QPSK_SCALE
+    ybar = np.concatenate([y0.real, y0.imag], axis=1)
+    top = np.concatenate([Yr.real, -Yr.imag], axis=2)
+    bot = np.concatenate([Yr.imag, Yr.real], axis=2)
+    Hbar = np.concatenate([top, bot], axis=1)
+    A = np.concatenate([Hbar, ybar[:, :, None]], axis=2)
+    return -np.matmul(np.transpose(A, (0, 2, 1)), A)
+
+
 def build_T(kind, H_or_Y, y=None):
     if kind == "mimo_bpsk":
         return T_mimo(H_or_Y, y, "bpsk")
@@ -120,6 +147,8 @@ def build_T(kind, H_or_Y, y=None):
         return T_mimo(H_or_Y, y, "qpsk")
     if kind == "jed_bpsk":
         return T_jed_bpsk(H_or_Y)
+    if kind == "jed_qpsk":
+        return T_jed_qpsk(H_or_Y)
     raise ValueError(kind)
 
 

@@ -67,27 +67,38 @@ def make_mimo(n, B, U, snr_db, constellation="qpsk", seed=0):
     }
 
 
-def make_jed(n, B, K, snr_db, seed=0):
-    """n independent SIMO JED instances over K slots (slot 0 carries the +1 pilot).
+def make_jed(n, B, K, snr_db, seed=0, constellation="bpsk"):
+    """n independent SIMO JED instances over K slots, Y = h s^H + noise (slot 0 is the pilot).
 
-    Returns Y complex64 [n, B, K], s int8 [n, K] (s[:, 0] == +1), N0, snr_db.
+    BPSK: s int8 [n, K] of +-1 with s[:, 0] == +1.
+    QPSK: s complex [n, K] of (+-1 +-j)/sqrt2 with s[:, 0] == (1 + j)/sqrt2, plus bits_re,
+          bits_im int8 [n, K] (the signs of its real and imaginary parts).
+    Returns Y complex64 [n, B, K], s, N0, snr_db (N0 = 1/SNR per receive antenna).
     """
     rng = rng_for(seed)
     snr_db = np.broadcast_to(np.asarray(snr_db, dtype=np.float64), (n,)).copy()
     h = _cn(rng, (n, B))
-    s = _pm1(rng, (n, K))
-    s[:, 0] = 1
+    out = {}
+    if constellation == "bpsk":
+        s = _pm1(rng, (n, K))
+        s[:, 0] = 1
+        sym = s.astype(np.float64)
+        out["s"] = s
+    elif constellation == "qpsk":
+        bits_re = _pm1(rng, (n, K))
+        bits_im = _pm1(rng, (n, K))
+        bits_re[:, 0] = 1
+        bits_im[:, 0] = 1
+        sym = (bits_re + 1j * bits_im) / np.sqrt(2.0)
+        out.update(s=sym, bits_re=bits_re, bits_im=bits_im)
+    else:
+        raise ValueError(constellation)
     N0 = 1.0 / 10.0 ** (snr_db / 10.0)
     noise = _cn(rng, (n, B, K)) * np.sqrt(N0)[:, None, None]
-    Y = h[:, :, None] * s[:, None, :].astype(np.float64) + noise
-    return {
-        "Y": np.ascontiguousarray(Y.astype(np.complex64)),
-        "s": s,
-        "N0": N0,
-        "snr_db": snr_db,
-        "B": B,
-        "K": K,
-    }
+    Y = h[:, :, None] * np.conj(sym)[:, None, :] + noise
+    out.update(Y=np.ascontiguousarray(Y.astype(np.complex64)), N0=N0, snr_db=snr_db, B=B, K=K,
+               constellation=constellation)
+    return out
 
 
 # (B, U) pairs of the uneven QPSK batch: N = 2U + 1 = 9, 17, 33, 65.

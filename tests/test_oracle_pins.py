@@ -58,6 +58,40 @@ def test_T_jed_equals_minus_energy():
         np.testing.assert_allclose(lhs, -energy, rtol=1e-12)
 
 
+def test_T_jed_qpsk_equals_minus_energy():
+    """s~^T T s~ = -||Y s||^2 for QPSK JED with the pilot s_0 = (1 + j)/sqrt2 and data
+    s_k = (a_k + j b_k)/sqrt2, s~ = [a; b; 1] (Eq. 4 vs Eq. 5, readings R1, R16), in
+    complex arithmetic."""
+    n, B, K = 12, 6, 5
+    w = make_jed(n, B, K, 5.0, seed=13, constellation="qpsk")
+    T = O.T_jed_qpsk(w["Y"])
+    assert T.shape[1] == O.problem_size("jed_qpsk", K) == 2 * K - 1
+    Y = w["Y"].astype(np.complex128)
+    rng = np.random.default_rng(2)
+    for _ in range(20):
+        a = _random_signs(rng, n, K)[:, :-1]
+        b = _random_signs(rng, n, K)[:, :-1]
+        s_full = np.concatenate([np.full((n, 1), (1 + 1j) / np.sqrt(2.0)), (a + 1j * b) / np.sqrt(2.0)], axis=1)
+        s_t = np.concatenate([a, b, np.ones((n, 1))], axis=1)
+        energy = np.sum(np.abs(np.einsum("nbk,nk->nb", Y, s_full)) ** 2, axis=1)
+        lhs = np.einsum("ni,nij,nj->n", s_t, T, s_t)
+        np.testing.assert_allclose(lhs, -energy, rtol=1e-12)
+
+
+def test_noise_free_jed_qpsk_equals_ml_and_truth():
+    """Y = h s^H without noise: the exhaustive ML over the data slots and TASER both return
+    the transmitted QPSK symbols (the pilot fixes the phase ambiguity of Sec. II-B)."""
+    w = make_jed(20, 16, 5, 400.0, seed=21, constellation="qpsk")
+    r = O.detect("jed_qpsk", w["Y"], None, 0.45, 50)
+    truth = np.concatenate([w["bits_re"][:, 1:], w["bits_im"][:, 1:]], axis=1)
+    ml, _ = O.brute_force_ml(r["T"])
+    np.testing.assert_array_equal(ml, truth)
+    np.testing.assert_array_equal(r["s_hat"], truth)
+    re, im = O.map_back_qpsk(r["s_hat"])
+    np.testing.assert_array_equal(re, w["bits_re"][:, 1:])
+    np.testing.assert_array_equal(im, w["bits_im"][:, 1:])
+
+
 def test_T_structure_and_preconditioning():
     """T symmetric, PSD (MIMO) / NSD (JED); T~ has a +-1 diagonal and D^2 = |diag T|
     (Sec. III-C)."""
