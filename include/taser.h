@@ -45,7 +45,9 @@ typedef enum {
 typedef enum {
     TASER_MIMO_BPSK = 0,     /* N = U + 1,  H complex64 [batch][B][U], y [batch][B]      */
     TASER_MIMO_QPSK = 1,     /* N = 2U + 1, same inputs                                  */
-    TASER_SIMO_JED_BPSK = 2  /* N = K,      Y complex64 [batch][B][K], slot 0 = +1 pilot */
+    TASER_SIMO_JED_BPSK = 2, /* N = K,      Y complex64 [batch][B][K], slot 0 = +1 pilot */
+    TASER_SIMO_JED_QPSK = 3  /* N = 2K - 1, Y complex64 [batch][B][K], slot 0 = (1+j)/sqrt2
+                                pilot; data slots use the effective Y_r/sqrt2 (Sec. II-B) */
 } taser_problem;
 
 /* Arithmetic of the iterations.  For the first three the triangular product L~ T^
@@ -119,8 +121,10 @@ const char* taser_last_error(void);
  *   flags     out, uint32 [batch] (overwritten with ZERO_DIAG / NONFINITE bits), or NULL.
  *
  * QPSK symbols are taken as (+-1 +-j)/sqrt2: T is built from the effective channel
- * H/sqrt2 so that the relaxed vector lies in {+-1}^N.  For JED the pilot column is
- * moved to the last index, so decisions 0..N-2 are slots 1..K-1.
+ * H/sqrt2 (or Y_r/sqrt2) so that the relaxed vector lies in {+-1}^N.  For JED the pilot
+ * column is moved to the last index, so decisions 0..N-2 are slots 1..K-1 (BPSK), or
+ * the real parts of slots 1..K-1 followed by their imaginary parts (QPSK, pilot
+ * s_0 = (1+j)/sqrt2).
  * ||T~||_2 is the largest |eigenvalue|, from an FP32 Householder tridiagonalisation
  * and Sturm-count multisection (not a power iteration, which converges too slowly on
  * MU-MIMO matrices with nearly equal top eigenvalues).
@@ -143,6 +147,7 @@ taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K,
  *               TASER_MIMO_QPSK      the real form of a complex Hermitian (U+1) x (U+1)
  *                                    matrix with Im(last) deleted (N = 2U + 1), as built by
  *                                    taser_build_T; ||T~|| is computed on that matrix;
+ *               TASER_SIMO_JED_QPSK  the same form, negative semidefinite (N = 2K - 1);
  *               TASER_GENERIC_SYMMETRIC  nothing known.
  *   tau       out float [batch]; spec_norm out float [batch] or NULL.
  */

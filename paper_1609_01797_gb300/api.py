@@ -7,9 +7,10 @@ import numpy as np
 
 from ._native import UnevenTuning, check, lib
 
-BPSK, QPSK, JED_BPSK = 0, 1, 2
-KINDS = {"mimo_bpsk": BPSK, "mimo_qpsk": QPSK, "jed_bpsk": JED_BPSK, BPSK: BPSK, QPSK: QPSK,
-         JED_BPSK: JED_BPSK}
+BPSK, QPSK, JED_BPSK, JED_QPSK = 0, 1, 2, 3
+KINDS = {"mimo_bpsk": BPSK, "mimo_qpsk": QPSK, "jed_bpsk": JED_BPSK, "jed_qpsk": JED_QPSK, BPSK: BPSK, QPSK: QPSK,
+         JED_BPSK: JED_BPSK, JED_QPSK: JED_QPSK}
+JED_KINDS = (JED_BPSK, JED_QPSK)
 PRECISIONS = {"fp32": 0, "bf16_tc": 1, "fp16_tc": 2, "fixed14": 3}
 LNN_MODES = {"fixed": 0, "literal": 1}
 
@@ -44,7 +45,7 @@ def build_T(kind, H_or_Y, y=None, alpha=0.5, out=None, stream=None, with_tau=Tru
     k = KINDS[kind]
     X = _dev(H_or_Y, torch.complex64, "H_or_Y")
     n, B, M = X.shape
-    if k != JED_BPSK:
+    if k not in JED_KINDS:
         _dev(y, torch.complex64, "y")
         if tuple(y.shape) != (n, B):
             raise ValueError("y must have shape [n, B]")
@@ -56,7 +57,7 @@ def build_T(kind, H_or_Y, y=None, alpha=0.5, out=None, stream=None, with_tau=Tru
                "tau": torch.empty((n,), device=dev, dtype=torch.float32),
                "spec_norm": torch.empty((n,), device=dev, dtype=torch.float32),
                "flags": torch.zeros((n,), device=dev, dtype=torch.int32)}
-    st = lib().taser_build_T(k, n, B, M, _ptr(X), _ptr(y if k != JED_BPSK else None), float(alpha),
+    st = lib().taser_build_T(k, n, B, M, _ptr(X), _ptr(y if k not in JED_KINDS else None), float(alpha),
                              _ptr(out["T_tilde"]), _ptr(out["D"]), _ptr(out["tau"] if with_tau else None),
                              _ptr(out.get("spec_norm")), _ptr(out.get("flags")), _stream(stream))
     check(st, "taser_build_T")
@@ -107,11 +108,11 @@ def run_host(kind, H_or_Y, y, alpha, t_max, precision, workspace, s_hat, flags=N
     `workspace` is a uint8 CUDA tensor of at least host_workspace_bytes(...) bytes."""
     k = KINDS[kind]
     n, B, M = H_or_Y.shape
-    for name, t in (("H_or_Y", H_or_Y), ("s_hat", s_hat)) + ((("y", y),) if k != JED_BPSK else ()):
+    for name, t in (("H_or_Y", H_or_Y), ("s_hat", s_hat)) + ((("y", y),) if k not in JED_KINDS else ()):
         if t.is_cuda or not t.is_contiguous():
             raise ValueError("%s must be a contiguous host tensor" % name)
     _dev(workspace, torch.uint8, "workspace")
-    st = lib().taser_run_host(k, n, B, M, _ptr(H_or_Y), _ptr(y if k != JED_BPSK else None), float(alpha),
+    st = lib().taser_run_host(k, n, B, M, _ptr(H_or_Y), _ptr(y if k not in JED_KINDS else None), float(alpha),
                               int(t_max), PRECISIONS[precision], LNN_MODES[lnn_mode], _ptr(workspace),
                               workspace.numel(), _ptr(s_hat), _ptr(flags), _stream(stream))
     check(st, "taser_run_host")
@@ -122,10 +123,10 @@ def run_host_static(kind, H_or_Y, y, alpha, t_max, precision, s_hat, flags=None,
     library's static device scratch (a batch must fit in it; see include/taser.h)."""
     k = KINDS[kind]
     n, B, M = H_or_Y.shape
-    for name, t in (("H_or_Y", H_or_Y), ("s_hat", s_hat)) + ((("y", y),) if k != JED_BPSK else ()):
+    for name, t in (("H_or_Y", H_or_Y), ("s_hat", s_hat)) + ((("y", y),) if k not in JED_KINDS else ()):
         if t.is_cuda or not t.is_contiguous():
             raise ValueError("%s must be a contiguous host tensor" % name)
-    st = lib().taser_run_host_static(k, n, B, M, _ptr(H_or_Y), _ptr(y if k != JED_BPSK else None), float(alpha),
+    st = lib().taser_run_host_static(k, n, B, M, _ptr(H_or_Y), _ptr(y if k not in JED_KINDS else None), float(alpha),
                                      int(t_max), PRECISIONS[precision], LNN_MODES[lnn_mode], _ptr(s_hat),
                                      _ptr(flags), _stream(stream))
     check(st, "taser_run_host_static")

@@ -80,7 +80,7 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   // Padding columns (2P .. 2MP-3 and >= 2MP) stay zero for the whole Gram phase.
   for (int i = lane; i < C::WARP_FLOATS / 4; i += 32) reinterpret_cast<float4*>(Ws)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   __syncwarp();
-  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  const bool jed = kind == TASER_SIMO_JED_BPSK || kind == TASER_SIMO_JED_QPSK;
   const int src_cols = jed ? P + 1 : P;                 // complex columns per antenna row
   const float2* Xi = X + inst * (int64_t)B * src_cols;
   const float2* yi = jed ? nullptr : yv + inst * (int64_t)B;
@@ -193,7 +193,8 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   const bool holder = (g & 1) == 0;
   // Complex column p -> real indices of T: (ire, iim, kind of column) with the augmented
   // column last.  QPSK user p: real p and U + p; BPSK / JED data column p: real p.
-  const bool qpsk = kind == TASER_MIMO_QPSK;
+  const bool qpsk = kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_QPSK;
+  const bool jq = kind == TASER_SIMO_JED_QPSK;
   float* Dc = Ws + C::WARP_FLOATS - 2 * 72;   // D per complex column
   float* rDc = Dc + 72;                       // 1 / D per complex column
   float* Ts = Ws;                             // N x N staging of T~ (reuses the buffers)
@@ -229,7 +230,7 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   // Off-diagonal and diagonal entries of T~ into the staging tile.
   const int NU = P;                   // users / data columns
   const int Nr = N;
-  const float dsg = kind == TASER_SIMO_JED_BPSK ? -1.f : 1.f;   // sign of T_aa
+  const float dsg = jed ? -1.f : 1.f;   // sign of T_aa
 #pragma unroll
   for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -262,16 +263,20 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
           Ts[ap * Nr + aq] = v;
           Ts[aq * Nr + ap] = v;
         } else if (qa) {
-          // user p with the augmented column: -c [Re z; Im z]
+          // user p with the augmented column: -c [Re z; Im z].  JED QPSK: the pilot column
+          // is y_0 s_0 with s_0 = (1 + j)/sqrt2, so z = s_0 (Y_r^H y_0) (and A = [Hbar, +ybar]
+          // with T = -A^T A gives the same sign as MIMO's A = [Hbar, -ybar], T = A^T A).
           const float c = 0.70710678118654752f;
-          const float vr = -c * re * sc, vi = -c * im * sc;
+          const float zr = jq ? c * (re - im) : re, zi = jq ? c * (re + im) : im;
+          const float vr = -c * zr * sc, vi = -c * zi * sc;
           Ts[p * Nr + aq] = vr;
           Ts[aq * Nr + p] = vr;
           Ts[(NU + p) * Nr + aq] = vi;
           Ts[aq * Nr + (NU + p)] = vi;
         } else {
-          // users p < q: [[Re G, -Im G], [Im G, Re G]] / 2
-          const float vr = 0.5f * re * sc, vi = 0.5f * im * sc;
+          // users p < q: [[Re G, -Im G], [Im G, Re G]] / 2 (negated for JED: T = -A^T A)
+          const float h = jq ? -0.5f : 0.5f;
+          const float vr = h * re * sc, vi = h * im * sc;
           Ts[p * Nr + q] = vr;
           Ts[q * Nr + p] = vr;
           Ts[(NU + p) * Nr + (NU + q)] = vr;

@@ -259,8 +259,8 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * 
 
 template <int UV>
 __global__ void __launch_bounds__(128)
-spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float alpha, float* __restrict__ tau,
-                     float* __restrict__ nrm_out) {
+spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float sg, float alpha,
+                     float* __restrict__ tau, float* __restrict__ nrm_out) {
   using C = HermCfg<UV>;
   constexpr int NP = C::NP, VB = C::VB, G = C::G;
   __shared__ __align__(16) float sm[C::IPC * C::INST_FLOATS];
@@ -275,7 +275,9 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
   float* eb2 = db + VB;
   const int N = 2 * U + 1;
   const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
-  auto t = [&](int a, int b) -> float { return active ? T[(int64_t)a * N + b] : 0.f; };
+  // sg = -1 reads the negative semidefinite JED form as its (positive semidefinite)
+  // negation; the norm is the same.
+  auto t = [&](int a, int b) -> float { return active ? sg * T[(int64_t)a * N + b] : 0.f; };
 
   // col[j] = M~[j][c], c = gl + 1; index UV is the augmented coordinate.
   const int c = gl + 1;
@@ -422,19 +424,21 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
 }
 
 template <int UV>
-static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
-                               cudaStream_t st) {
+static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, float sg, float alpha, float* tau,
+                               float* nrm, cudaStream_t st) {
   const int64_t blocks = (batch + HermCfg<UV>::IPC - 1) / HermCfg<UV>::IPC;
-  spectral_herm_kernel<UV><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+  spectral_herm_kernel<UV><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, sg, alpha, tau, nrm);
   return cudaGetLastError();
 }
 
-// ||T~||_2 of QPSK matrices (N = 2U + 1) through the complex form; U <= 32.
-cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
+// ||T~||_2 of QPSK matrices (N = 2U + 1) through the complex form; U <= 32.  sign = +1 for
+// a positive semidefinite T~ (MIMO), -1 for a negative semidefinite one (JED).
+cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, int sign, float alpha, float* tau, float* nrm,
                           cudaStream_t st) {
-  if (U + 1 <= 9) return launch_herm<8>(batch, U, Tt, alpha, tau, nrm, st);
-  if (U + 1 <= 17) return launch_herm<16>(batch, U, Tt, alpha, tau, nrm, st);
-  return launch_herm<32>(batch, U, Tt, alpha, tau, nrm, st);
+  const float sg = sign < 0 ? -1.f : 1.f;
+  if (U + 1 <= 9) return launch_herm<8>(batch, U, Tt, sg, alpha, tau, nrm, st);
+  if (U + 1 <= 17) return launch_herm<16>(batch, U, Tt, sg, alpha, tau, nrm, st);
+  return launch_herm<32>(batch, U, Tt, sg, alpha, tau, nrm, st);
 }
 
 template <int NV>

@@ -10,7 +10,7 @@ cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X,
                     float* D, uint32_t* flags, cudaStream_t st);
 cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, int hint, float* tau, float* nrm,
                      cudaStream_t st);
-cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, float alpha, float* tau, float* nrm,
+cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, int sign, float alpha, float* tau, float* nrm,
                           cudaStream_t st);
 cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,
                      const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
@@ -73,6 +73,7 @@ int taser_problem_size(int kind, int U_or_K) {
     case TASER_MIMO_BPSK: return U_or_K + 1;
     case TASER_MIMO_QPSK: return 2 * U_or_K + 1;
     case TASER_SIMO_JED_BPSK: return U_or_K;
+    case TASER_SIMO_JED_QPSK: return U_or_K >= 2 ? 2 * U_or_K - 1 : -1;
     default: return -1;
   }
 }
@@ -94,12 +95,13 @@ const char* taser_last_error(void) { return g_err; }
 taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y, const void* y,
                            float alpha, float* T_tilde, float* D, float* tau, float* spec_norm, uint32_t* flags,
                            void* stream) {
-  TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK,
+  TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK ||
+                    kind == TASER_SIMO_JED_QPSK,
                 "unknown problem kind %d", kind);
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(B >= 1, "B must be >= 1 (got %d)", B);
   TASER_REQUIRE(alpha > 0.f && alpha < 1.f, "alpha must lie in (0, 1) (got %g)", (double)alpha);
-  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  const bool jed = kind == TASER_SIMO_JED_BPSK || kind == TASER_SIMO_JED_QPSK;
   if (jed) {
     TASER_REQUIRE(U_or_K >= 2 && U_or_K <= 33, "JED needs 2 <= K <= 33 (got %d)", U_or_K);
     TASER_REQUIRE(y == nullptr, "y must be NULL for JED");
@@ -131,17 +133,21 @@ taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int str
   TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
   TASER_REQUIRE(alpha > 0.f && alpha < 1.f, "alpha must lie in (0, 1) (got %g)", (double)alpha);
   TASER_REQUIRE(structure == TASER_GENERIC_SYMMETRIC || structure == TASER_MIMO_BPSK ||
-                    structure == TASER_MIMO_QPSK || structure == TASER_SIMO_JED_BPSK,
+                    structure == TASER_MIMO_QPSK || structure == TASER_SIMO_JED_BPSK ||
+                    structure == TASER_SIMO_JED_QPSK,
                 "unknown structure %d", structure);
-  TASER_REQUIRE(structure != TASER_MIMO_QPSK || N % 2 == 1, "QPSK structure needs odd N = 2U + 1 (got %d)", N);
+  TASER_REQUIRE((structure != TASER_MIMO_QPSK && structure != TASER_SIMO_JED_QPSK) || N % 2 == 1,
+                "QPSK structure needs odd N (got %d)", N);
   if (batch == 0) return ok();
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(tau, "tau");
   if (spec_norm != nullptr) TASER_REQUIRE(aligned16(spec_norm), "spec_norm must be 16-byte aligned");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (structure == TASER_MIMO_QPSK) {
+  if (structure == TASER_MIMO_QPSK || structure == TASER_SIMO_JED_QPSK) {
     // ||T~||_2 equals the norm of its (U+1) x (U+1) complex Hermitian form.
-    return from_cuda(taser::spectral_qpsk(batch, (N - 1) / 2, T_tilde, alpha, tau, spec_norm, st), "spectral_qpsk");
+    const int sign = structure == TASER_MIMO_QPSK ? 1 : -1;
+    return from_cuda(taser::spectral_qpsk(batch, (N - 1) / 2, T_tilde, sign, alpha, tau, spec_norm, st),
+                     "spectral_qpsk");
   }
   // T = A^T A is positive semidefinite (MIMO), T = -A^T A negative semidefinite (JED).
   const int hint = structure == TASER_MIMO_BPSK ? 1 : (structure == TASER_SIMO_JED_BPSK ? -1 : 0);
@@ -190,7 +196,7 @@ size_t up256(size_t v) { return (v + 255) & ~size_t(255); }
 bool host_layout(int kind, int64_t batch, int B, int M, HostLayout& L) {
   const int N = taser_problem_size(kind, M);
   if (N < 2 || batch < 0 || B < 1) return false;
-  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  const bool jed = kind == TASER_SIMO_JED_BPSK || kind == TASER_SIMO_JED_QPSK;
   size_t off = 0;
   L.x = off; off = up256(off + size_t(batch) * B * M * 8);
   L.y = off; off = up256(off + (jed ? 0 : size_t(batch) * B * 8));
@@ -215,14 +221,15 @@ size_t taser_host_workspace_bytes(int kind, int64_t batch, int B, int U_or_K) {
 taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y, const void* y,
                             float alpha, int t_max, int precision, int lnn_mode, void* workspace,
                             size_t workspace_bytes, int8_t* s_hat, uint32_t* flags, void* stream) {
-  TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK,
+  TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK ||
+                    kind == TASER_SIMO_JED_QPSK,
                 "unknown problem kind %d", kind);
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
   HostLayout L;
   TASER_REQUIRE(host_layout(kind, batch, B, U_or_K, L), "invalid problem shape");
   if (batch == 0) return ok();
-  const bool jed = kind == TASER_SIMO_JED_BPSK;
+  const bool jed = kind == TASER_SIMO_JED_BPSK || kind == TASER_SIMO_JED_QPSK;
   TASER_REQUIRE(H_or_Y != nullptr, "H_or_Y must not be NULL");
   TASER_REQUIRE(jed || y != nullptr, "y must not be NULL");
   TASER_REQUIRE(s_hat != nullptr, "s_hat must not be NULL");

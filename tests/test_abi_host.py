@@ -38,6 +38,8 @@ def test_problem_size(lib):
     assert lib.taser_problem_size(0, 8) == 9
     assert lib.taser_problem_size(1, 16) == 33
     assert lib.taser_problem_size(2, 16) == 16
+    assert lib.taser_problem_size(3, 16) == 31         # QPSK JED: 2K - 1
+    assert lib.taser_problem_size(3, 1) == -1
     assert lib.taser_problem_size(7, 16) == -1
     assert lib.taser_problem_size(1, 0) == -1
 
@@ -85,7 +87,8 @@ def _build(lib, **kw):
 
 @pytest.mark.parametrize("kw", [dict(kind=5), dict(B=0), dict(U=0), dict(U=33), dict(alpha=0.0),
                                 dict(alpha=1.0), dict(X=None), dict(y=None), dict(kind=2, U=16),
-                                dict(kind=2, U=34, y=None), dict(kind=2, U=1, y=None), dict(T=P4),
+                                dict(kind=2, U=34, y=None), dict(kind=2, U=1, y=None), dict(kind=3, U=16),
+                                dict(kind=3, U=34, y=None), dict(kind=3, U=1, y=None), dict(T=P4),
                                 dict(nrm=P4), dict(batch=-3)])
 def test_build_rejects_invalid_arguments(lib, kw):
     assert _build(lib, **kw) == 1
