@@ -40,8 +40,9 @@ def parse_args():
     ap.add_argument("--instances", type=int, default=65536, help="instances per GPU per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=32768, help="instances timed on the CPU oracle")
-    ap.add_argument("--workload", choices=["qpsk128x16", "uneven"], default="qpsk128x16",
-                    help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20} (not the headline)")
+    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff"], default="qpsk128x16",
+                    help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20}; tradeoff: SNR "
+                         "for 1%% VER vs throughput over t_max = 1..20 for 32x32 BPSK/QPSK (neither is the headline)")
     return ap.parse_args()
 
 
@@ -67,7 +68,7 @@ def spectral_flops_per_instance(u):
 
 
 KERNEL_SOURCES = {"build": "build_T.cu", "spectral": "spectral.cu", "detect_tc": "detect_tc.cu",
-                  "detect_fp32": "detect_fp32.cu"}
+                  "detect_fp32": "detect_fp32.cu", "detect_fx14": "detect_fx14.cu"}
 
 
 def measured_traffic():
@@ -302,12 +303,123 @@ def run_uneven(args):
     return 0
 
 
+def _device_mimo(n, b, u, snr_db, constellation, gen, dev):
+    """Seeded MU-MIMO instances drawn on the GPU with the recipe of synth.make_mimo:
+    H i.i.d. CN(0, 1), unit-energy BPSK / QPSK symbols, noise CN(0, N0), N0 = U / SNR."""
+    import torch
+    half = 0.5 ** 0.5
+
+    def cn(shape):
+        return torch.complex(torch.randn(shape, generator=gen, device=dev),
+                             torch.randn(shape, generator=gen, device=dev)) * half
+
+    H = cn((n, b, u))
+    bre = torch.randint(0, 2, (n, u), generator=gen, device=dev, dtype=torch.int8) * 2 - 1
+    if constellation == "qpsk":
+        bim = torch.randint(0, 2, (n, u), generator=gen, device=dev, dtype=torch.int8) * 2 - 1
+        s = torch.complex(bre.float(), bim.float()) * half
+        truth = torch.cat([bre, bim], dim=1)
+    else:
+        s = torch.complex(bre.float(), torch.zeros_like(bre, dtype=torch.float32))
+        truth = bre
+    n0 = u / 10.0 ** (snr_db / 10.0)
+    y = torch.einsum("nbu,nu->nb", H, s) + cn((n, b)) * n0 ** 0.5
+    return H.contiguous(), y.contiguous(), truth
+
+
+def run_tradeoff(args):
+    """Throughput vs the SNR needed for 1% VER as t_max goes from 1 to 20, for 32-user
+    systems (B = 32, U = 32, BPSK N = 33 and QPSK N = 65): the GPU counterpart of the
+    paper's trade-off figures (Sec. V-A).  alpha is the paper's system-dependent tuning
+    parameter (Sec. III-B): per t_max the best alpha of a small grid is reported.  VER per
+    SNR point on fresh instances (65,536 by default), 1 dB steps, the 1% crossing
+    interpolated in log10(VER); throughput of taser_detect alone (as the paper's FPGA
+    figures, which exclude the preprocessing) at each t_max."""
+    import torch
+    import paper_1609_01797_gb300 as taser
+    dev = torch.device("cuda", 0)
+    n = args.instances
+    t_list = list(range(1, 21))
+    alphas = (0.5, 0.7, 0.9, 0.99)
+    precisions = ("bf16_tc", "fp32")
+    snrs = np.arange(0.0, 41.0, 1.0)
+
+    def crossing(pts):
+        for (s0, v0), (s1, v1) in zip(pts, pts[1:]):
+            if v0 >= 0.01 > v1:
+                if v1 <= 0:
+                    return s1
+                l0, l1 = np.log10(v0), np.log10(v1)
+                return s0 + (s1 - s0) * (l0 + 2.0) / (l0 - l1)
+        return None
+
+    table = {}
+    for const in ("bpsk", "qpsk"):
+        u = b = 32
+        kind = "mimo_" + const
+        nn = 2 * u + 1 if const == "qpsk" else u + 1
+        bits = u * (2 if const == "qpsk" else 1)
+        gen = torch.Generator(device=dev)
+        gen.manual_seed(17 if const == "bpsk" else 18)
+        keys = [(p, a) for p in precisions for a in alphas]
+        ver = {(p, a, t): [] for p, a in keys for t in t_list}
+        done = {k: False for k in keys}
+        tau = torch.empty(n, device=dev)
+        for snr in snrs:
+            H, y, truth = _device_mimo(n, b, u, float(snr), const, gen, dev)
+            out = taser.build_T(kind, H, y, 0.5, with_tau=False)
+            for a in alphas:
+                taser.step_size(out["T_tilde"], a, structure=kind, tau=tau)
+                for p in precisions:
+                    if done[(p, a)]:
+                        continue
+                    for t in t_list:
+                        s, _, _ = taser.detect(out["T_tilde"], out["D"], tau, t, p, want_L=False)
+                        ver[(p, a, t)].append((float(snr), (s != truth).any(dim=1).float().mean().item()))
+                    done[(p, a)] = all(ver[(p, a, t)][-1][1] < 0.005 for t in t_list)
+            if all(done.values()):
+                break
+        rows = []
+        for t in t_list:
+            row = {"t_max": t}
+            for p in precisions:
+                best = None
+                for a in alphas:
+                    req = crossing(ver[(p, a, t)])
+                    if req is not None and (best is None or req < best[0]):
+                        best = (req, a)
+                row["snr_1pct_ver_db_" + p] = None if best is None else best[0]
+                row["alpha_" + p] = None if best is None else best[1]
+                for _ in range(3):
+                    taser.detect(out["T_tilde"], out["D"], tau, t, p, want_L=False)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize()
+                e0.record()
+                for _ in range(10):
+                    taser.detect(out["T_tilde"], out["D"], tau, t, p, want_L=False)
+                e1.record()
+                torch.cuda.synchronize()
+                det = n / (e0.elapsed_time(e1) / 10 * 1e-3)
+                row["detect_det_per_s_" + p] = det
+                row["detect_mbit_per_s_" + p] = det * bits / 1e6
+            rows.append(row)
+        table[const] = {"B": b, "U": u, "N": nn, "rows": rows}
+    print(json.dumps({"metric": "SNR for 1% VER vs detection throughput over t_max = 1..20, 32x32 MU-MIMO",
+                      "unit": "dB / detections/s", "n_gpus": 1, "dtype": "bf16 and f32", "data": "synthetic",
+                      "config": {"workload": "tradeoff_32x32_bpsk_qpsk_tmax1-20", "instances_per_snr": n,
+                                 "snr_grid_db": "0..40 step 1 (stops once every t_max is below 0.5% VER)",
+                                 "alpha_grid": list(alphas)}, "table": table}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "uneven":
         return run_uneven(args)
+    if args.workload == "tradeoff":
+        return run_tradeoff(args)
 
     import torch
     import torch.distributed as dist
@@ -377,7 +489,7 @@ def main():
     sampler = ClockSampler(local)
     sampler.start()
     paths = {}
-    for precision in ("bf16_tc", "fp32", "fp16_tc"):
+    for precision in ("bf16_tc", "fp32", "fp16_tc", "fixed14"):
         paths[precision] = run_path(precision, args.steps, args.warmup)
     clocks = sampler.stop()
 

@@ -257,10 +257,10 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * 
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
 }
 
-template <int UV>
+template <int UV, bool NEG>
 __global__ void __launch_bounds__(128)
-spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float sg, float alpha,
-                     float* __restrict__ tau, float* __restrict__ nrm_out) {
+spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float alpha, float* __restrict__ tau,
+                     float* __restrict__ nrm_out) {
   using C = HermCfg<UV>;
   constexpr int NP = C::NP, VB = C::VB, G = C::G;
   __shared__ __align__(16) float sm[C::IPC * C::INST_FLOATS];
@@ -275,9 +275,12 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float s
   float* eb2 = db + VB;
   const int N = 2 * U + 1;
   const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
-  // sg = -1 reads the negative semidefinite JED form as its (positive semidefinite)
-  // negation; the norm is the same.
-  auto t = [&](int a, int b) -> float { return active ? sg * T[(int64_t)a * N + b] : 0.f; };
+  // NEG reads the negative semidefinite JED form as its (positive semidefinite) negation;
+  // the norm is the same.
+  auto t = [&](int a, int b) -> float {
+    const float v = active ? T[(int64_t)a * N + b] : 0.f;
+    return NEG ? -v : v;
+  };
 
   // col[j] = M~[j][c], c = gl + 1; index UV is the augmented coordinate.
   const int c = gl + 1;
@@ -424,10 +427,11 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float s
 }
 
 template <int UV>
-static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, float sg, float alpha, float* tau,
+static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, bool neg, float alpha, float* tau,
                                float* nrm, cudaStream_t st) {
   const int64_t blocks = (batch + HermCfg<UV>::IPC - 1) / HermCfg<UV>::IPC;
-  spectral_herm_kernel<UV><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, sg, alpha, tau, nrm);
+  if (neg) spectral_herm_kernel<UV, true><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+  else spectral_herm_kernel<UV, false><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
   return cudaGetLastError();
 }
 
@@ -435,10 +439,10 @@ static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, float sg, 
 // a positive semidefinite T~ (MIMO), -1 for a negative semidefinite one (JED).
 cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, int sign, float alpha, float* tau, float* nrm,
                           cudaStream_t st) {
-  const float sg = sign < 0 ? -1.f : 1.f;
-  if (U + 1 <= 9) return launch_herm<8>(batch, U, Tt, sg, alpha, tau, nrm, st);
-  if (U + 1 <= 17) return launch_herm<16>(batch, U, Tt, sg, alpha, tau, nrm, st);
-  return launch_herm<32>(batch, U, Tt, sg, alpha, tau, nrm, st);
+  const bool neg = sign < 0;
+  if (U + 1 <= 9) return launch_herm<8>(batch, U, Tt, neg, alpha, tau, nrm, st);
+  if (U + 1 <= 17) return launch_herm<16>(batch, U, Tt, neg, alpha, tau, nrm, st);
+  return launch_herm<32>(batch, U, Tt, neg, alpha, tau, nrm, st);
 }
 
 template <int NV>

@@ -7,9 +7,9 @@ consume the same inputs.
 Models (Sec. II-A and II-B of the paper):
   * MU-MIMO uplink  y = H s + n,  H i.i.d. CN(0, 1), n i.i.d. CN(0, N0),
     N0 = U / SNR with unit-energy symbols (BPSK +-1, QPSK (+-1 +-j)/sqrt 2).
-  * SIMO block fading  Y = h s^T + N over K slots, h ~ CN(0, I_B) constant over the
-    slots, s_0 = +1 a known pilot, BPSK data, N0 = 1 / SNR per receive antenna.
-    For BPSK s^H = s^T, so the paper's conjugate makes no difference here.
+  * SIMO block fading  Y = h s^H + N over K slots, h ~ CN(0, I_B) constant over the
+    slots, slot 0 a known pilot (+1 for BPSK, (1 + j)/sqrt2 for QPSK), N0 = 1 / SNR per
+    receive antenna.
 
 Arrays are complex64 (what the C-ABI consumes). Bits are returned as +-1 int8.
 """
