@@ -15,7 +15,8 @@
 // One warp per instance, lane j owns column j (and j + 32 at N > 33).  Its column of T^
 // lives in registers; L~ lives in shared memory, one int per entry, and its rows are
 // broadcast to the lanes (one LDS.128 feeds four IMADs).  Products are below 2^26, so
-// 16 of them are summed in int32 before each 64-bit accumulate: exact for every input.
+// 16 of them (four partial sums of four) are summed in int32 before each 64-bit
+// accumulate: exact for every input.
 #include <math.h>
 
 #include "common.cuh"
@@ -105,6 +106,29 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
   }
   __syncwarp();
 
+  // acc[c] += sum over the KC columns k of chunk ch of L~_ik T^_kj, with four independent
+  // int32 partial sums (each at most 4 products below 2^26: exact) for instruction-level
+  // parallelism, then one 64-bit accumulate.
+  auto chunk_mac = [&](const int* lrow, int ch, long long (&acc)[CPL]) {
+    int p0[CPL], p1[CPL], p2[CPL], p3[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) p0[c] = p1[c] = p2[c] = p3[c] = 0;
+#pragma unroll
+    for (int kk = 0; kk < KC; kk += 4) {
+      const int4 l4 = *reinterpret_cast<const int4*>(lrow + kk);
+      const int k0 = ch * KC + kk;
+#pragma unroll
+      for (int c = 0; c < CPL; ++c) {
+        p0[c] += l4.x * tc[c][k0];
+        p1[c] += l4.y * tc[c][k0 + 1];
+        p2[c] += l4.z * tc[c][k0 + 2];
+        p3[c] += l4.w * tc[c][k0 + 3];
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) acc[c] += (long long)((p0[c] + p1[c]) + (p2[c] + p3[c]));
+  };
+
   for (int t = 0; t < jb.t_max; ++t) {
     long long x[CPL];
 #pragma unroll
@@ -119,20 +143,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
 #pragma unroll
       for (int ch = 0; ch < NCH; ++ch) {
         if (ch * KC > i) break;                    // L~_ik = 0 for k > i
-        int s32[CPL];
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) s32[c] = 0;
-#pragma unroll
-        for (int kk = 0; kk < KC; kk += 4) {
-          const int4 l4 = *reinterpret_cast<const int4*>(row + ch * KC + kk);
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            const int k0 = ch * KC + kk;
-            s32[c] += l4.x * tc[c][k0] + l4.y * tc[c][k0 + 1] + l4.z * tc[c][k0 + 2] + l4.w * tc[c][k0 + 3];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[c] += s32[c];
+        chunk_mac(row + ch * KC, ch, acc);
       }
       int v[CPL];
 #pragma unroll
@@ -157,22 +168,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
 #pragma unroll
       for (int c = 0; c < CPL; ++c) acc[c] = 0;
 #pragma unroll
-      for (int ch = 0; ch < NCH; ++ch) {
-        int s32[CPL];
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) s32[c] = 0;
-#pragma unroll
-        for (int kk = 0; kk < KC; kk += 4) {
-          const int4 l4 = *reinterpret_cast<const int4*>(rowN + ch * KC + kk);
-#pragma unroll
-          for (int c = 0; c < CPL; ++c) {
-            const int k0 = ch * KC + kk;
-            s32[c] += l4.x * tc[c][k0] + l4.y * tc[c][k0 + 1] + l4.z * tc[c][k0 + 2] + l4.w * tc[c][k0 + 3];
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < CPL; ++c) acc[c] += s32[c];
-      }
+      for (int ch = 0; ch < NCH; ++ch) chunk_mac(rowN + ch * KC, ch, acc);
       // V_NN (for the flag only): L~_NN 2^14 - sum_k L~_Nk T^_kN - (L~_NN T^_NN) 2^2.
       long long part = 0;
 #pragma unroll
@@ -255,7 +251,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
 
 // Persistent kernel: dense instances at a fixed stride, or items popped from a bucket queue.
 template <int NB, bool QUEUE>
-__global__ void __launch_bounds__(128, NB == 64 ? 1 : 2)
+__global__ void __launch_bounds__(128, NB == 64 ? 1 : 4)
 detect_fx14_kernel(int64_t batch, int N, int t_max, const float* __restrict__ Tt, const float* __restrict__ Dg,
                    const float* __restrict__ tau, float* __restrict__ L, int8_t* __restrict__ s,
                    uint32_t* __restrict__ flags, Queue q, const float* __restrict__ T_pool,

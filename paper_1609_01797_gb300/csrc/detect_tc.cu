@@ -77,6 +77,24 @@ __device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
     f2unpack(_y, arr[e], arr[e + 1]);           \
   } while (0)
 
+// The same mma for the m-tile of row N, whose rows g + 8 are identically zero: their
+// accumulators are fed zeros and discarded, so they occupy no registers across iterations.
+template <bool FP16>
+__device__ __forceinline__ void mma16816_top(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  float z2 = 0.f, z3 = 0.f;
+  if constexpr (FP16) {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(z2), "+f"(z3)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  } else {
+    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(z2), "+f"(z3)
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+  }
+}
+
 // Tile bookkeeping for bucket NB (16 or 32).
 template <int NB>
 struct TcCfg {
@@ -226,14 +244,11 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int c = 8 * nt + 2 * tq + p;
-        tN[nt][p] = c < N - 1 ? m2tau * T[(N - 1) * N + c] : 0.f;
+        tN[nt][p] = (g == 0 && c < N - 1) ? m2tau * T[(N - 1) * N + c] : 0.f;
       }
-    uint64_t tN2[NT], tNg2[NT];   // packed pairs; tNg2 is zero off the lanes holding row N
+    uint64_t tN2[NT];   // packed pairs (zero off the lanes g == 0 that hold row N)
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) {
-      tN2[nt] = f2pack(tN[nt][0], tN[nt][1]);
-      tNg2[nt] = g == 0 ? tN2[nt] : 0ull;
-    }
+    for (int nt = 0; nt < NT; ++nt) tN2[nt] = f2pack(tN[nt][0], tN[nt][1]);
     const float tnNN = m2tau * T[(N - 1) * N + (N - 1)];
     const float DN = Di[N - 1];
     // After the column-sum reduction this lane owns column cown.
@@ -298,13 +313,16 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           // k = N term of row N in FP32: L~_NN T^_{N,c}.
           const uint64_t lnn2 = f2pack(LNN, LNN);
 #pragma unroll
-          for (int n = 0; n < NT; ++n) TASER_PAIR_APPLY(acc[M][n], 0, f2fma(lnn2, tNg2[n], _x));
+          for (int n = 0; n < NT; ++n) TASER_PAIR_APPLY(acc[M][n], 0, f2fma(lnn2, tN2[n], _x));
         }
 #pragma unroll
         for (int n = 0; n < NT; ++n) {
           if (!C::has_tile(M, n)) continue;
 #pragma unroll
-          for (int kt = 0; kt <= C::kmax(M); ++kt) mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+          for (int kt = 0; kt <= C::kmax(M); ++kt) {
+            if (M == MT - 1) mma16816_top<FP16>(acc[M][n], a[kt], bf[kt][n]);
+            else mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+          }
         }
       }
       // Keep V lower-triangular inside the diagonal tiles.

@@ -80,7 +80,6 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
   constexpr int MLO = ROLE ? 1 : 0, MHI = ROLE ? 2 : 3;
   constexpr int NLO = 2 * MLO + 2, NHI = 2 * MHI + 2;   // n-tiles of the two row blocks
   constexpr int RN0 = 4 * ROLE;                          // first n-tile of this warp's row-64 half
-  constexpr int NB = 64;
   const int g = lane >> 2, tq = lane & 3;
   const int N = jb.N;
   const float* T = jb.T;
@@ -200,8 +199,8 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
         a[kt][1] = 0u;
         a[kt][3] = 0u;
       }
-#pragma unroll
       const uint64_t lnn2 = p2pack(LNN, LNN);
+#pragma unroll
       for (int n = 0; n < 4; ++n) {
         // k = N term in FP32 (tN is 0 for g != 0)
         p2unpack(p2fma(lnn2, tN2[n], p2pack(rw[n][0], rw[n][1])), rw[n][0], rw[n][1]);

@@ -16,6 +16,7 @@ cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm
 constexpr int kClasses = 64;               // t_max classes per bucket (64 = 64 and more)
 constexpr int kKeys = 4 * kClasses;
 constexpr int kMetaInts = 16;              // start[4], count[4], head[4], spare
+static_assert(kMetaInts * sizeof(int) <= 256, "the queue metadata lives in the 256 bytes after the item list");
 
 __device__ __forceinline__ int bucket_index(int N) {
   const int nv = N - 1;
