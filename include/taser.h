@@ -193,7 +193,12 @@ size_t taser_host_workspace_bytes(int kind, int64_t batch, int B, int U_or_K);
  *                 256-byte aligned, owned by the caller; its contents are scratch.
  *   s_hat, flags  HOST outputs, int8 [batch][N-1] and uint32 [batch] (flags may be NULL).
  * The call returns once the work is enqueued; synchronize `stream` before reading the
- * host outputs.
+ * host outputs.  Batches above 8,192 instances are pipelined in chunks of 8,192: the
+ * host-to-device copies run on a side stream the library creates once per host thread and
+ * device, each chunk's kernels wait for its copy on `stream`, and `stream` orders the whole
+ * call (the side stream first waits for the work already queued on `stream`, and `stream`
+ * waits for every copy), so the call keeps the semantics of one stream-ordered operation,
+ * also under CUDA graph capture.
  */
 taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y,
                             const void* y, float alpha, int t_max, int precision, int lnn_mode,

@@ -189,6 +189,37 @@ taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const floa
 }  // extern "C"
 
 namespace {
+// Side stream (per host thread and device) that carries taser_run_host's host-to-device
+// copies, so chunk k + 1 is in flight while chunk k is detected on the caller's stream.
+// Created on first use and kept for the thread's lifetime.
+struct CopyLane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t fork = nullptr, copied = nullptr;
+};
+cudaError_t copy_lane(CopyLane*& out) {
+  thread_local CopyLane lanes[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  CopyLane& c = lanes[dev];
+  if (c.stream == nullptr) {
+    e = cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c.copied, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      c = CopyLane{};
+      return e;
+    }
+  }
+  out = &c;
+  return cudaSuccess;
+}
+
+// Instances per pipelined chunk of taser_run_host: large enough that every kernel still
+// fills the GPU, small enough that the copy of the first chunk is a small part of the whole.
+constexpr int64_t kHostChunk = 8192;
+
 struct HostLayout {
   size_t x, y, t, d, tau, s, flags, total;
 };
@@ -239,27 +270,50 @@ taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const vo
   const int N = taser_problem_size(kind, U_or_K);
   char* w = static_cast<char*>(workspace);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  cudaError_t e = cudaMemcpyAsync(w + L.x, H_or_Y, size_t(batch) * B * U_or_K * 8, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return from_cuda(e, "copy H_or_Y");
-  if (!jed) {
-    e = cudaMemcpyAsync(w + L.y, y, size_t(batch) * B * 8, cudaMemcpyHostToDevice, st);
-    if (e != cudaSuccess) return from_cuda(e, "copy y");
-  }
+  CopyLane* lane = nullptr;
+  cudaError_t e = copy_lane(lane);
+  if (e != cudaSuccess) return from_cuda(e, "copy stream");
+  // The copies may only start once earlier work on `stream` (which may still read the
+  // workspace) is done: fork the side stream from it.
+  e = cudaEventRecord(lane->fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(lane->stream, lane->fork, 0);
+  if (e != cudaSuccess) return from_cuda(e, "fork copy stream");
+  const size_t xrow = size_t(B) * U_or_K * 8, yrow = size_t(B) * 8;
   float* Tt = reinterpret_cast<float*>(w + L.t);
   float* D = reinterpret_cast<float*>(w + L.d);
   float* tau = reinterpret_cast<float*>(w + L.tau);
   int8_t* s = reinterpret_cast<int8_t*>(w + L.s);
   uint32_t* fl = reinterpret_cast<uint32_t*>(w + L.flags);
-  taser_status rs = taser_build_T(kind, batch, B, U_or_K, w + L.x, jed ? nullptr : w + L.y, alpha, Tt, D, tau,
-                                  nullptr, fl, stream);
-  if (rs != TASER_OK) return rs;
-  rs = taser_detect(batch, N, Tt, D, tau, t_max, precision, lnn_mode, nullptr, s, fl, stream);
-  if (rs != TASER_OK) return rs;
-  e = cudaMemcpyAsync(s_hat, s, size_t(batch) * (N - 1), cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return from_cuda(e, "copy s_hat");
-  if (flags != nullptr) {
-    e = cudaMemcpyAsync(flags, fl, size_t(batch) * 4, cudaMemcpyDeviceToHost, st);
-    if (e != cudaSuccess) return from_cuda(e, "copy flags");
+  for (int64_t c0 = 0; c0 < batch; c0 += kHostChunk) {
+    const int64_t nc = batch - c0 < kHostChunk ? batch - c0 : kHostChunk;
+    char* xk = w + L.x + size_t(c0) * xrow;
+    char* yk = w + L.y + size_t(c0) * yrow;
+    e = cudaMemcpyAsync(xk, static_cast<const char*>(H_or_Y) + size_t(c0) * xrow, size_t(nc) * xrow,
+                        cudaMemcpyHostToDevice, lane->stream);
+    if (e != cudaSuccess) return from_cuda(e, "copy H_or_Y");
+    if (!jed) {
+      e = cudaMemcpyAsync(yk, static_cast<const char*>(y) + size_t(c0) * yrow, size_t(nc) * yrow,
+                          cudaMemcpyHostToDevice, lane->stream);
+      if (e != cudaSuccess) return from_cuda(e, "copy y");
+    }
+    // The event is re-recorded per chunk: each wait binds to the record just before it.
+    e = cudaEventRecord(lane->copied, lane->stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, lane->copied, 0);
+    if (e != cudaSuccess) return from_cuda(e, "join copy stream");
+    float* Tk = Tt + size_t(c0) * N * N;
+    float* Dk = D + size_t(c0) * N;
+    int8_t* sk = s + size_t(c0) * (N - 1);
+    taser_status rs = taser_build_T(kind, nc, B, U_or_K, xk, jed ? nullptr : yk, alpha, Tk, Dk, tau + c0,
+                                    nullptr, fl + c0, stream);
+    if (rs != TASER_OK) return rs;
+    rs = taser_detect(nc, N, Tk, Dk, tau + c0, t_max, precision, lnn_mode, nullptr, sk, fl + c0, stream);
+    if (rs != TASER_OK) return rs;
+    e = cudaMemcpyAsync(s_hat + size_t(c0) * (N - 1), sk, size_t(nc) * (N - 1), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return from_cuda(e, "copy s_hat");
+    if (flags != nullptr) {
+      e = cudaMemcpyAsync(flags + c0, fl + c0, size_t(nc) * 4, cudaMemcpyDeviceToHost, st);
+      if (e != cudaSuccess) return from_cuda(e, "copy flags");
+    }
   }
   return ok();
 }

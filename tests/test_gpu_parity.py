@@ -305,3 +305,28 @@ def test_run_host_matches_device_path(T, kind, B, M, t_max, precision):
     r = O.detect(kind, X, y, ALPHA, t_max)
     m = confident(r["L"], 1e-3 if precision == "fp32" else 5e-2)
     np.testing.assert_array_equal(s_host.numpy()[m], r["s_hat"][m])
+
+
+@pytest.mark.parametrize("kind,B,M,n", [("mimo_bpsk", 32, 8, 20000), ("mimo_qpsk", 64, 8, 16384),
+                                        ("jed_bpsk", 16, 16, 8193)])
+def test_run_host_pipelined_chunks(T, kind, B, M, n):
+    """Batches beyond one 8,192-instance chunk: the copies of later chunks overlap the
+    detection of earlier ones on a side stream; the decisions and flags equal the
+    device-resident calls, also when the caller's stream is not the default stream and
+    the host outputs are read right after a stream synchronize."""
+    X, y, _ = problem(kind, n, B, M, np.linspace(0, 15, n), 21)
+    N = T.problem_size(kind, M)
+    ws = torch.empty(T.host_workspace_bytes(kind, n, B, M), device="cuda", dtype=torch.uint8)
+    Xh = torch.from_numpy(X).pin_memory()
+    yh = torch.from_numpy(y).pin_memory() if y is not None else None
+    s_host = torch.zeros((n, N - 1), dtype=torch.int8).pin_memory()
+    f_host = torch.zeros((n,), dtype=torch.int32).pin_memory()
+    side = torch.cuda.Stream()
+    with torch.cuda.stream(side):
+        T.run_host(kind, Xh, yh, ALPHA, 10, "fp32", ws, s_host, flags=f_host)
+    side.synchronize()
+    out = T.build_T(kind, *to_dev(X), None if y is None else to_dev(y)[0], alpha=ALPHA)
+    s, _, flags = T.detect(out["T_tilde"], out["D"], out["tau"], 10, "fp32", want_L=False, flags=out["flags"])
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(s_host.numpy(), s.cpu().numpy())
+    np.testing.assert_array_equal(f_host.numpy(), flags.cpu().numpy())
