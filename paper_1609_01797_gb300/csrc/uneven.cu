@@ -24,52 +24,91 @@ __device__ __forceinline__ int bucket_index(int N) {
 }
 
 // Counting sort of the item indices by (bucket, t_max descending): the longest items of a
-// bucket come first, which balances the persistent kernels' tails.  One block.
-__global__ void __launch_bounds__(1024)
-bucketize_kernel(int n, const taser_item* __restrict__ items, int* __restrict__ list, int* __restrict__ meta,
-                 uint32_t* __restrict__ flags) {
+// bucket come first, which balances the persistent kernels' tails.  Three grid-wide passes:
+// per-block histograms added into a global one, an exclusive scan (one block), and a
+// scatter in which each block reserves one range per key with a single global atomic.
+__device__ __forceinline__ int item_key(const taser_item& it) {
+  return bucket_index(it.N) * kClasses + (kClasses - min(it.t_max, kClasses));
+}
+__device__ __forceinline__ bool item_ok(const taser_item& it) {
+  return it.N >= 2 && it.N <= TASER_MAX_N && it.t_max >= 1;
+}
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItemsPerBlock = 4096;
+
+__global__ void __launch_bounds__(kSortThreads)
+bucket_hist_kernel(int n, const taser_item* __restrict__ items, int* __restrict__ ghist,
+                   uint32_t* __restrict__ flags) {
   __shared__ int hist[kKeys];
-  __shared__ int offs[kKeys];
-  const int tid = threadIdx.x;
-  for (int k = tid; k < kKeys; k += blockDim.x) hist[k] = 0;
+  for (int k = threadIdx.x; k < kKeys; k += blockDim.x) hist[k] = 0;
   __syncthreads();
-  for (int i = tid; i < n; i += blockDim.x) {
+  const int i0 = blockIdx.x * kSortItemsPerBlock, i1 = min(n, i0 + kSortItemsPerBlock);
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const taser_item it = items[i];
-    if (it.N >= 2 && it.N <= TASER_MAX_N && it.t_max >= 1) {
-      const int key = bucket_index(it.N) * kClasses + (kClasses - min(it.t_max, kClasses));
-      atomicAdd(&hist[key], 1);
-    } else if (flags != nullptr) {
-      flags[i] |= TASER_FLAG_BAD_ITEM;
-    }
+    if (item_ok(it)) atomicAdd(&hist[item_key(it)], 1);
+    else if (flags != nullptr) flags[i] |= TASER_FLAG_BAD_ITEM;
   }
   __syncthreads();
-  if (tid == 0) {
-    int run = 0;
-    for (int k = 0; k < kKeys; ++k) {
-      offs[k] = run;
-      run += hist[k];
-    }
-    for (int b = 0; b < 4; ++b) {
-      int cnt = 0;
-      for (int k = 0; k < kClasses; ++k) cnt += hist[b * kClasses + k];
-      meta[b] = offs[b * kClasses];
-      meta[4 + b] = cnt;
-      meta[8 + b] = 0;
-    }
+  for (int k = threadIdx.x; k < kKeys; k += blockDim.x)
+    if (hist[k] != 0) atomicAdd(&ghist[k], hist[k]);
+}
+
+// One block of kKeys threads: goffs = exclusive scan of ghist; queue metadata per bucket.
+__global__ void __launch_bounds__(kKeys)
+bucket_scan_kernel(const int* __restrict__ ghist, int* __restrict__ goffs, int* __restrict__ meta) {
+  __shared__ int sc[kKeys];
+  const int k = threadIdx.x;
+  sc[k] = ghist[k];
+  __syncthreads();
+  for (int o = 1; o < kKeys; o <<= 1) {     // inclusive Hillis-Steele scan
+    const int v = k >= o ? sc[k - o] : 0;
+    __syncthreads();
+    sc[k] += v;
+    __syncthreads();
+  }
+  const int excl = sc[k] - ghist[k];
+  goffs[k] = excl;
+  if (k % kClasses == 0) {
+    const int b = k / kClasses;
+    meta[b] = excl;
+    meta[4 + b] = sc[k + kClasses - 1] - excl;
+    meta[8 + b] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads)
+bucket_scatter_kernel(int n, const taser_item* __restrict__ items, int* __restrict__ goffs,
+                      int* __restrict__ list) {
+  __shared__ int hist[kKeys];
+  __shared__ int base[kKeys];
+  for (int k = threadIdx.x; k < kKeys; k += blockDim.x) hist[k] = 0;
+  __syncthreads();
+  const int i0 = blockIdx.x * kSortItemsPerBlock, i1 = min(n, i0 + kSortItemsPerBlock);
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+    const taser_item it = items[i];
+    if (item_ok(it)) atomicAdd(&hist[item_key(it)], 1);
   }
   __syncthreads();
-  for (int i = tid; i < n; i += blockDim.x) {
+  for (int k = threadIdx.x; k < kKeys; k += blockDim.x) {
+    base[k] = hist[k] != 0 ? atomicAdd(&goffs[k], hist[k]) : 0;
+    hist[k] = 0;
+  }
+  __syncthreads();
+  for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const taser_item it = items[i];
-    if (it.N >= 2 && it.N <= TASER_MAX_N && it.t_max >= 1) {
-      const int key = bucket_index(it.N) * kClasses + (kClasses - min(it.t_max, kClasses));
-      list[atomicAdd(&offs[key], 1)] = i;
+    if (item_ok(it)) {
+      const int key = item_key(it);
+      list[base[key] + atomicAdd(&hist[key], 1)] = i;
     }
   }
 }
 
+// Workspace: [list: n_items ints, 256-byte aligned] [meta: 256 bytes] [histogram: kKeys ints]
+// [running offsets: kKeys ints].
 size_t uneven_workspace_bytes(int64_t n_items) {
   const size_t list = ((size_t)n_items * sizeof(int) + 255) & ~size_t(255);
-  return list + 256;
+  return list + 256 + 2 * kKeys * sizeof(int);
 }
 
 cudaError_t detect_fx14_queue(int nb, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
@@ -81,8 +120,17 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
   int* list = static_cast<int*>(workspace);
   int* meta = reinterpret_cast<int*>(static_cast<char*>(workspace) +
                                      (((size_t)n_items * sizeof(int) + 255) & ~size_t(255)));
-  bucketize_kernel<<<1, 1024, 0, st>>>((int)n_items, items, list, meta, flags);
-  cudaError_t e = cudaGetLastError();
+  int* ghist = meta + 256 / sizeof(int);
+  int* goffs = ghist + kKeys;
+  cudaError_t e = cudaMemsetAsync(ghist, 0, kKeys * sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  const int sort_blocks = (int)((n_items + kSortItemsPerBlock - 1) / kSortItemsPerBlock);
+  if (sort_blocks > 0)
+    bucket_hist_kernel<<<sort_blocks, kSortThreads, 0, st>>>((int)n_items, items, ghist, flags);
+  bucket_scan_kernel<<<1, kKeys, 0, st>>>(ghist, goffs, meta);
+  if (sort_blocks > 0)
+    bucket_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>((int)n_items, items, goffs, list);
+  e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int order[4] = {3, 2, 1, 0};        // the heaviest bucket first
   for (int oi = 0; oi < 4; ++oi) {
@@ -94,7 +142,8 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
     q.meta = meta;
     q.b = b;
     const int bps = tuning != nullptr ? tuning->blocks_per_sm[b] : 0;
-    const int pop = tuning != nullptr ? tuning->pop[b] : 1;
+    // Default items per pop: short N <= 17 jobs amortise the queue atomic over four items.
+    const int pop = tuning != nullptr ? tuning->pop[b] : (b == 1 ? 4 : b == 2 ? 2 : 1);
     if (precision == TASER_FIXED14) {
       e = detect_fx14_queue(nb, q, bps, T_pool, D_pool, tau, L_pool, s_pool, flags, st);
     } else if (precision != TASER_FP32 && nb >= 16) {
