@@ -254,7 +254,9 @@ typedef struct {
 /* Per-bucket launch tuning of taser_detect_uneven (buckets N <= 9, 17, 33, 65). */
 typedef struct {
     int32_t blocks_per_sm[4];   /* persistent blocks per SM, 0 = as many as fit */
-    int32_t pop[4];             /* items a warp takes per queue pop, 0 = 1 */
+    int32_t pop[4];             /* items a warp takes per queue pop in the tensor-core
+                                   N <= 17 and N <= 33 buckets, 0 = 1 (defaults without
+                                   tuning: 4 and 2); the other buckets ignore it */
 } taser_uneven_tuning;
 
 /* Device workspace (bytes) taser_detect_uneven needs for n_items items. */
@@ -264,10 +266,11 @@ size_t taser_uneven_workspace_bytes(int64_t n_items);
  * taser_detect_uneven -- Algorithm 1 on a batch of problems of different sizes and
  * iteration counts (N = 2..65, any t_max >= 1 per item), in one stream-ordered sequence
  * without host synchronisation (capturable in a CUDA graph and replayed with one launch):
- * a counting-sort kernel builds a size-bucketed work queue in `workspace` (items grouped
- * by bucket N <= 9 / 17 / 33 / 65, then by t_max), and one persistent kernel per bucket
- * pulls items from its queue with an atomic counter.  Precisions as in taser_detect
- * (tensor cores for N >= 10, FP32 below).
+ * a counting sort (three short kernels) builds a size-bucketed work queue in `workspace`
+ * (items grouped by bucket N <= 9 / 17 / 33 / 65, then by t_max, longest first), and one
+ * persistent kernel per bucket takes its items: from an atomic counter, or (the N <= 65
+ * tensor-core bucket) at a fixed stride per warp pair over the sorted list.  Precisions as
+ * in taser_detect (tensor cores for N >= 10, FP32 below).
  *   items     device array of n_items taser_item.
  *   T_pool, D_pool, tau (float [n_items]), L_pool (may be NULL), s_pool: device pools
  *             addressed by the items' offsets.

@@ -348,9 +348,9 @@ __device__ __forceinline__ void cp_async4_64(float* smem_dst, const float* gsrc)
 // p + 2P, ... of its source: the dense batch, or the bucket's list of item indices, which
 // the bucketing kernel sorted by t_max (longest first), so the strided split is balanced.
 // While a pair iterates on one job, both warps prefetch the next job's T~, D and tau into
-// the other slot with cp.async; for a bucket list, thread 0 also prefetches the list entry
-// five jobs ahead and the item record three jobs ahead (each lands in a commit group that
-// is complete before it is read), so no global load sits between jobs.
+// the other slot with cp.async; for a bucket list, thread 0 also prefetches, when a job is
+// taken, the list entry four jobs and the item record two jobs after it (each lands in a
+// commit group that is complete before it is read), so no global load sits between jobs.
 // `from_list` repeats QUEUE at run time: the queue-fed instantiation then keeps both job
 // sources in its code, and measured 20% faster (its iteration loop is compiled with more
 // registers) than with the source fixed at compile time; the dense instantiation does not
