@@ -249,12 +249,28 @@ struct HermCfg {
   static constexpr int VB = (NP + 1) & ~1;     // complex vector length (16B pairs)
   static constexpr int WARPS = 4;
   static constexpr int IPC = WARPS * IPW;
-  static constexpr int INST_FLOATS = 4 * VB + 2 * VB;  // xb, wb (complex), db, eb2
+  static constexpr int INST_FLOATS = 8 * VB + 2 * VB;  // xd, wd ({re, re, im, im}), db, eb2
   static constexpr int ROUNDS = UV == 32 ? 5 : (UV == 16 ? 6 : 8);   // (UV+1)^ROUNDS >= 2e7
 };
 
 __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * b
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+
+// Packed FP32 pairs (fma.rn.f32x2): the complex multiply-adds of the reduction run as pair
+// operations on {re, im} against duplicated pairs {v, v} read from shared memory.
+__device__ __forceinline__ uint64_t sp_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void sp_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t sp_fma(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
 }
 
 template <int UV, bool NEG>
@@ -269,9 +285,11 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
   const int local = warp * C::IPW + grp;
   const int64_t inst = (int64_t)blockIdx.x * C::IPC + local;
   const bool active = inst < batch;
-  float2* xb = reinterpret_cast<float2*>(sm + local * C::INST_FLOATS);
-  float2* wb = xb + VB;
-  float* db = reinterpret_cast<float*>(wb + VB);
+  // x and w of the current reflection as duplicated pairs {re, re, im, im} (one LDS.128
+  // gives both pair operands of a complex multiply-add).
+  float4* xd = reinterpret_cast<float4*>(sm + local * C::INST_FLOATS);
+  float4* wd = xd + VB;
+  float* db = reinterpret_cast<float*>(wd + VB);
   float* eb2 = db + VB;
   const int N = 2 * U + 1;
   const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
@@ -297,8 +315,8 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
     col[j] = v;
   }
   for (int i = gl; i < VB; i += G) {
-    xb[i] = make_float2(0.f, 0.f);
-    wb[i] = make_float2(0.f, 0.f);
+    xd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    wd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
   if (gl == 0) db[0] = U >= 1 ? t(0, 0) : 0.f;
   __syncwarp();
@@ -312,20 +330,28 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
       float2 ck = make_float2(0.f, 0.f);
 #pragma unroll
       for (int r = KB; r < KE; ++r) ck = (r == k) ? col[r] : ck;
-      xb[c] = (c > k) ? make_float2(ck.x, -ck.y) : make_float2(0.f, 0.f);
+      xd[c] = (c > k) ? make_float4(ck.x, ck.x, -ck.y, -ck.y) : make_float4(0.f, 0.f, 0.f, 0.f);
       if (c == k) db[k] = ck.x;
       __syncwarp();
-      float2 x[VB];
+      const float4 x1q = xd[k + 1];
+      const float2 x1 = make_float2(x1q.x, x1q.z);
+      // |x|^2 and p_c's sum conj(M[j][c]) x_j in one pass over j:
+      //   A = sum {Re M, Im M} {Re x, Re x},  Bs = sum {Re M, Im M} {Im x, Im x},
+      //   conj(M) x = (A.re + Bs.im, Bs.re - A.im).
+      uint64_t A = 0ull, Bs = 0ull, S2 = 0ull;
 #pragma unroll
-      for (int j2 = (KB + 1) & ~1; j2 < VB; j2 += 2) {
-        const float4 q = *reinterpret_cast<const float4*>(xb + j2);
-        x[j2] = make_float2(q.x, q.y);
-        x[j2 + 1] = make_float2(q.z, q.w);
+      for (int j = KB + 1; j < NP; ++j) {
+        const float4 q = xd[j];
+        const uint64_t X1 = sp_pack(q.x, q.y), X2 = sp_pack(q.z, q.w);
+        const uint64_t Mj = sp_pack(col[j].x, col[j].y);
+        S2 = sp_fma(X2, X2, sp_fma(X1, X1, S2));
+        A = sp_fma(Mj, X1, A);
+        Bs = sp_fma(Mj, X2, Bs);
       }
-      const float2 x1 = xb[k + 1];
-      float sig2 = 0.f;
-#pragma unroll
-      for (int j = KB + 1; j < NP; ++j) sig2 = fmaf(x[j].x, x[j].x, fmaf(x[j].y, x[j].y, sig2));
+      float sig2, sig2_dup, ax, ay, bx, by;
+      sp_unpack(S2, sig2, sig2_dup);
+      sp_unpack(A, ax, ay);
+      sp_unpack(Bs, bx, by);
       const float sig = sqrtf(sig2);
       const float ax1 = sqrtf(fmaf(x1.x, x1.x, x1.y * x1.y));
       const float2 ph = ax1 > 0.f ? make_float2(x1.x / ax1, x1.y / ax1) : make_float2(1.f, 0.f);
@@ -334,39 +360,39 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
       const float vv2 = 2.f * sig * (sig + ax1);
       const float beta = vv2 > 0.f ? 2.f / vv2 : 0.f;
       // p_c = beta (sum_j conj(M[j][c]) v_j), v = x except v_{k+1} = x_{k+1} - alpha.
-      float2 acc = make_float2(0.f, 0.f), ck1 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int j = KB + 1; j < NP; ++j) {
-        const float2 m = cmul_conj(col[j], x[j]);
-        acc.x += m.x;
-        acc.y += m.y;
-      }
+      const float2 acc = make_float2(ax + by, bx - ay);
+      float2 ck1 = make_float2(0.f, 0.f);
 #pragma unroll
       for (int r = KB + 1; r <= KE && r < NP; ++r) ck1 = (r == k + 1) ? col[r] : ck1;
       const float2 corr = cmul_conj(ck1, make_float2(-al.x, -al.y));
       const bool live = c > k;
       const float2 p = live ? make_float2(beta * (acc.x + corr.x), beta * (acc.y + corr.y)) : make_float2(0.f, 0.f);
-      const float2 vc = !live ? make_float2(0.f, 0.f) : (c == k + 1 ? v1 : xb[c]);
+      float2 vc = make_float2(0.f, 0.f);
+      if (live) {
+        const float4 xc = xd[c];
+        vc = c == k + 1 ? v1 : make_float2(xc.x, xc.z);
+      }
       float kk = fmaf(vc.x, p.x, vc.y * p.y);                       // Re(conj(v_c) p_c)
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) kk += __shfl_xor_sync(TASER_FULL_MASK, kk, o);
       kk *= 0.5f * beta;
       const float2 w = make_float2(fmaf(-kk, vc.x, p.x), fmaf(-kk, vc.y, p.y));
-      wb[c] = w;
+      wd[c] = make_float4(w.x, w.x, w.y, w.y);
       if (c == k + 1) eb2[k] = sig2;                               // |alpha|^2
       __syncwarp();
-      float2 wv[VB];
-#pragma unroll
-      for (int j2 = (KB + 1) & ~1; j2 < VB; j2 += 2) {
-        const float4 q = *reinterpret_cast<const float4*>(wb + j2);
-        wv[j2] = make_float2(q.x, q.y);
-        wv[j2 + 1] = make_float2(q.z, q.w);
-      }
-      // M[j][c] -= v_j conj(w_c) + w_j conj(v_c)
+      // M[j][c] -= v_j conj(w_c) + w_j conj(v_c), as four pair FMAs per row:
+      //   v conj(w) = {Re v, Re v}{Re w, -Im w} + {Im v, Im v}{Im w, Re w}.
+      const uint64_t nWa = sp_pack(-w.x, w.y), nWb = sp_pack(-w.y, -w.x);
+      const uint64_t nVa = sp_pack(-vc.x, vc.y), nVb = sp_pack(-vc.y, -vc.x);
 #pragma unroll
       for (int j = KB + 1; j < NP; ++j) {
-        col[j].x -= fmaf(x[j].x, w.x, fmaf(x[j].y, w.y, fmaf(wv[j].x, vc.x, wv[j].y * vc.y)));
-        col[j].y -= fmaf(x[j].y, w.x, fmaf(-x[j].x, w.y, fmaf(wv[j].y, vc.x, -wv[j].x * vc.y)));
+        const float4 q = xd[j], u = wd[j];
+        uint64_t Mj = sp_pack(col[j].x, col[j].y);
+        Mj = sp_fma(sp_pack(q.x, q.y), nWa, Mj);
+        Mj = sp_fma(sp_pack(q.z, q.w), nWb, Mj);
+        Mj = sp_fma(sp_pack(u.x, u.y), nVa, Mj);
+        Mj = sp_fma(sp_pack(u.z, u.w), nVb, Mj);
+        sp_unpack(Mj, col[j].x, col[j].y);
       }
       // v_{k+1} = x_{k+1} - alpha: add alpha conj(w_c) to row k+1
 #pragma unroll
