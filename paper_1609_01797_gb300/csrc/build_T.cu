@@ -12,12 +12,17 @@
 // imaginary parts interleaved, exactly the complex64 memory layout):
 //   Re Gamma_pq = G'[2p][2q] + G'[2p+1][2q+1],   Im Gamma_pq = G'[2p][2q+1] - G'[2p+1][2q].
 // G' is a dense contraction over the B antennas, so it runs on the tensor cores with
-// mma.sync m16n8k8 TF32 in the split form x = hi + lo (hi = tf32(x), lo = tf32(x - hi)),
-// G' = hi^T hi + hi^T lo + lo^T hi, which keeps FP32-level accuracy (relative error about
-// 2^-22 per product) while the reduction over B happens inside the tensor core.
+// mma.sync m16n8k16 FP16 (FP32 accumulation) in the split form x = hi + lo (hi = fp16(x),
+// lo = fp16(x - hi)), G' = hi^T hi + hi^T lo + lo^T hi, which keeps FP32-level accuracy
+// (relative error about 2^-22 per product) while the reduction over B happens inside the
+// tensor core.  FP16's range is met by a power-of-two scale per column of W (exact, undone
+// on G'), taken from the first 32 antenna rows with 2^8 of headroom; an overflow restarts
+// the instance at a smaller scale.
 //
 // Mapping: one warp per instance.  X is staged into shared memory 32 antennas at a time
 // (double-buffered cp.async); only the upper-triangular 16 x 8 tiles of G' are computed.
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace taser {
@@ -35,6 +40,9 @@ struct BuildCfg {
   static constexpr int WARPS = 4;
   static constexpr int WARP_FLOATS = 2 * BUF_FLOATS;  // double buffer; reused by the epilogue
   static constexpr int SMEM_BYTES = WARPS * WARP_FLOATS * 4;
+  // FP16 split Gram (m16n8k16) from 17 complex columns on; 3xTF32 (m16n8k8) below, where
+  // the scale search costs more than the faster tensor rate saves (measured).
+  static constexpr bool F16 = MP >= 17;
   __host__ __device__ static constexpr bool tile(int i, int j) { return j >= 2 * i && j < NT; }
 };
 
@@ -63,8 +71,27 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
+__device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+  asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// Splits a pair of (scaled) floats into FP16 high and low parts: x = hi + lo + O(2^-22 x).
+__device__ __forceinline__ void split_f16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  const __half2 h = __floats2half2_rn(x0, x1);
+  const float2 hf = __half22float2(h);
+  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  hi = *reinterpret_cast<const uint32_t*>(&h);
+  lo = *reinterpret_cast<const uint32_t*>(&l);
+}
+
+// 2^e as a float for -126 <= e <= 127.
+__device__ __forceinline__ float pow2i(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
 template <int MP>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, MP == 17 ? 4 : 1)
 build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __restrict__ X,
                const float2* __restrict__ yv, float* __restrict__ Tt, float* __restrict__ Dout,
                uint32_t* __restrict__ flags) {
@@ -109,66 +136,186 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   };
 
   float acc[MT][NT][4];
-#pragma unroll
-  for (int i = 0; i < MT; ++i)
-#pragma unroll
-    for (int j = 0; j < NT; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-  stage(0);
-  if (nchunks > 1) stage(1);
-  for (int chunk = 0; chunk < nchunks; ++chunk) {
-    if (chunk + 1 < nchunks) cp_async_wait<1>(); else cp_async_wait<0>();
-    __syncwarp();
-    float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
-    const int rows = min(CH, B - chunk * CH);
-    if (rows < CH) {  // zero the unused tail rows of the last chunk
-      for (int i = rows * WS + lane; i < CH * WS; i += 32) buf[i] = 0.f;
-      __syncwarp();
-    }
-#pragma unroll
-    for (int ks = 0; ks < CH / 8; ++ks) {
-      // B fragments of every n-tile (k = 8 ks + tq, 8 ks + tq + 4; column 8j + g), split.
-      uint32_t bh[NT][2], bl[NT][2];
-      const float* r0p = buf + (8 * ks + tq) * WS + g;
-      const float* r1p = r0p + 4 * WS;
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const float x0 = r0p[8 * j], x1 = r1p[8 * j];
-        bh[j][0] = to_tf32(x0);
-        bh[j][1] = to_tf32(x1);
-        bl[j][0] = to_tf32(x0 - __uint_as_float(bh[j][0]));
-        bl[j][1] = to_tf32(x1 - __uint_as_float(bh[j][1]));
-      }
-#pragma unroll
-      for (int i = 0; i < MT; ++i) {
-        // A = W^T: rows 16i + g (+8) are n-tiles 2i and 2i+1 of the same loads.
-        const int j0 = 2 * i, j1 = 2 * i + 1;
-        uint32_t ah[4], al[4];
-        ah[0] = bh[j0][0];
-        ah[2] = bh[j0][1];
-        al[0] = bl[j0][0];
-        al[2] = bl[j0][1];
-        if (j1 < NT) {
-          ah[1] = bh[j1][0];
-          ah[3] = bh[j1][1];
-          al[1] = bl[j1][0];
-          al[3] = bl[j1][1];
-        } else {
-          ah[1] = ah[3] = al[1] = al[3] = 0u;
+  if constexpr (C::F16) {
+    // Per-column power-of-two scales: this lane's columns 8j + g are multiplied by 2^ex[j]
+    // before the FP16 split, chosen from the first 32 antenna rows so that their largest
+    // magnitude lands in [2^6, 2^7).  A later value beyond FP16's range (65504) becomes an
+    // infinite high part and a non-finite accumulator; the whole Gram then restarts with every
+    // scale 2^-9 smaller.
+    int ex[NT];
+    float sc[NT];
+  #pragma unroll
+    for (int j = 0; j < NT; ++j) ex[j] = 0;
+    for (int attempt = 0; attempt < 16; ++attempt) {
+  #pragma unroll
+      for (int i = 0; i < MT; ++i)
+  #pragma unroll
+        for (int j = 0; j < NT; ++j)
+  #pragma unroll
+          for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+      stage(0);
+      if (nchunks > 1) stage(1);
+      for (int chunk = 0; chunk < nchunks; ++chunk) {
+        if (chunk + 1 < nchunks) cp_async_wait<1>(); else cp_async_wait<0>();
+        __syncwarp();
+        float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
+        const int rows = min(CH, B - chunk * CH);
+        if (rows < CH) {  // zero the unused tail rows of the last chunk
+          for (int i = rows * WS + lane; i < CH * WS; i += 32) buf[i] = 0.f;
+          __syncwarp();
         }
-#pragma unroll
+        if (attempt == 0 && chunk == 0) {
+          // Column maxima over the first chunk: rows tq + 4r of column 8j + g, then over tq.
+  #pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            float m = 0.f;
+  #pragma unroll
+            for (int r = 0; r < CH / 4; ++r) m = fmaxf(m, fabsf(buf[(tq + 4 * r) * WS + 8 * j + g]));
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 2));
+            const int e2 = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;   // floor(log2 m), m normal
+            ex[j] = (m > 0.f && e2 > -127) ? min(max(6 - e2, -100), 100) : 0;
+          }
+        }
+  #pragma unroll
+        for (int j = 0; j < NT; ++j) sc[j] = pow2i(ex[j]);
+  #pragma unroll
+        for (int ks = 0; ks < CH / 16; ++ks) {
+          // B fragments of n-tile j: k = 2tq, 2tq+1, 2tq+8, 2tq+9 are staged rows tq, tq+4,
+          // tq+8, tq+12 of this 16-row step (any fixed row order gives the same Gram), column
+          // 8j + g; each value is scaled and split into FP16 high and low parts.
+          uint32_t bh[NT][2], bl[NT][2];
+          const float* rp = buf + (16 * ks + tq) * WS + g;
+  #pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const float x0 = rp[8 * j] * sc[j], x1 = rp[4 * WS + 8 * j] * sc[j];
+            const float x2 = rp[8 * WS + 8 * j] * sc[j], x3 = rp[12 * WS + 8 * j] * sc[j];
+            split_f16(x0, x1, bh[j][0], bl[j][0]);
+            split_f16(x2, x3, bh[j][1], bl[j][1]);
+          }
+  #pragma unroll
+          for (int i = 0; i < MT; ++i) {
+            // A = W^T: rows 16i + g (+8) are n-tiles 2i and 2i+1 of the same loads.
+            const int j0 = 2 * i, j1 = 2 * i + 1;
+            uint32_t ah[4], al[4];
+            ah[0] = bh[j0][0];
+            ah[2] = bh[j0][1];
+            al[0] = bl[j0][0];
+            al[2] = bl[j0][1];
+            if (j1 < NT) {
+              ah[1] = bh[j1][0];
+              ah[3] = bh[j1][1];
+              al[1] = bl[j1][0];
+              al[3] = bl[j1][1];
+            } else {
+              ah[1] = ah[3] = al[1] = al[3] = 0u;
+            }
+  #pragma unroll
+            for (int j = 0; j < NT; ++j) {
+              if (!C::tile(i, j)) continue;
+              mma_f16(acc[i][j], ah, bh[j][0], bh[j][1]);
+              mma_f16(acc[i][j], ah, bl[j][0], bl[j][1]);
+              mma_f16(acc[i][j], al, bh[j][0], bh[j][1]);
+            }
+          }
+        }
+        __syncwarp();  // every lane has read this buffer
+        if (chunk + 2 < nchunks) stage(chunk + 2);
+      }
+      bool finite = true;
+  #pragma unroll
+      for (int i = 0; i < MT; ++i)
+  #pragma unroll
+        for (int j = 0; j < NT; ++j)
+  #pragma unroll
+          for (int e = 0; e < 4; ++e) finite = finite && isfinite(acc[i][j][e]);
+      if (__all_sync(TASER_FULL_MASK, finite)) break;   // no FP16 overflow (non-finite input retries)
+  #pragma unroll
+      for (int j = 0; j < NT; ++j) ex[j] -= 9;
+    }
+    // Undo the scales: G'[m][n] was computed as 2^(ex_m + ex_n) G'[m][n].  Row m = 16i + g + 8h
+    // is this lane's column of n-tile 2i + h; column n = 8j + 2tq + p is held by lane 4 (2tq + p).
+    {
+      int exc[NT][2];
+  #pragma unroll
+      for (int j = 0; j < NT; ++j)
+  #pragma unroll
+        for (int p = 0; p < 2; ++p) exc[j][p] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq + p));
+  #pragma unroll
+      for (int i = 0; i < MT; ++i)
+  #pragma unroll
         for (int j = 0; j < NT; ++j) {
           if (!C::tile(i, j)) continue;
-          mma_tf32(acc[i][j], ah, bh[j][0], bh[j][1]);
-          mma_tf32(acc[i][j], ah, bl[j][0], bl[j][1]);
-          mma_tf32(acc[i][j], al, bh[j][0], bh[j][1]);
+  #pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int h = e >> 1;
+            const int er = 2 * i + h < NT ? ex[2 * i + h < NT ? 2 * i + h : 0] : 0;
+            acc[i][j][e] = ldexpf(acc[i][j][e], -(er + exc[j][e & 1]));
+          }
+        }
+    }
+  } else {   // 3xTF32 on m16n8k8: no range handling needed, cheaper for few columns
+  #pragma unroll
+    for (int i = 0; i < MT; ++i)
+  #pragma unroll
+      for (int j = 0; j < NT; ++j)
+  #pragma unroll
+        for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+    stage(0);
+    if (nchunks > 1) stage(1);
+    for (int chunk = 0; chunk < nchunks; ++chunk) {
+      if (chunk + 1 < nchunks) cp_async_wait<1>(); else cp_async_wait<0>();
+      __syncwarp();
+      float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
+      const int rows = min(CH, B - chunk * CH);
+      if (rows < CH) {  // zero the unused tail rows of the last chunk
+        for (int i = rows * WS + lane; i < CH * WS; i += 32) buf[i] = 0.f;
+        __syncwarp();
+      }
+  #pragma unroll
+      for (int ks = 0; ks < CH / 8; ++ks) {
+        // B fragments of every n-tile (k = 8 ks + tq, 8 ks + tq + 4; column 8j + g), split.
+        uint32_t bh[NT][2], bl[NT][2];
+        const float* r0p = buf + (8 * ks + tq) * WS + g;
+        const float* r1p = r0p + 4 * WS;
+  #pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const float x0 = r0p[8 * j], x1 = r1p[8 * j];
+          bh[j][0] = to_tf32(x0);
+          bh[j][1] = to_tf32(x1);
+          bl[j][0] = to_tf32(x0 - __uint_as_float(bh[j][0]));
+          bl[j][1] = to_tf32(x1 - __uint_as_float(bh[j][1]));
+        }
+  #pragma unroll
+        for (int i = 0; i < MT; ++i) {
+          // A = W^T: rows 16i + g (+8) are n-tiles 2i and 2i+1 of the same loads.
+          const int j0 = 2 * i, j1 = 2 * i + 1;
+          uint32_t ah[4], al[4];
+          ah[0] = bh[j0][0];
+          ah[2] = bh[j0][1];
+          al[0] = bl[j0][0];
+          al[2] = bl[j0][1];
+          if (j1 < NT) {
+            ah[1] = bh[j1][0];
+            ah[3] = bh[j1][1];
+            al[1] = bl[j1][0];
+            al[3] = bl[j1][1];
+          } else {
+            ah[1] = ah[3] = al[1] = al[3] = 0u;
+          }
+  #pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            if (!C::tile(i, j)) continue;
+            mma_tf32(acc[i][j], ah, bh[j][0], bh[j][1]);
+            mma_tf32(acc[i][j], ah, bl[j][0], bl[j][1]);
+            mma_tf32(acc[i][j], al, bh[j][0], bh[j][1]);
+          }
         }
       }
+      __syncwarp();  // every lane has read this buffer
+      if (chunk + 2 < nchunks) stage(chunk + 2);
     }
-    __syncwarp();  // every lane has read this buffer
-    if (chunk + 2 < nchunks) stage(chunk + 2);
   }
 
   // Gamma_pq (p <= q) from the accumulators: lane (g, tq) holds rows 16i + g (+8) and

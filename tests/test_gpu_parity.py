@@ -155,6 +155,40 @@ def test_build_T_matches_oracle(T, kind, B, M):
     assert (out["flags"].cpu().numpy() == 0).all()
 
 
+@pytest.mark.parametrize("case", ["near_far", "huge", "tiny", "late_loud_rows", "jed_late_loud"])
+def test_build_T_range_handling(T, case):
+    """The FP16 split Gram scales each column by a power of two chosen on the first 32
+    antenna rows and restarts at a smaller scale if a later value overflows FP16.  Inputs
+    that stress this: users 80 dB apart, overall scales of 1e6 and 1e-8, and rows after the
+    first 32 that are 1e4 times louder (forcing the restart).  T~, D and tau must still
+    match the oracle to the usual tolerances."""
+    n = 29
+    kind, B, M = ("jed_qpsk", 96, 17) if case == "jed_late_loud" else ("mimo_qpsk", 128, 16)
+    X, y, _ = problem(kind, n, B, M, 8.0, 77)
+    X = X.astype(np.complex128)
+    y = None if y is None else y.astype(np.complex128)
+    if case == "near_far":
+        X = X * (10.0 ** np.linspace(-2.0, 2.0, M))[None, None, :]
+        y = X.sum(axis=2) * 0.3 + 0.01 * y
+    elif case == "huge":
+        X, y = X * 1e6, y * 1e6
+    elif case == "tiny":
+        X, y = X * 1e-8, y * 1e-8
+    else:
+        X[:, 40:, :] *= 1e4
+        if y is not None:
+            y[:, 40:] *= 1e4
+    X = X.astype(np.complex64)
+    y = None if y is None else y.astype(np.complex64)
+    r = O.detect(kind, X, y, ALPHA, 1)
+    out = T.build_T(kind, *to_dev(X), None if y is None else to_dev(y)[0], alpha=ALPHA)
+    torch.cuda.synchronize()
+    assert np.abs(out["T_tilde"].cpu().numpy() - r["T_tilde"]).max() <= 2e-5
+    np.testing.assert_allclose(out["D"].cpu().numpy(), r["D"], rtol=1e-5)
+    np.testing.assert_allclose(out["tau"].cpu().numpy(), r["tau"], rtol=1e-5)
+    assert (out["flags"].cpu().numpy() == 0).all()
+
+
 def test_step_size_closed_forms(T):
     rng = np.random.default_rng(5)
     mats, want = [], []
