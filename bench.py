@@ -556,7 +556,7 @@ def main():
             "peak_source": peak_src, "algorithmic_flops_per_launch": fl * n, "ms_per_launch": head["detect_ms"],
             "fp32_pipe_frac": det_tc / fp32_peak}),
         "build": (head["build_ms"], {
-            "kernel": "build_T_kernel<17> (3xTF32 mma.sync Gram)", "bound": "hbm", "achieved": build_gbs,
+            "kernel": "build_T_kernel<17> (FP16 split mma.sync Gram)", "bound": "hbm", "achieved": build_gbs,
             "peak": hbm_peak, "unit": "GB/s", "frac": build_gbs / hbm_peak, "traffic": tr("build"),
             "peak_source": peak_src, "algorithmic_bytes_per_launch": n * build_bytes_per_instance(B, U, N),
             "ms_per_launch": head["build_ms"]}),
