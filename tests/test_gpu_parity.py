@@ -313,7 +313,8 @@ def test_full_size_qpsk_128x16_sampled(T, precision):
 @pytest.mark.parametrize("kind,B,M,t_max,precision", [("mimo_qpsk", 128, 16, 20, "bf16_tc"),
                                                       ("mimo_bpsk", 32, 8, 10, "fp32"),
                                                       ("jed_bpsk", 16, 16, 20, "fp32"),
-                                                      ("jed_qpsk", 16, 16, 20, "bf16_tc")])
+                                                      ("jed_qpsk", 16, 16, 20, "bf16_tc"),
+                                                      ("mimo_qpsk", 64, 8, 20, "fixed14")])
 def test_run_host_matches_device_path(T, kind, B, M, t_max, precision):
     """taser_run_host (host buffers in and out, caller-owned device workspace) gives the
     same decisions and flags as the device-resident calls, and its decisions agree with
