@@ -40,9 +40,10 @@ def parse_args():
     ap.add_argument("--instances", type=int, default=65536, help="instances per GPU per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=int, default=32768, help="instances timed on the CPU oracle")
-    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff"], default="qpsk128x16",
+    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff", "unfolded"], default="qpsk128x16",
                     help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20}; tradeoff: SNR "
-                         "for 1%% VER vs throughput over t_max = 1..20 for 32x32 BPSK/QPSK (neither is the headline)")
+                         "for 1%% VER vs throughput over t_max = 1..20 for 32x32 BPSK/QPSK; unfolded: training "
+                         "steps of unfolded TASER on batches of 8,192 (none of these is the headline)")
     return ap.parse_args()
 
 
@@ -412,6 +413,84 @@ def run_tradeoff(args):
     return 0
 
 
+def run_unfolded(args):
+    """Unfolded TASER training (learnable per-iteration steps, hand-written adjoint): one
+    step = taser_build_T on a fresh batch of 8,192 QPSK 128x16 instances (SNR uniform in
+    [4, 14] dB; eight pre-generated batches resident in HBM, cycled) + the forward with
+    checkpoints every 4 iterations (t_max = 10) + the MSE loss gradient + the adjoint +
+    one Adam update of alpha_t.  Reports training instances/s and the forward and adjoint
+    kernels against the FP32 pipe."""
+    import torch
+    import paper_1609_01797_gb300 as taser
+    from synth import make_mimo
+    dev = torch.device("cuda", 0)
+    n, t_max, c = 8192, 10, 4
+    batches = []
+    for k in range(8):
+        w = make_mimo(n, B, U, np.random.default_rng(100 + k).uniform(4, 14, n), "qpsk", seed=4000 + k)
+        truth = torch.from_numpy(truth_bits(w).astype(np.float32)).to(dev)
+        batches.append((torch.from_numpy(w["H"]).to(dev), torch.from_numpy(w["y"]).to(dev), truth))
+    alpha = torch.full((t_max,), ALPHA, device=dev, requires_grad=True)
+    opt = torch.optim.Adam([alpha], lr=0.02)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(i, ev=None):
+        H, y, truth = batches[i % len(batches)]
+        out = taser.build_T("mimo_qpsk", H, y, ALPHA)
+        inv = 1.0 / out["spec_norm"]
+        if ev is not None:
+            ev[0].record(stream)
+        soft, _, ckpt = taser.unfolded_forward(out["T_tilde"], out["D"], inv, alpha.detach(), c)
+        if ev is not None:
+            ev[1].record(stream)
+        g_soft = 2.0 * (soft - truth) / soft.numel()
+        if ev is not None:
+            ev[2].record(stream)
+        _, g_alpha = taser.unfolded_backward(out["T_tilde"], out["D"], inv, alpha.detach(), c, ckpt, g_soft)
+        if ev is not None:
+            ev[3].record(stream)
+        alpha.grad = g_alpha
+        opt.step()
+        return soft, truth
+
+    for i in range(args.warmup):
+        step(i)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize(dev)
+    e0.record(stream)
+    for i in range(args.steps):
+        step(i, ev[i])
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / args.steps
+    fwd_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    bwd_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
+    soft, truth = step(args.steps)
+    loss = float(torch.mean((soft - truth) ** 2))
+    props = torch.cuda.get_device_properties(dev)
+    fp32_peak = props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12
+    P = N * (N + 1) * (2 * N + 1) // 6
+    it_fwd = 2 * P + 3 * N * (N + 1) // 2 + N
+    fwd_fl = t_max * it_fwd
+    bwd_fl = t_max * it_fwd + t_max * (2 * P + 9 * N * (N + 1) // 2)   # one recompute + the adjoint
+    fwd_tf = n * fwd_fl / (fwd_ms * 1e-3) / 1e12
+    bwd_tf = n * bwd_fl / (bwd_ms * 1e-3) / 1e12
+    print(json.dumps({
+        "metric": "unfolded TASER training instances/s, QPSK 128x16 (N = 33), t_max = 10, batch 8,192",
+        "value": n / (ms * 1e-3), "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "unfolded_qpsk128x16_tmax10_c4_batch8192", "instances_per_step": n, "t_max": t_max,
+                   "checkpoint_every": c, "step": "build_T + forward + loss gradient + adjoint + Adam"},
+        "forward_ms": fwd_ms, "backward_ms": bwd_ms, "loss_after": loss,
+        "alpha_t": [round(float(a), 4) for a in alpha.detach().cpu()],
+        "roofline_forward": {"bound": "alu", "achieved": fwd_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                             "frac": fwd_tf / fp32_peak, "algorithmic_flops_per_instance": fwd_fl},
+        "roofline_backward": {"bound": "alu", "achieved": bwd_tf, "peak": fp32_peak, "unit": "TFLOP/s",
+                              "frac": bwd_tf / fp32_peak, "algorithmic_flops_per_instance": bwd_fl}}))
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
@@ -420,6 +499,8 @@ def main():
         return run_uneven(args)
     if args.workload == "tradeoff":
         return run_tradeoff(args)
+    if args.workload == "unfolded":
+        return run_unfolded(args)
 
     import torch
     import torch.distributed as dist
