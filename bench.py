@@ -592,6 +592,18 @@ def main():
     barrier()
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
     e2e_errs = int((s_host.numpy() != bits).sum())
+    # The host link's own rate: a plain pinned H2D copy of the same H (best of 3).
+    h2d_bytes = int(H_host.numel() * 8 + y_host.numel() * 8)
+    H_dev = torch.empty(H_host.shape, dtype=H_host.dtype, device=dev)
+    link_ms = []
+    for _ in range(3):
+        e0.record(stream)
+        H_dev.copy_(H_host, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        link_ms.append(e0.elapsed_time(e1))
+    link_gbs = H_host.numel() * 8 / (min(link_ms) * 1e-3) / 1e9
+    del H_dev
 
     # Whole-job numbers: max step time over ranks, instances summed over ranks.
     total = n * world
@@ -684,9 +696,12 @@ def main():
                                               % (props.multi_processor_count, smax)},
         "clocks": clocks,
         "e2e": {"value": total / (e2e_ms * 1e-3), "unit": "detections/s",
-                "h2d_bytes_per_step": int(H_host.numel() * 8 + y_host.numel() * 8),
+                "h2d_bytes_per_step": h2d_bytes,
                 "d2h_bytes_per_step": int(s_host.numel()), "ms_per_step": e2e_ms,
-                "path": "taser_run_host (bf16_tc)", "bit_errors": e2e_errs},
+                "path": "taser_run_host (bf16_tc)", "bit_errors": e2e_errs,
+                "host_link": {"h2d_gbs": link_gbs, "bound": total / (h2d_bytes / (link_gbs * 1e9)),
+                              "frac": (total / (e2e_ms * 1e-3)) / (total / (h2d_bytes / (link_gbs * 1e9))),
+                              "note": "bound = instances / (H2D bytes / measured pinned H2D rate)"}},
         "gpu_launches": 3 * args.steps,
     }
     if world == 1 and not args.no_cpu_baseline:

@@ -19,8 +19,8 @@
 // on G'), taken from the first 32 antenna rows with 2^8 of headroom; an overflow restarts
 // the instance at a smaller scale.
 //
-// Mapping: one warp per instance.  X is staged into shared memory 32 antennas at a time
-// (double-buffered cp.async); only the upper-triangular 16 x 8 tiles of G' are computed.
+// Mapping: one warp per instance.  X is staged into shared memory through a cp.async ring
+// of antenna-row chunks; only the upper-triangular 16 x 8 tiles of G' are computed.
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -35,10 +35,14 @@ struct BuildCfg {
   // Row stride (floats) of a staged antenna row: >= 8 NT and = 8 or 24 mod 32, so the
   // fragment loads (rows t and t + 4, columns 8j + g) hit 32 distinct banks.
   static constexpr int WS = (8 * NT) % 32 == 8 || (8 * NT) % 32 == 24 ? 8 * NT : 8 * NT + 8;
-  static constexpr int CH = 32;                       // antennas per staged chunk
+  // Staging: a ring of NS chunks of CH antenna rows.  17 complex columns (the QPSK 128x16
+  // case) use 16-row chunks with three in flight; the others a double buffer of 32 rows
+  // (measured: the deeper ring was slower for 33 columns).
+  static constexpr int CH = MP == 17 ? 16 : 32;       // antennas per staged chunk
+  static constexpr int NS = MP == 17 ? 4 : 2;         // chunks in the cp.async ring
   static constexpr int BUF_FLOATS = CH * WS;
   static constexpr int WARPS = 4;
-  static constexpr int WARP_FLOATS = 2 * BUF_FLOATS;  // double buffer; reused by the epilogue
+  static constexpr int WARP_FLOATS = NS * BUF_FLOATS; // ring; reused by the epilogue
   static constexpr int SMEM_BYTES = WARPS * WARP_FLOATS * 4;
   // FP16 split Gram (m16n8k16) from 17 complex columns on; 3xTF32 (m16n8k8) below, where
   // the scale search costs more than the faster tensor rate saves (measured).
@@ -90,13 +94,15 @@ __device__ __forceinline__ void split_f16(float x0, float x1, uint32_t& hi, uint
 // 2^e as a float for -126 <= e <= 127.
 __device__ __forceinline__ float pow2i(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
-template <int MP>
-__global__ void __launch_bounds__(128, MP == 17 ? 4 : 1)
-build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __restrict__ X,
+// KIND >= 0 compiles the epilogue for that problem kind; -1 takes it from kind_rt.
+template <int MP, int KIND>
+__global__ void __launch_bounds__(128, MP == 17 ? 5 : 1)
+build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __restrict__ X,
                const float2* __restrict__ yv, float* __restrict__ Tt, float* __restrict__ Dout,
                uint32_t* __restrict__ flags) {
   using C = BuildCfg<MP>;
   constexpr int NT = C::NT, MT = C::MT, WS = C::WS, CH = C::CH;
+  const int kind = KIND >= 0 ? KIND : kind_rt;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
@@ -118,7 +124,7 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   const int nchunks = (B + CH - 1) / CH;
 
   auto stage = [&](int chunk) {
-    float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
+    float* buf = Ws + (chunk % C::NS) * C::BUF_FLOATS;
     const int r0 = chunk * CH;
     const int rows = min(CH, B - r0);
     if (crow < rows_per_iter) {
@@ -153,24 +159,40 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
         for (int j = 0; j < NT; ++j)
   #pragma unroll
           for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-      stage(0);
-      if (nchunks > 1) stage(1);
+      // One cp.async group per chunk (empty past the end), so the wait for chunk c always
+      // leaves the NS - 2 younger groups in flight.
+  #pragma unroll
+      for (int s = 0; s < C::NS - 1; ++s) {
+        if (s < nchunks) stage(s); else cp_async_commit();
+      }
       for (int chunk = 0; chunk < nchunks; ++chunk) {
-        if (chunk + 1 < nchunks) cp_async_wait<1>(); else cp_async_wait<0>();
+        cp_async_wait<C::NS - 2>();
         __syncwarp();
-        float* buf = Ws + (chunk & 1) * C::BUF_FLOATS;
+        float* buf = Ws + (chunk % C::NS) * C::BUF_FLOATS;
         const int rows = min(CH, B - chunk * CH);
         if (rows < CH) {  // zero the unused tail rows of the last chunk
           for (int i = rows * WS + lane; i < CH * WS; i += 32) buf[i] = 0.f;
           __syncwarp();
         }
         if (attempt == 0 && chunk == 0) {
-          // Column maxima over the first chunk: rows tq + 4r of column 8j + g, then over tq.
+          // Column maxima over the first 32 antenna rows (rows past B read as zero): rows
+          // tq + 4r of column 8j + g, then over tq.  With 16-row chunks these are chunks 0
+          // and 1, which sit next to each other at the start of the ring.
+          if constexpr (CH < 32) {
+            static_assert(CH == 16 && C::NS >= 3, "the first 32 rows must be chunks 0 and 1");
+            cp_async_wait<C::NS - 3>();
+            __syncwarp();
+            if (nchunks > 1 && B - CH < CH) {
+              float* b1 = Ws + C::BUF_FLOATS;
+              for (int i = (B - CH) * WS + lane; i < CH * WS; i += 32) b1[i] = 0.f;
+              __syncwarp();
+            }
+          }
   #pragma unroll
           for (int j = 0; j < NT; ++j) {
             float m = 0.f;
   #pragma unroll
-            for (int r = 0; r < CH / 4; ++r) m = fmaxf(m, fabsf(buf[(tq + 4 * r) * WS + 8 * j + g]));
+            for (int r = 0; r < 32 / 4; ++r) m = fmaxf(m, fabsf(Ws[(tq + 4 * r) * WS + 8 * j + g]));
             m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 1));
             m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 2));
             const int e2 = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;   // floor(log2 m), m normal
@@ -220,7 +242,7 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
           }
         }
         __syncwarp();  // every lane has read this buffer
-        if (chunk + 2 < nchunks) stage(chunk + 2);
+        if (chunk + C::NS - 1 < nchunks) stage(chunk + C::NS - 1); else cp_async_commit();
       }
       bool finite = true;
   #pragma unroll
@@ -250,7 +272,10 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
           for (int e = 0; e < 4; ++e) {
             const int h = e >> 1;
             const int er = 2 * i + h < NT ? ex[2 * i + h < NT ? 2 * i + h : 0] : 0;
-            acc[i][j][e] = ldexpf(acc[i][j][e], -(er + exc[j][e & 1]));
+            // 2^sh as one exact multiply while it is a normal float, else ldexpf.
+            const int sh = -(er + exc[j][e & 1]);
+            const float v = acc[i][j][e] * pow2i(min(max(sh, -126), 127));
+            acc[i][j][e] = (sh >= -126 && sh <= 127) ? v : ldexpf(acc[i][j][e], sh);
           }
         }
     }
@@ -445,19 +470,19 @@ build_T_kernel(int kind, int64_t batch, int B, int P, int N, const float2* __res
   }
 }
 
-template <int MP>
+template <int MP, int KIND>
 static cudaError_t launch_build(int kind, int64_t batch, int B, int P, int N, const float2* X, const float2* y,
                                 float* Tt, float* D, uint32_t* flags, cudaStream_t st) {
   using C = BuildCfg<MP>;
   static_assert((2 * MP - 1) * (2 * MP - 1) + 144 <= C::WARP_FLOATS, "epilogue scratch must fit the staging buffers");
   if (C::SMEM_BYTES > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(build_T_kernel<MP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(build_T_kernel<MP, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
   }
   const int64_t blocks = (batch + C::WARPS - 1) / C::WARPS;
-  build_T_kernel<MP><<<(unsigned)blocks, 32 * C::WARPS, C::SMEM_BYTES, st>>>(kind, batch, B, P, N, X, y, Tt, D,
-                                                                           flags);
+  build_T_kernel<MP, KIND><<<(unsigned)blocks, 32 * C::WARPS, C::SMEM_BYTES, st>>>(kind, batch, B, P, N, X, y, Tt,
+                                                                                 D, flags);
   return cudaGetLastError();
 }
 
@@ -466,9 +491,13 @@ cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X,
                     float* D, uint32_t* flags, cudaStream_t st) {
   const float2* Xc = static_cast<const float2*>(X);
   const float2* yc = static_cast<const float2*>(y);
-  if (P + 1 <= 9) return launch_build<9>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
-  if (P + 1 <= 17) return launch_build<17>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
-  if (P + 1 <= 33) return launch_build<33>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+  if (P + 1 <= 9) return launch_build<9, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+  if (P + 1 <= 17) {
+    if (kind == TASER_MIMO_QPSK)
+      return launch_build<17, TASER_MIMO_QPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+    return launch_build<17, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+  }
+  if (P + 1 <= 33) return launch_build<33, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
   return cudaErrorNotSupported;
 }
 

@@ -279,6 +279,9 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
     }
     float LNN = DN;
     uint32_t fl = 0;
+    // Inside a diagonal 16 x 16 block the element (row g + 8h, column 2tq + p + 8h') lies
+    // above the diagonal iff h' > h, or h' == h and 2tq + p > g.
+    const bool up0 = 2 * tq > g, up1 = 2 * tq + 1 > g;
 
     for (int t = 0; t < t_max; ++t) {
       // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
@@ -325,16 +328,17 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           }
         }
       }
-      // Keep V lower-triangular inside the diagonal tiles.
+      // Keep V lower-triangular inside the diagonal blocks: the rows g of n-tile 2M + 1
+      // are above the diagonal on every lane.
 #pragma unroll
-      for (int M = 0; M < MT - 1; ++M)
-#pragma unroll
-        for (int n = 2 * M; n <= 2 * M + 1; ++n)
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
-            if (c > r) acc[M][n][e] = 0.f;
-          }
+      for (int M = 0; M < MT - 1; ++M) {
+        if (up0) acc[M][2 * M][0] = 0.f;
+        if (up1) acc[M][2 * M][1] = 0.f;
+        acc[M][2 * M + 1][0] = 0.f;
+        acc[M][2 * M + 1][1] = 0.f;
+        if (up0) acc[M][2 * M + 1][2] = 0.f;
+        if (up1) acc[M][2 * M + 1][3] = 0.f;
+      }
 
       const float vnn = fmaf(LNN, tnNN, LNN) + part;
       if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
@@ -348,8 +352,10 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
 #pragma unroll
         for (int M = 0; M < MT; ++M) {
           if (!C::has_tile(M, n)) continue;
-          const uint64_t x01 = f2pack(acc[M][n][0], acc[M][n][1]);
-          v2 = f2fma(x01, x01, v2);
+          if (!(M < MT - 1 && n == 2 * M + 1)) {   // rows g of n-tile 2M + 1 are zero
+            const uint64_t x01 = f2pack(acc[M][n][0], acc[M][n][1]);
+            v2 = f2fma(x01, x01, v2);
+          }
           if (M < MT - 1) {
             const uint64_t x23 = f2pack(acc[M][n][2], acc[M][n][3]);
             v2 = f2fma(x23, x23, v2);
@@ -396,7 +402,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
 #pragma unroll
         for (int M = 0; M < MT; ++M) {
           if (!C::has_tile(M, n)) continue;
-          TASER_PAIR_APPLY(acc[M][n], 0, f2mul(_x, sc2));
+          if (!(M < MT - 1 && n == 2 * M + 1)) TASER_PAIR_APPLY(acc[M][n], 0, f2mul(_x, sc2));
           if (M < MT - 1) TASER_PAIR_APPLY(acc[M][n], 2, f2mul(_x, sc2));
         }
       }

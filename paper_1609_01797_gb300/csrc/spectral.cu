@@ -28,16 +28,35 @@ struct SpecCfg {
   static constexpr int WARP_FLOATS = 2 * VB + 2 * VB;  // x, w, d, e
 };
 
-constexpr int KBLK = 4;  // Householder steps per compiled block
+// Householder steps per compiled block: the real kernel's steps are longer, the complex
+// one's shorter (measured: 2 beats 1, whose fully unrolled body misses the instruction
+// cache, and 4).
+constexpr int KBLK = 4;
+constexpr int KBLK_HERM = 2;
 
-// Calls f(std::integral_constant<int, KB>) for KB = 0, KBLK, 2 KBLK, ... < NV - 1.
-template <int NV, int KB = 0, typename F>
+// Calls f(std::integral_constant<int, KB>) for KB = 0, BLK, 2 BLK, ... < NV - 1.
+template <int NV, int BLK, int KB = 0, typename F>
 __device__ __forceinline__ void static_for_blocks(F&& f) {
   if constexpr (KB < NV - 1) {
     f(std::integral_constant<int, KB>{});
-    static_for_blocks<NV, KB + KBLK>(f);
+    static_for_blocks<NV, BLK, KB + BLK>(f);
   }
 }
+
+// Exponent e with 2^e <= m < 2^(e+1), clamped to [-126, 126] (0 for zero or non-finite m):
+// the matrix is scaled by 2^-e (exact, both factors normal floats) so its largest entry
+// lies in [1, 4) and tiny reflector norms are judged against that scale; ||T~|| is scaled
+// back by 2^e.
+__device__ __forceinline__ int scale_exponent(float m) {
+  if (!(m > 0.f) || !(m <= 3.0e38f)) return 0;
+  const int e = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;
+  return e < -126 ? -126 : (e > 126 ? 126 : e);
+}
+__device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
+
+// Below this squared norm (relative to the scaled matrix, largest entry about 1) the
+// column is already eliminated: the rest is rounding residue far under FP32's resolution.
+constexpr float kTinyNorm2 = 0x1p-100f;
 
 // Sturm count: number of eigenvalues of the tridiagonal (sg*d, e) below sigma.
 template <int NP>
@@ -80,7 +99,23 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
 #pragma unroll
     for (int r = 0; r < NP; ++r) col[s][r] = (r < N && c < N) ? T[(int64_t)r * N + c] : 0.f;
   }
-  const float d0 = T[0];
+  float d0 = T[0];
+  float amax = fabsf(d0);
+#pragma unroll
+  for (int s = 0; s < S; ++s)
+#pragma unroll
+    for (int r = 0; r < NP; ++r) amax = fmaxf(amax, fabsf(col[s][r]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(TASER_FULL_MASK, amax, o));
+  const int ex = scale_exponent(amax);
+  {
+    const float sc = pow2f(-ex);
+    d0 *= sc;
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+#pragma unroll
+      for (int r = 0; r < NP; ++r) col[s][r] *= sc;
+  }
   for (int i = lane; i < VB; i += 32) {
     xb[i] = 0.f;
     wb[i] = 0.f;
@@ -89,25 +124,50 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
 
   // Householder steps k = 0 .. NV-2 in blocks of KBLK: each block body is compiled once
   // with its trailing range starting at KB + 1 (entries j <= k inside the block are zero
-  // in the published vector), which keeps the code inside the instruction cache.  Only
-  // the entry k+1 of the reflector differs from the published column, so it is corrected
-  // through short select chains over the block's rows.
+  // in the published vector), which keeps the code inside the instruction cache.  Row k of
+  // the lane's columns is picked by a short select chain over the block's rows.
   if (lane == 0) db[0] = d0;
-  static_for_blocks<NV>([&](auto kb) {
+  static_for_blocks<NV, KBLK>([&](auto kb) {
     constexpr int KB = decltype(kb)::value;
     constexpr int KE = (KB + KBLK < NV - 1) ? KB + KBLK : NV - 1;   // k in [KB, KE)
 #pragma unroll 1
     for (int k = KB; k < KE; ++k) {
-      // Publish column k below the diagonal: xb[j] = A[j][k] = A[k][j] for j > k, else 0;
-      // the owner of column k records d_k = A[k][k].
+      // x = column k below the diagonal: x_c = A[c][k] = A[k][c] sits in the owner of column
+      // c.  The reflector H = I - beta v v^T with v = x - ah e_{k+1}, ah = -sign(x_{k+1}) ||x||,
+      // maps x to ah e_{k+1}; v is published (zero for rows <= k).
+      float ck[S];
+      float sig2 = 0.f;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
         const int c = lane + 1 + 32 * s;
-        float ck = 0.f;
+        float v = 0.f;
 #pragma unroll
-        for (int r = KB; r < KE; ++r) ck = (r == k) ? col[s][r] : ck;
-        if (c <= NV) xb[c] = (c > k) ? ck : 0.f;
-        if (c == k) db[k] = ck;
+        for (int r = KB; r < KE; ++r) v = (r == k) ? col[s][r] : v;
+        ck[s] = v;
+        if (c > k && c <= NV) sig2 = fmaf(v, v, sig2);
+      }
+      sig2 = warp_sum(sig2);
+      // x_{k+1} from the owner of column k + 1 (lane k mod 32, column slot k / 32).
+      float xs = ck[0];
+#pragma unroll
+      for (int s = 1; s < S; ++s) xs = (k / 32 == s) ? ck[s] : xs;
+      const float x1 = __shfl_sync(TASER_FULL_MASK, xs, k & 31);
+      // Reflector scalars from a reciprocal square root (a few ulp; the reflection stays
+      // orthogonal to that order, below the FP32 rounding of the updates).  A column with
+      // ||x||^2 under kTinyNorm2 is left as it is (beta = 0).
+      const bool refl = sig2 >= kTinyNorm2;
+      const float sig = refl ? sig2 * rsqrtf(sig2) : 0.f;
+      const float ah = x1 >= 0.f ? -sig : sig;             // new subdiagonal entry
+      const float vv2 = 2.f * (sig2 + sig * fabsf(x1));    // ||v||^2
+      const float beta = refl ? __fdividef(2.f, vv2) : 0.f;
+      float vi[S];
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const int c = lane + 1 + 32 * s;
+        const bool live = c > k && c <= NV;
+        vi[s] = live ? (c == k + 1 ? ck[s] - ah : ck[s]) : 0.f;
+        if (c <= NV) xb[c] = vi[s];
+        if (c == k) db[k] = ck[s];
       }
       __syncwarp();
       float x[VB];
@@ -116,28 +176,15 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
         const float4 q = *reinterpret_cast<const float4*>(xb + j4);
         x[j4] = q.x; x[j4 + 1] = q.y; x[j4 + 2] = q.z; x[j4 + 3] = q.w;
       }
-      const float x1 = xb[k + 1];
-      float sig2 = 0.f;
-#pragma unroll
-      for (int j = KB + 1; j < NP; ++j) sig2 = fmaf(x[j], x[j], sig2);
-      const float sig = sqrtf(sig2);
-      const float ah = x1 >= 0.f ? -sig : sig;             // new subdiagonal entry
-      const float vv2 = 2.f * (sig2 + sig * fabsf(x1));    // ||v||^2, v = x - ah e_{k+1}
-      const float beta = vv2 > 0.f ? 2.f / vv2 : 0.f;
-      // p_i = beta (sum_j A[j][i] x_j - ah A[k+1][i]) for this lane's columns i > k.
-      float p[S], vi[S];
+      // p_i = beta sum_j A[j][i] v_j for this lane's columns i > k.
+      float p[S];
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const int c = lane + 1 + 32 * s;
-        float acc = 0.f, ck1 = 0.f;
+        float acc = 0.f;
 #pragma unroll
         for (int j = KB + 1; j < NP; ++j) acc = fmaf(col[s][j], x[j], acc);
-#pragma unroll
-        for (int r = KB + 1; r <= KE && r < NP; ++r) ck1 = (r == k + 1) ? col[s][r] : ck1;
-        const bool live = c > k && c <= NV;
-        p[s] = live ? beta * fmaf(-ah, ck1, acc) : 0.f;
-        const float vc = (c == k + 1) ? x1 - ah : xb[c <= NV ? c : 0];
-        vi[s] = live ? vc : 0.f;
+        const int c = lane + 1 + 32 * s;
+        p[s] = (c > k && c <= NV) ? beta * acc : 0.f;
       }
       float kk = 0.f;
 #pragma unroll
@@ -158,13 +205,11 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
         const float4 q = *reinterpret_cast<const float4*>(wb + j4);
         wv[j4] = q.x; wv[j4 + 1] = q.y; wv[j4 + 2] = q.z; wv[j4 + 3] = q.w;
       }
-      // A <- A - v w^T - w v^T on the trailing block; v = x except v_{k+1} = x_{k+1} - ah.
+      // A <- A - v w^T - w v^T on the trailing block.
 #pragma unroll
       for (int s = 0; s < S; ++s) {
 #pragma unroll
         for (int j = KB + 1; j < NP; ++j) col[s][j] = fmaf(-x[j], w[s], fmaf(-wv[j], vi[s], col[s][j]));
-#pragma unroll
-        for (int r = KB + 1; r <= KE && r < NP; ++r) col[s][r] = fmaf((r == k + 1) ? ah : 0.f, w[s], col[s][r]);
       }
       __syncwarp();
     }
@@ -222,6 +267,7 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
   }
   float nrm = 0.5f * (lo + hi);
   if (two) nrm = fmaxf(nrm, __shfl_xor_sync(TASER_FULL_MASK, nrm, 16));
+  nrm *= pow2f(ex);
   if (lane == 0) {
     tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
     if (nrm_out != nullptr) nrm_out[inst] = nrm;
@@ -314,64 +360,79 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
     else if (ja && ca) v = make_float2(t(2 * U, 2 * U), 0.f);
     col[j] = v;
   }
+  float m00 = U >= 1 ? t(0, 0) : 0.f;
+  float amax = fabsf(m00);
+#pragma unroll
+  for (int j = 0; j < NP; ++j) amax = fmaxf(amax, fmaxf(fabsf(col[j].x), fabsf(col[j].y)));
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(TASER_FULL_MASK, amax, o));
+  const int ex = scale_exponent(amax);
+  {
+    const float sc = pow2f(-ex);
+    m00 *= sc;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) col[j] = make_float2(col[j].x * sc, col[j].y * sc);
+  }
   for (int i = gl; i < VB; i += G) {
     xd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
     wd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (gl == 0) db[0] = U >= 1 ? t(0, 0) : 0.f;
+  if (gl == 0) db[0] = m00;
   __syncwarp();
 
-  static_for_blocks<UV>([&](auto kb) {
+  static_for_blocks<UV, KBLK_HERM>([&](auto kb) {
     constexpr int KB = decltype(kb)::value;
-    constexpr int KE = (KB + KBLK < UV - 1) ? KB + KBLK : UV - 1;   // k in [KB, KE)
+    constexpr int KE = (KB + KBLK_HERM < UV - 1) ? KB + KBLK_HERM : UV - 1;   // k in [KB, KE)
 #pragma unroll 1
     for (int k = KB; k < KE; ++k) {
-      // Publish x = column k below the diagonal: x_j = M[j][k] = conj(M[k][j]), j > k.
+      // x = column k below the diagonal: lane c holds x_c = M[c][k] = conj(M[k][c]) in its
+      // own column.  The reflector H = I - beta v v^H with v = x - alpha e_{k+1},
+      // alpha = -e^{i theta} sigma (theta = arg x_{k+1}, sigma = ||x||) maps x to alpha e_{k+1}.
       float2 ck = make_float2(0.f, 0.f);
 #pragma unroll
       for (int r = KB; r < KE; ++r) ck = (r == k) ? col[r] : ck;
-      xd[c] = (c > k) ? make_float4(ck.x, ck.x, -ck.y, -ck.y) : make_float4(0.f, 0.f, 0.f, 0.f);
+      const bool live = c > k;
+      const float2 xc = make_float2(ck.x, -ck.y);
+      float sig2 = live ? fmaf(ck.x, ck.x, ck.y * ck.y) : 0.f;
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) sig2 += __shfl_xor_sync(TASER_FULL_MASK, sig2, o);
+      const int src = grp * G + k;                                   // lane of column k + 1
+      const float2 x1 = make_float2(__shfl_sync(TASER_FULL_MASK, xc.x, src), __shfl_sync(TASER_FULL_MASK, xc.y, src));
+      // Reflector scalars from reciprocal square roots (a few ulp; the reflection stays
+      // orthogonal to that order, below the FP32 rounding of the updates).  A column with
+      // ||x||^2 under kTinyNorm2 is left as it is (beta = 0); an x_{k+1} that small takes
+      // the phase 1, and ||v||^2 then uses Re(conj(e^{i theta}) x_{k+1}) = Re x_{k+1}.
+      const bool refl = sig2 >= kTinyNorm2;
+      const float sig = refl ? sig2 * rsqrtf(sig2) : 0.f;
+      const float n1 = fmaf(x1.x, x1.x, x1.y * x1.y);
+      const bool big1 = n1 >= kTinyNorm2;
+      const float r1 = big1 ? rsqrtf(n1) : 0.f;
+      const float2 ph = big1 ? make_float2(x1.x * r1, x1.y * r1) : make_float2(1.f, 0.f);
+      const float ax1 = big1 ? n1 * r1 : x1.x;                                   // Re(conj(ph) x_{k+1})
+      const float2 v1 = make_float2(fmaf(ph.x, sig, x1.x), fmaf(ph.y, sig, x1.y));   // x_{k+1} - alpha
+      const float vv2 = 2.f * sig * (sig + ax1);                                 // ||v||^2
+      const float beta = refl ? __fdividef(2.f, vv2) : 0.f;
+      // Publish v (zero for rows <= k) as duplicated pairs.
+      const float2 vc = live ? (c == k + 1 ? v1 : xc) : make_float2(0.f, 0.f);
+      xd[c] = make_float4(vc.x, vc.x, vc.y, vc.y);
       if (c == k) db[k] = ck.x;
       __syncwarp();
-      const float4 x1q = xd[k + 1];
-      const float2 x1 = make_float2(x1q.x, x1q.z);
-      // |x|^2 and p_c's sum conj(M[j][c]) x_j in one pass over j:
-      //   A = sum {Re M, Im M} {Re x, Re x},  Bs = sum {Re M, Im M} {Im x, Im x},
-      //   conj(M) x = (A.re + Bs.im, Bs.re - A.im).
-      uint64_t A = 0ull, Bs = 0ull, S2 = 0ull;
+      // p_c = beta sum_j conj(M[j][c]) v_j in one pass over j:
+      //   A = sum {Re M, Im M} {Re v, Re v},  Bs = sum {Re M, Im M} {Im v, Im v},
+      //   conj(M) v = (A.re + Bs.im, Bs.re - A.im).
+      uint64_t A = 0ull, Bs = 0ull;
 #pragma unroll
       for (int j = KB + 1; j < NP; ++j) {
         const float4 q = xd[j];
         const uint64_t X1 = sp_pack(q.x, q.y), X2 = sp_pack(q.z, q.w);
         const uint64_t Mj = sp_pack(col[j].x, col[j].y);
-        S2 = sp_fma(X2, X2, sp_fma(X1, X1, S2));
         A = sp_fma(Mj, X1, A);
         Bs = sp_fma(Mj, X2, Bs);
       }
-      float sig2, sig2_dup, ax, ay, bx, by;
-      sp_unpack(S2, sig2, sig2_dup);
+      float ax, ay, bx, by;
       sp_unpack(A, ax, ay);
       sp_unpack(Bs, bx, by);
-      const float sig = sqrtf(sig2);
-      const float ax1 = sqrtf(fmaf(x1.x, x1.x, x1.y * x1.y));
-      const float2 ph = ax1 > 0.f ? make_float2(x1.x / ax1, x1.y / ax1) : make_float2(1.f, 0.f);
-      const float2 al = make_float2(-ph.x * sig, -ph.y * sig);       // alpha = -e^{i theta} sigma
-      const float2 v1 = make_float2(ph.x * (ax1 + sig), ph.y * (ax1 + sig));
-      const float vv2 = 2.f * sig * (sig + ax1);
-      const float beta = vv2 > 0.f ? 2.f / vv2 : 0.f;
-      // p_c = beta (sum_j conj(M[j][c]) v_j), v = x except v_{k+1} = x_{k+1} - alpha.
-      const float2 acc = make_float2(ax + by, bx - ay);
-      float2 ck1 = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int r = KB + 1; r <= KE && r < NP; ++r) ck1 = (r == k + 1) ? col[r] : ck1;
-      const float2 corr = cmul_conj(ck1, make_float2(-al.x, -al.y));
-      const bool live = c > k;
-      const float2 p = live ? make_float2(beta * (acc.x + corr.x), beta * (acc.y + corr.y)) : make_float2(0.f, 0.f);
-      float2 vc = make_float2(0.f, 0.f);
-      if (live) {
-        const float4 xc = xd[c];
-        vc = c == k + 1 ? v1 : make_float2(xc.x, xc.z);
-      }
+      const float2 p = live ? make_float2(beta * (ax + by), beta * (bx - ay)) : make_float2(0.f, 0.f);
       float kk = fmaf(vc.x, p.x, vc.y * p.y);                       // Re(conj(v_c) p_c)
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) kk += __shfl_xor_sync(TASER_FULL_MASK, kk, o);
@@ -393,14 +454,6 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
         Mj = sp_fma(sp_pack(u.x, u.y), nVa, Mj);
         Mj = sp_fma(sp_pack(u.z, u.w), nVb, Mj);
         sp_unpack(Mj, col[j].x, col[j].y);
-      }
-      // v_{k+1} = x_{k+1} - alpha: add alpha conj(w_c) to row k+1
-#pragma unroll
-      for (int r = KB + 1; r <= KE && r < NP; ++r) {
-        if (r == k + 1) {
-          col[r].x += fmaf(al.x, w.x, al.y * w.y);
-          col[r].y += fmaf(al.y, w.x, -al.x * w.y);
-        }
       }
       __syncwarp();
     }
@@ -445,7 +498,7 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
       hi = nhi;
     }
   }
-  const float nrm = 0.5f * (lo + hi);
+  const float nrm = 0.5f * (lo + hi) * pow2f(ex);
   if (active && gl == 0) {
     tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
     if (nrm_out != nullptr) nrm_out[inst] = nrm;

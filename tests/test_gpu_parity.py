@@ -208,6 +208,35 @@ def test_step_size_closed_forms(T):
         np.testing.assert_allclose(tau.cpu().numpy()[0], 0.5 / w, rtol=1e-5)
 
 
+@pytest.mark.parametrize("scale", [2.0 ** -70, 1e-30, 1.0, 1e30])
+def test_step_size_scale_and_rank(T, scale):
+    """||c A|| = |c| ||A|| over 120 decades, on rank-deficient matrices whose Householder
+    steps leave pure rounding residue (rank 1 and 2, the zero matrix), through the generic
+    two-sided search, the semidefinite one, and the complex Hermitian form of QPSK T~."""
+    rng = np.random.default_rng(11)
+    for N in (3, 9, 17, 33, 65):
+        s = rng.choice([-1.0, 1.0], size=N)
+        u, v = rng.standard_normal(N), rng.standard_normal(N)
+        cases = [(np.outer(s, s), float(N), "mimo_bpsk"), (-np.outer(s, s), float(N), "jed_bpsk"),
+                 (np.outer(u, u) + np.outer(v, v), None, "mimo_bpsk"), (np.zeros((N, N)), 0.0, "mimo_bpsk")]
+        for M, w, hint in cases:
+            w = O.spectral_norm(M[None])[0] if w is None else w
+            Ms = (M * scale).astype(np.float32)
+            for structure in (T.GENERIC, hint):
+                tau, nrm = T.step_size(to_dev(Ms[None])[0], 0.5, structure=structure)
+                got = float(nrm.cpu().numpy()[0])
+                assert np.isfinite(got), (N, structure)
+                if w == 0.0:
+                    assert got == 0.0 and float(tau.cpu().numpy()[0]) == 0.0
+                else:
+                    np.testing.assert_allclose(got / scale, w, rtol=1e-5, err_msg=str((N, structure)))
+    X, y, _ = problem("mimo_qpsk", 9, 64, 8, 3.0, 8)
+    Tt = O.detect("mimo_qpsk", X, y, ALPHA, 1)["T_tilde"]
+    Ts = (Tt * scale).astype(np.float32)
+    tau, nrm = T.step_size(to_dev(Ts)[0], ALPHA, structure="mimo_qpsk")
+    np.testing.assert_allclose(nrm.cpu().numpy() / scale, O.spectral_norm(Tt), rtol=1e-5)
+
+
 @pytest.mark.parametrize("N", [2, 5, 9, 16, 17, 30, 33, 47, 65])
 def test_step_size_matches_oracle(T, N):
     rng = np.random.default_rng(N)
