@@ -15,15 +15,20 @@
 //
 // Mapping as in the FP32 detector: one warp per instance, lane j owns column j of L~, V,
 // G, Vbar and Lbar; the column j of T~ stays in registers; rows of L~ and Vbar are
-// broadcast from shared memory, so both products keep the triangular skip.
+// broadcast from shared memory, so both products keep the triangular skip.  Shared memory
+// holds only the lower triangle: row i takes i + 1 floats rounded up to a multiple of 4
+// (16-byte rows for the float4 broadcasts), 612 floats at bucket 32 instead of 33 x 36.
 #include "common.cuh"
 
 namespace taser {
 
+// Offset (floats) of row i of a packed lower-triangular matrix whose row r holds
+// (r + 1) rounded up to 4 floats: with i = 4q + m, 16 q (q + 1) / 2 + 4 m (q + 1).
+__host__ __device__ constexpr int tri_off(int i) { return 4 * ((i >> 2) + 1) * (2 * (i >> 2) + (i & 3)); }
+
 template <int NB>
 struct UfCfg {
-  static constexpr int S = NB + 4;                  // smem row stride (floats)
-  static constexpr int MAT = (NB + 1) * S;          // one bucket matrix in smem
+  static constexpr int MAT = tri_off(NB + 1);       // one bucket matrix in smem (rows 0..NB)
   static constexpr int WARPS = 4;
 };
 
@@ -31,7 +36,7 @@ struct UfCfg {
 template <int NB>
 __device__ __forceinline__ float tri_row(const float* R, int i, const float (&t)[NB + 1]) {
   float acc = 0.f;
-  const float* row = R + i * UfCfg<NB>::S;
+  const float* row = R + tri_off(i);
 #pragma unroll
   for (int k4 = 0; k4 <= NB; k4 += 4) {
     if (k4 > i) break;
@@ -53,7 +58,7 @@ __device__ __forceinline__ void forward_step(const float* Lin, float* Lout, floa
 #pragma unroll
   for (int i = 0; i <= NB; ++i) {
     const float g = 2.f * tri_row<NB>(Lin, i, tcol);
-    v[i] = (i >= j) ? fmaf(-tau, g, Lin[i * UfCfg<NB>::S + j]) : 0.f;
+    v[i] = (i >= j) ? fmaf(-tau, g, Lin[tri_off(i) + j]) : 0.f;
   }
   float n2 = 0.f;
 #pragma unroll
@@ -62,7 +67,7 @@ __device__ __forceinline__ void forward_step(const float* Lin, float* Lout, floa
 #pragma unroll
   for (int i = 0; i <= NB; ++i) {
     l[i] = v[i] * sc;
-    Lout[i * UfCfg<NB>::S + j] = l[i];
+    if (i >= j) Lout[tri_off(i) + j] = l[i];
   }
 }
 
@@ -79,8 +84,8 @@ template <int NB>
 __device__ __forceinline__ void init_diag(float* L, int j, float Dj, float DN, int lane) {
   for (int idx = lane; idx < UfCfg<NB>::MAT; idx += 32) L[idx] = 0.f;
   __syncwarp();
-  if (j < NB) L[j * UfCfg<NB>::S + j] = Dj;
-  if (lane == 0) L[NB * UfCfg<NB>::S + NB] = DN;
+  if (j < NB) L[tri_off(j) + j] = Dj;
+  if (lane == 0) L[tri_off(NB) + NB] = DN;
   __syncwarp();
 }
 
@@ -117,10 +122,14 @@ unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, cons
     if (t % c == 0 && ckpt != nullptr) {
       // checkpoint L~(t) in real indices, full N x N with zeros above the diagonal
       float* out = ckpt + (inst * n_ckpt + t / c) * (int64_t)N * N;
+      const int dq = 32 / N, dm = 32 % N;
+      int r = lane / N, cc = lane % N;                 // (r, cc) of element e, advanced by 32
       for (int e = lane; e < N * N; e += 32) {
-        const int r = e / N, cc = e % N;
         const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
-        out[e] = cur[br * C::S + bc];
+        out[e] = bc <= br ? cur[tri_off(br) + bc] : 0.f;
+        r += dq;
+        cc += dm;
+        if (cc >= N) { cc -= N; ++r; }
       }
     }
     const float tau = alpha_t[t] * inv;
@@ -171,10 +180,14 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
       const float* in = ckpt + (inst * n_ckpt + kc) * (int64_t)N * N;
       for (int idx = lane; idx < C::MAT; idx += 32) seg[idx] = 0.f;
       __syncwarp();
+      const int dq = 32 / N, dm = 32 % N;
+      int r = lane / N, cc = lane % N;                 // (r, cc) of element e, advanced by 32
       for (int e = lane; e < N * N; e += 32) {
-        const int r = e / N, cc = e % N;
         const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
-        seg[br * C::S + bc] = in[e];
+        if (bc <= br) seg[tri_off(br) + bc] = in[e];
+        r += dq;
+        cc += dm;
+        if (cc >= N) { cc -= N; ++r; }
       }
       __syncwarp();
     }
@@ -192,11 +205,11 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
     for (int s = t1; s > t0; --s) {
       const float* Lin = seg + (s - 1 - t0) * C::MAT;
       const float tau = alpha_t[s - 1] * inv;
-      float g[NB + 1], v[NB + 1], vbar[NB + 1];
+      float g[NB + 1], v[NB + 1];
 #pragma unroll
       for (int i = 0; i <= NB; ++i) {
         g[i] = (j < NB) ? 2.f * tri_row<NB>(Lin, i, tcol) : 0.f;
-        v[i] = (i >= j && j < NB) ? fmaf(-tau, g[i], Lin[i * C::S + (j < NB ? j : 0)]) : 0.f;
+        v[i] = (i >= j && j < NB) ? fmaf(-tau, g[i], Lin[tri_off(i) + (j < NB ? j : 0)]) : 0.f;
       }
       float n2 = 0.f;
 #pragma unroll
@@ -206,24 +219,25 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
 #pragma unroll
       for (int i = 0; i <= NB; ++i) proj = fmaf(v[i] * rn, lbar[i], proj);
       const float f = Dj * rn;
+      // Vbar overwrites Lbar(s) in place.
       float tb = 0.f;
 #pragma unroll
       for (int i = 0; i <= NB; ++i) {
-        vbar[i] = (i >= j) ? f * fmaf(-v[i] * rn, proj, lbar[i]) : 0.f;
-        tb = fmaf(vbar[i], g[i], tb);
+        lbar[i] = (i >= j) ? f * fmaf(-v[i] * rn, proj, lbar[i]) : 0.f;
+        tb = fmaf(lbar[i], g[i], tb);
       }
       tb = -warp_sum(tb);
       if (lane == 0) grad_tau[inst * t_max + (s - 1)] = tb;
       // Lbar(s-1) = tril(Vbar - tau Vbar (2 T~)): rows of Vbar through shared memory
 #pragma unroll
       for (int i = 0; i <= NB; ++i)
-        if (j < NB) vb[i * C::S + j] = vbar[i];
-      if (lane == 0) vb[NB * C::S + NB] = 0.f;   // column N of Vbar is zero
+        if (j < NB && i >= j) vb[tri_off(i) + j] = lbar[i];
+      if (lane == 0) vb[tri_off(NB) + NB] = 0.f;   // column N of Vbar is zero
       __syncwarp();
 #pragma unroll
       for (int i = 0; i <= NB; ++i) {
         const float p = 2.f * tri_row<NB>(vb, i, tcol);
-        lbar[i] = (i >= j && j < NB) ? fmaf(-tau, p, vbar[i]) : 0.f;
+        lbar[i] = (i >= j && j < NB) ? fmaf(-tau, p, lbar[i]) : 0.f;
       }
       __syncwarp();
     }
@@ -277,7 +291,7 @@ static cudaError_t launch_unfolded(bool backward, int64_t batch, int N, const fl
 // Shared memory the backward kernel needs for checkpoint spacing c at size N (bytes).
 size_t unfolded_backward_smem(int N, int c) {
   const int NB = bucket_of(N);
-  return (size_t)4 * (c + 2) * (NB + 1) * (NB + 4) * sizeof(float);
+  return (size_t)4 * (c + 2) * tri_off(NB + 1) * sizeof(float);
 }
 
 cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,
