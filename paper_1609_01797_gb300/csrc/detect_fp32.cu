@@ -1,9 +1,12 @@
 // FP32 TASER iterations (Algorithm 1) on the CUDA cores.
 //
 // Mapping: lane j of an instance owns variable column j of L~ and V.  Column j of
-// T^ = -2 tau T~ (negated so every product is one FFMA) lives in registers for all
-// t_max iterations; the rows of L~(t-1) are broadcast from shared memory (one LDS.128
-// feeds four FFMAs).  Column norms of the prox (Sec. III-C) are then lane-local sums.
+// T^ = -2 tau T~ (negated so every product is one FMA) lives in registers for all
+// t_max iterations, as packed pairs (T^_kj, T^_k+1,j); the rows of L~(t-1) are broadcast
+// from shared memory, and one LDS.128 feeds two packed f32x2 FMAs, which keep the even-
+// and odd-k partial sums of the row.  The stored L~ is zero above the diagonal and in the
+// row padding, so the last float4 of a row needs no masking.  Column norms of the prox
+// (Sec. III-C) are then lane-local sums.
 // Buckets: NB = 8 / 16 -> 4 / 2 instances per warp, NB = 32 -> one instance per warp,
 // NB = 64 -> two warps per instance (the second warp skips rows < 32, all above its
 // columns).  L~ never leaves the SM between iterations.
@@ -14,6 +17,21 @@
 #include "common.cuh"
 
 namespace taser {
+
+// Packed FP32 pairs (fma.rn.f32x2): each half is the IEEE result of the scalar FMA.
+__device__ __forceinline__ uint64_t fp_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void fp_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t fp_fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
 
 template <int NB>
 struct Fp32Cfg {
@@ -51,14 +69,26 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
   const float tau = active ? *jb.tau : 0.f;
   const float m2tau = -2.f * tau;
 
-  // Column j of T^ = -2 tau T~ (T~ symmetric: T~[k][j] read row by row, coalesced).
-  float tn[NB + 1];
+  // Column j of T^ = -2 tau T~ (T~ symmetric: T~[k][j] read row by row, coalesced), as
+  // pairs (k, k + 1); pairs past k = NB are zero.
+  constexpr int NP2 = NB / 2 + 2;
+  uint64_t tn2[NP2];
+  float tNB = 0.f;
 #pragma unroll
-  for (int k = 0; k <= NB; ++k) {
-    const int kr = bucket_to_real(k, N, NB);
-    float v = 0.f;
-    if (active && jr >= 0 && kr >= 0) v = jb.T[(int64_t)kr * N + jr];
-    tn[k] = m2tau * v;
+  for (int p = 0; p < NP2; ++p) {
+    float v2[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * p + h;
+      float v = 0.f;
+      if (k <= NB) {
+        const int kr = bucket_to_real(k, N, NB);
+        if (active && jr >= 0 && kr >= 0) v = jb.T[(int64_t)kr * N + jr];
+      }
+      v2[h] = m2tau * v;
+      if (k == NB) tNB = v2[h];
+    }
+    tn2[p] = fp_pack(v2[0], v2[1]);
   }
   const float Dj = (active && jr >= 0) ? jb.D[jr] : 0.f;
   const float DN = active ? jb.D[N - 1] : 0.f;
@@ -107,7 +137,7 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
 
   for (int t = 0; t < t_loop; ++t) {
     // Partial of V_NN = L~_NN (1 - 2 tau T~_NN) - 2 tau sum_k L~_Nk T~_kN from L~(t-1).
-    float part = l[NB] * tn[NB];
+    float part = l[NB] * tNB;
 #pragma unroll
     for (int o = C::G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(TASER_FULL_MASK, part, o);
 
@@ -118,17 +148,17 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
         l[i] = 0.f;  // rows above every column of this warp
         continue;
       }
-      float acc = l[i];
+      uint64_t acc2 = fp_pack(l[i], 0.f);
       const float* row = Ls + i * C::S;
 #pragma unroll
       for (int k4 = 0; k4 <= i; k4 += 4) {
         const float4 q = *reinterpret_cast<const float4*>(row + k4);
-        acc = fmaf(q.x, tn[k4], acc);
-        if (k4 + 1 <= i) acc = fmaf(q.y, tn[k4 + 1], acc);
-        if (k4 + 2 <= i) acc = fmaf(q.z, tn[k4 + 2], acc);
-        if (k4 + 3 <= i) acc = fmaf(q.w, tn[k4 + 3], acc);
+        acc2 = fp_fma2(fp_pack(q.x, q.y), tn2[k4 / 2], acc2);
+        if (k4 + 2 <= i) acc2 = fp_fma2(fp_pack(q.z, q.w), tn2[k4 / 2 + 1], acc2);
       }
-      l[i] = (i >= j) ? acc : 0.f;  // l now holds column j of V
+      float a0, a1;
+      fp_unpack(acc2, a0, a1);
+      l[i] = (i >= j) ? a0 + a1 : 0.f;  // l now holds column j of V
     }
     if constexpr (NB > 32) {
       if (lane == 0) xs[warp % C::WPI] = part;
@@ -183,7 +213,7 @@ __device__ __forceinline__ void fp32_lane_layout(int warp, int lane, int& local_
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128, NB == 32 ? 4 : 1)
+__global__ void __launch_bounds__(128, NB == 32 ? 3 : 1)
 detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
                    const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
                    int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags) {
@@ -202,7 +232,7 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
 // Persistent, queue-fed: each warp (each warp pair for NB = 64) pops the next items of
 // its bucket until the queue is empty.
 template <int NB>
-__global__ void __launch_bounds__(128, NB == 32 ? 4 : 1)
+__global__ void __launch_bounds__(128, NB == 32 ? 3 : 1)
 detect_fp32_queue_kernel(Queue q, const float* __restrict__ T_pool, const float* __restrict__ D_pool,
                          const float* __restrict__ tau, int literal, float* __restrict__ L_pool,
                          int8_t* __restrict__ s_pool, uint32_t* __restrict__ flags) {

@@ -96,6 +96,29 @@ def test_checkpoint_spacing_does_not_change_the_gradient(T):
         assert torch.equal(gt, ref), c
 
 
+def test_wide_checkpoint_spacing_at_n33(T):
+    """At N = 33 the packed shared-memory iterates admit c up to 21 (c + 2 iterates per
+    warp); every spacing gives the same gradient bit for bit, and c = 22 is rejected on the
+    host before any launch."""
+    t_max = 21
+    Tt, D, inv, alpha, truth = setup(40, 128, 16, "qpsk", t_max, seed=9)
+    dT, dD, dinv, dalpha = dev(Tt, D, inv, alpha)
+    g_soft = dev((np.random.default_rng(2).standard_normal((40, 32)) * 1e-3).astype(np.float32))[0]
+    ref = None
+    for c in (1, 5, 20, 21):
+        soft, _, ckpt = T.unfolded_forward(dT, dD, dinv, dalpha, c)
+        gt, _ = T.unfolded_backward(dT, dD, dinv, dalpha, c, ckpt, g_soft)
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = gt.clone()
+        assert torch.equal(gt, ref), c
+    Tt2, D2, inv2, alpha2, _ = setup(8, 128, 16, "qpsk", 22, seed=3)
+    a2 = dev(Tt2, D2, inv2, alpha2)
+    soft, _, ckpt = T.unfolded_forward(*a2, 22)
+    with pytest.raises(Exception, match="shared memory"):
+        T.unfolded_backward(*a2, 22, ckpt, torch.zeros_like(soft))
+
+
 def test_unfolded_training_lowers_the_loss(T):
     """A few Adam steps on alpha_t with fresh seeded QPSK 128x16 batches (N = 33,
     t_max = 10, c = 4) lower the MSE between the soft last row and the symbols."""
