@@ -32,28 +32,52 @@ struct UfCfg {
   static constexpr int WARPS = 4;
 };
 
-// acc_i = sum_{k <= i} R[i][k] t[k] for the rows i of a lower-triangular smem matrix R.
+// Packed FP32 pairs (fma.rn.f32x2): each half is the IEEE result of the scalar FMA.
+__device__ __forceinline__ uint64_t uf_pack(float lo, float hi) {
+  uint64_t r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void uf_unpack(uint64_t v, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+__device__ __forceinline__ uint64_t uf_fma2(uint64_t a, uint64_t b, uint64_t c) {
+  uint64_t d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+
+// Column j of T~ as pairs (T~_kj, T~_k+1,j), zero past k = NB.
 template <int NB>
-__device__ __forceinline__ float tri_row(const float* R, int i, const float (&t)[NB + 1]) {
-  float acc = 0.f;
+struct TPairs {
+  static constexpr int P = NB / 2 + 2;
+  uint64_t v[P];
+};
+
+// acc_i = sum_{k <= i} R[i][k] t[k] for the rows i of a lower-triangular smem matrix R whose
+// row padding is zero: one LDS.128 feeds two packed FMAs (even and odd k), and the last
+// float4 of a row needs no mask.
+template <int NB>
+__device__ __forceinline__ float tri_row(const float* R, int i, const TPairs<NB>& t) {
+  uint64_t acc = 0ull;
   const float* row = R + tri_off(i);
 #pragma unroll
   for (int k4 = 0; k4 <= NB; k4 += 4) {
     if (k4 > i) break;
     const float4 q = *reinterpret_cast<const float4*>(row + k4);
-    acc = fmaf(q.x, t[k4], acc);
-    if (k4 + 1 <= i) acc = fmaf(q.y, t[k4 + 1], acc);
-    if (k4 + 2 <= i) acc = fmaf(q.z, t[k4 + 2], acc);
-    if (k4 + 3 <= i) acc = fmaf(q.w, t[k4 + 3], acc);
+    acc = uf_fma2(uf_pack(q.x, q.y), t.v[k4 / 2], acc);
+    if (k4 + 2 <= i) acc = uf_fma2(uf_pack(q.z, q.w), t.v[k4 / 2 + 1], acc);
   }
-  return acc;
+  float a0, a1;
+  uf_unpack(acc, a0, a1);
+  return a0 + a1;
 }
 
 // One forward step on the smem iterate Lin -> Lout (column j of the result also
 // returned in l[]).  Returns nothing; l holds L~(t) column j on exit.
 template <int NB>
 __device__ __forceinline__ void forward_step(const float* Lin, float* Lout, float (&l)[NB + 1],
-                                             const float (&tcol)[NB + 1], float tau, float Dj, int j) {
+                                             const TPairs<NB>& tcol, float tau, float Dj, int j) {
   float v[NB + 1];
 #pragma unroll
   for (int i = 0; i <= NB; ++i) {
@@ -72,11 +96,17 @@ __device__ __forceinline__ void forward_step(const float* Lin, float* Lout, floa
 }
 
 template <int NB>
-__device__ __forceinline__ void load_tcol(float (&tcol)[NB + 1], const float* T, int N, int jr) {
+__device__ __forceinline__ void load_tcol(TPairs<NB>& tcol, const float* T, int N, int jr) {
 #pragma unroll
-  for (int k = 0; k <= NB; ++k) {
-    const int kr = bucket_to_real(k, N, NB);
-    tcol[k] = (jr >= 0 && kr >= 0) ? T[(int64_t)kr * N + jr] : 0.f;
+  for (int p = 0; p < TPairs<NB>::P; ++p) {
+    float v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = 2 * p + h;
+      const int kr = k <= NB ? bucket_to_real(k, N, NB) : -1;
+      v[h] = (jr >= 0 && kr >= 0) ? T[(int64_t)kr * N + jr] : 0.f;
+    }
+    tcol.v[p] = uf_pack(v[0], v[1]);
   }
 }
 
@@ -90,7 +120,7 @@ __device__ __forceinline__ void init_diag(float* L, int j, float Dj, float DN, i
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 5)
 unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
                         const float* __restrict__ inv_norm, const float* __restrict__ alpha_t, int t_max, int c,
                         float* __restrict__ ckpt, float* __restrict__ soft, int8_t* __restrict__ s_hat) {
@@ -104,7 +134,7 @@ unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, cons
   const int j = lane;                                  // lanes >= NB carry zero columns
   const int jr = j < N - 1 ? j : -1;
   const float* T = Tt + inst * (int64_t)N * N;
-  float tcol[NB + 1];
+  TPairs<NB> tcol;
   load_tcol<NB>(tcol, T, N, jr);
   const float Dj = jr >= 0 ? Dg[inst * N + jr] : 0.f;
   const float DN = Dg[inst * N + N - 1];
@@ -162,10 +192,13 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
   const int j = lane;
   const int jr = j < N - 1 ? j : -1;
   const float* T = Tt + inst * (int64_t)N * N;
-  float tcol[NB + 1];
+  TPairs<NB> tcol;
   load_tcol<NB>(tcol, T, N, jr);
   const float Dj = jr >= 0 ? Dg[inst * N + jr] : 0.f;
   const float inv = inv_norm[inst];
+  // The rows of Vbar are written on and below the diagonal only: zero the padding once.
+  for (int idx = lane; idx < C::MAT; idx += 32) vb[idx] = 0.f;
+  __syncwarp();
   const int n_ckpt = (t_max + c - 1) / c;
   // Lbar(t_max): only the last row, dloss/dL~_{N,k} = dloss/dx_k / D_k
   float lbar[NB + 1];
