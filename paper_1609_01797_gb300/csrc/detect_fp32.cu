@@ -18,20 +18,6 @@
 
 namespace taser {
 
-// Packed FP32 pairs (fma.rn.f32x2): each half is the IEEE result of the scalar FMA.
-__device__ __forceinline__ uint64_t fp_pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void fp_unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t fp_fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 
 template <int NB>
 struct Fp32Cfg {
@@ -88,7 +74,7 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
       v2[h] = m2tau * v;
       if (k == NB) tNB = v2[h];
     }
-    tn2[p] = fp_pack(v2[0], v2[1]);
+    tn2[p] = f2pack(v2[0], v2[1]);
   }
   const float Dj = (active && jr >= 0) ? jb.D[jr] : 0.f;
   const float DN = active ? jb.D[N - 1] : 0.f;
@@ -148,16 +134,16 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
         l[i] = 0.f;  // rows above every column of this warp
         continue;
       }
-      uint64_t acc2 = fp_pack(l[i], 0.f);
+      uint64_t acc2 = f2pack(l[i], 0.f);
       const float* row = Ls + i * C::S;
 #pragma unroll
       for (int k4 = 0; k4 <= i; k4 += 4) {
         const float4 q = *reinterpret_cast<const float4*>(row + k4);
-        acc2 = fp_fma2(fp_pack(q.x, q.y), tn2[k4 / 2], acc2);
-        if (k4 + 2 <= i) acc2 = fp_fma2(fp_pack(q.z, q.w), tn2[k4 / 2 + 1], acc2);
+        acc2 = f2fma(f2pack(q.x, q.y), tn2[k4 / 2], acc2);
+        if (k4 + 2 <= i) acc2 = f2fma(f2pack(q.z, q.w), tn2[k4 / 2 + 1], acc2);
       }
       float a0, a1;
-      fp_unpack(acc2, a0, a1);
+      f2unpack(acc2, a0, a1);
       l[i] = (i >= j) ? a0 + a1 : 0.f;  // l now holds column j of V
     }
     if constexpr (NB > 32) {

@@ -48,27 +48,8 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
   }
 }
 
-// Packed FP32 pairs (fma/mul/add.rn.f32x2): one instruction for the two columns
-// (2tq, 2tq + 1) an accumulator register pair holds.  Each half is the IEEE result of the
-// scalar operation.
-__device__ __forceinline__ uint64_t f2pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void f2unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t f2fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t f2mul(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
+// The packed f32x2 operations (common.cuh) handle the two columns (2tq, 2tq + 1) an
+// accumulator register pair holds with one instruction.
 // acc[e], acc[e + 1] = f(acc[e], acc[e + 1]) for a packed operation f.
 #define TASER_PAIR_APPLY(arr, e, expr)          \
   do {                                          \

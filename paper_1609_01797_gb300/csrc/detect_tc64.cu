@@ -44,27 +44,9 @@ __device__ __forceinline__ void mma64(float (&d)[4], const uint32_t (&a)[4], con
   }
 }
 
-__device__ __forceinline__ uint64_t p2pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void p2unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t p2fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ uint64_t p2mul(uint64_t a, uint64_t b) {
-  uint64_t d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
 // (v[e], v[e + 1]) *= sc2, as one packed multiply.
 __device__ __forceinline__ void p2scale(float* v, uint64_t sc2) {
-  p2unpack(p2mul(p2pack(v[0], v[1]), sc2), v[0], v[1]);
+  f2unpack(f2mul(f2pack(v[0], v[1]), sc2), v[0], v[1]);
 }
 
 // Shared exchange area of one instance (floats): [parity][ row64 A pairs (32 u32) |
@@ -109,7 +91,7 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
     }
   uint64_t tN2[4];
 #pragma unroll
-  for (int n = 0; n < 4; ++n) tN2[n] = p2pack(tN[n][0], tN[n][1]);
+  for (int n = 0; n < 4; ++n) tN2[n] = f2pack(tN[n][0], tN[n][1]);
   const float tnNN = m2tau * T[(int64_t)(N - 1) * N + (N - 1)];
   const float DN = jb.D[N - 1];
   // Column scales are owned per lane for columns 8g + 2tq + p (after the reduction).
@@ -146,9 +128,9 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
     // --- exchange 1: this warp's half of row 64 (A pairs, lanes g == 0) and V_NN partial
     uint64_t part2 = 0ull;
 #pragma unroll
-    for (int n = 0; n < 4; ++n) part2 = p2fma(p2pack(rw[n][0], rw[n][1]), tN2[n], part2);
+    for (int n = 0; n < 4; ++n) part2 = f2fma(f2pack(rw[n][0], rw[n][1]), tN2[n], part2);
     float part, part_hi;
-    p2unpack(part2, part, part_hi);
+    f2unpack(part2, part, part_hi);
     part += part_hi;
     part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
     part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
@@ -199,11 +181,11 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
         a[kt][1] = 0u;
         a[kt][3] = 0u;
       }
-      const uint64_t lnn2 = p2pack(LNN, LNN);
+      const uint64_t lnn2 = f2pack(LNN, LNN);
 #pragma unroll
       for (int n = 0; n < 4; ++n) {
         // k = N term in FP32 (tN is 0 for g != 0)
-        p2unpack(p2fma(lnn2, tN2[n], p2pack(rw[n][0], rw[n][1])), rw[n][0], rw[n][1]);
+        f2unpack(f2fma(lnn2, tN2[n], f2pack(rw[n][0], rw[n][1])), rw[n][0], rw[n][1]);
 #pragma unroll
         for (int kt = 0; kt < 4; ++kt) mma64<FP16>(rw[n], a[kt], bf[kt][RN0 + n]);
       }
@@ -217,8 +199,8 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
     for (int n = 0; n < 8; ++n) {
       uint64_t v2 = 0ull;
       auto sq = [&](float a, float b) {
-        const uint64_t x = p2pack(a, b);
-        v2 = p2fma(x, x, v2);
+        const uint64_t x = f2pack(a, b);
+        v2 = f2fma(x, x, v2);
       };
       if (n < NLO) {
         sq(lo[n][2], lo[n][3]);
@@ -229,7 +211,7 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
         sq(hi[n][0], hi[n][1]);
       }
       if (n >= RN0 && n < RN0 + 4) sq(rw[n - RN0][0], rw[n - RN0][1]);
-      p2unpack(v2, s[2 * n], s[2 * n + 1]);
+      f2unpack(v2, s[2 * n], s[2 * n + 1]);
     }
     // transpose-reduce over g: lane ends with columns 8g + 2tq + {0, 1}
 #pragma unroll
@@ -262,7 +244,7 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
     }
 #pragma unroll
     for (int n = 0; n < 8; ++n) {
-      const uint64_t sc2 = p2pack(__shfl_sync(TASER_FULL_MASK, sc_own[0], 4 * n + tq),
+      const uint64_t sc2 = f2pack(__shfl_sync(TASER_FULL_MASK, sc_own[0], 4 * n + tq),
                                   __shfl_sync(TASER_FULL_MASK, sc_own[1], 4 * n + tq));
       if (n < NLO) {
         p2scale(&lo[n][0], sc2);

@@ -303,22 +303,9 @@ __device__ __forceinline__ float2 cmul_conj(float2 a, float2 b) {  // conj(a) * 
   return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
 }
 
-// Packed FP32 pairs (fma.rn.f32x2): the complex multiply-adds of the reduction run as pair
-// operations on {re, im} against duplicated pairs {v, v} read from shared memory.
-__device__ __forceinline__ uint64_t sp_pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void sp_unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t sp_fma(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-
+// The complex multiply-adds of the reduction and of the rank-2 update run as packed f32x2
+// operations (common.cuh) on {re, im} against duplicated pairs {v, v} read from shared
+// memory.
 template <int UV, bool NEG>
 __global__ void __launch_bounds__(128)
 spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float alpha, float* __restrict__ tau,
@@ -424,14 +411,14 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
 #pragma unroll
       for (int j = KB + 1; j < NP; ++j) {
         const float4 q = xd[j];
-        const uint64_t X1 = sp_pack(q.x, q.y), X2 = sp_pack(q.z, q.w);
-        const uint64_t Mj = sp_pack(col[j].x, col[j].y);
-        A = sp_fma(Mj, X1, A);
-        Bs = sp_fma(Mj, X2, Bs);
+        const uint64_t X1 = f2pack(q.x, q.y), X2 = f2pack(q.z, q.w);
+        const uint64_t Mj = f2pack(col[j].x, col[j].y);
+        A = f2fma(Mj, X1, A);
+        Bs = f2fma(Mj, X2, Bs);
       }
       float ax, ay, bx, by;
-      sp_unpack(A, ax, ay);
-      sp_unpack(Bs, bx, by);
+      f2unpack(A, ax, ay);
+      f2unpack(Bs, bx, by);
       const float2 p = live ? make_float2(beta * (ax + by), beta * (bx - ay)) : make_float2(0.f, 0.f);
       float kk = fmaf(vc.x, p.x, vc.y * p.y);                       // Re(conj(v_c) p_c)
 #pragma unroll
@@ -443,17 +430,17 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
       __syncwarp();
       // M[j][c] -= v_j conj(w_c) + w_j conj(v_c), as four pair FMAs per row:
       //   v conj(w) = {Re v, Re v}{Re w, -Im w} + {Im v, Im v}{Im w, Re w}.
-      const uint64_t nWa = sp_pack(-w.x, w.y), nWb = sp_pack(-w.y, -w.x);
-      const uint64_t nVa = sp_pack(-vc.x, vc.y), nVb = sp_pack(-vc.y, -vc.x);
+      const uint64_t nWa = f2pack(-w.x, w.y), nWb = f2pack(-w.y, -w.x);
+      const uint64_t nVa = f2pack(-vc.x, vc.y), nVb = f2pack(-vc.y, -vc.x);
 #pragma unroll
       for (int j = KB + 1; j < NP; ++j) {
         const float4 q = xd[j], u = wd[j];
-        uint64_t Mj = sp_pack(col[j].x, col[j].y);
-        Mj = sp_fma(sp_pack(q.x, q.y), nWa, Mj);
-        Mj = sp_fma(sp_pack(q.z, q.w), nWb, Mj);
-        Mj = sp_fma(sp_pack(u.x, u.y), nVa, Mj);
-        Mj = sp_fma(sp_pack(u.z, u.w), nVb, Mj);
-        sp_unpack(Mj, col[j].x, col[j].y);
+        uint64_t Mj = f2pack(col[j].x, col[j].y);
+        Mj = f2fma(f2pack(q.x, q.y), nWa, Mj);
+        Mj = f2fma(f2pack(q.z, q.w), nWb, Mj);
+        Mj = f2fma(f2pack(u.x, u.y), nVa, Mj);
+        Mj = f2fma(f2pack(u.z, u.w), nVb, Mj);
+        f2unpack(Mj, col[j].x, col[j].y);
       }
       __syncwarp();
     }

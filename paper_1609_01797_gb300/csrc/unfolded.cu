@@ -32,20 +32,6 @@ struct UfCfg {
   static constexpr int WARPS = 4;
 };
 
-// Packed FP32 pairs (fma.rn.f32x2): each half is the IEEE result of the scalar FMA.
-__device__ __forceinline__ uint64_t uf_pack(float lo, float hi) {
-  uint64_t r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
-  return r;
-}
-__device__ __forceinline__ void uf_unpack(uint64_t v, float& lo, float& hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
-__device__ __forceinline__ uint64_t uf_fma2(uint64_t a, uint64_t b, uint64_t c) {
-  uint64_t d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
 
 // Column j of T~ as pairs (T~_kj, T~_k+1,j), zero past k = NB.
 template <int NB>
@@ -65,11 +51,11 @@ __device__ __forceinline__ float tri_row(const float* R, int i, const TPairs<NB>
   for (int k4 = 0; k4 <= NB; k4 += 4) {
     if (k4 > i) break;
     const float4 q = *reinterpret_cast<const float4*>(row + k4);
-    acc = uf_fma2(uf_pack(q.x, q.y), t.v[k4 / 2], acc);
-    if (k4 + 2 <= i) acc = uf_fma2(uf_pack(q.z, q.w), t.v[k4 / 2 + 1], acc);
+    acc = f2fma(f2pack(q.x, q.y), t.v[k4 / 2], acc);
+    if (k4 + 2 <= i) acc = f2fma(f2pack(q.z, q.w), t.v[k4 / 2 + 1], acc);
   }
   float a0, a1;
-  uf_unpack(acc, a0, a1);
+  f2unpack(acc, a0, a1);
   return a0 + a1;
 }
 
@@ -106,7 +92,7 @@ __device__ __forceinline__ void load_tcol(TPairs<NB>& tcol, const float* T, int 
       const int kr = k <= NB ? bucket_to_real(k, N, NB) : -1;
       v[h] = (jr >= 0 && kr >= 0) ? T[(int64_t)kr * N + jr] : 0.f;
     }
-    tcol.v[p] = uf_pack(v[0], v[1]);
+    tcol.v[p] = f2pack(v[0], v[1]);
   }
 }
 
