@@ -160,7 +160,8 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   #pragma unroll
           for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
       // One cp.async group per chunk (empty past the end), so the wait for chunk c always
-      // leaves the NS - 2 younger groups in flight.
+      // leaves the NS - 2 younger groups in flight; chunk c + NS - 1 is issued before chunk
+      // c is consumed (into the buffer of chunk c - 1), so NS - 1 chunks load during the MMAs.
   #pragma unroll
       for (int s = 0; s < C::NS - 1; ++s) {
         if (s < nchunks) stage(s); else cp_async_commit();
@@ -201,6 +202,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
         }
   #pragma unroll
         for (int j = 0; j < NT; ++j) sc[j] = pow2i(ex[j]);
+        if (chunk + C::NS - 1 < nchunks) stage(chunk + C::NS - 1); else cp_async_commit();
   #pragma unroll
         for (int ks = 0; ks < CH / 16; ++ks) {
           // B fragments of n-tile j: k = 2tq, 2tq+1, 2tq+8, 2tq+9 are staged rows tq, tq+4,
@@ -241,8 +243,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
             }
           }
         }
-        __syncwarp();  // every lane has read this buffer
-        if (chunk + C::NS - 1 < nchunks) stage(chunk + C::NS - 1); else cp_async_commit();
+        __syncwarp();  // every lane has read this buffer before it is refilled
       }
       bool finite = true;
   #pragma unroll
@@ -272,10 +273,14 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
           for (int e = 0; e < 4; ++e) {
             const int h = e >> 1;
             const int er = 2 * i + h < NT ? ex[2 * i + h < NT ? 2 * i + h : 0] : 0;
-            // 2^sh as one exact multiply while it is a normal float, else ldexpf.
             const int sh = -(er + exc[j][e & 1]);
-            const float v = acc[i][j][e] * pow2i(min(max(sh, -126), 127));
-            acc[i][j][e] = (sh >= -126 && sh <= 127) ? v : ldexpf(acc[i][j][e], sh);
+            if constexpr (MP == 17) {
+              // 2^sh as one exact multiply while it is a normal float, else ldexpf.
+              const float v = acc[i][j][e] * pow2i(min(max(sh, -126), 127));
+              acc[i][j][e] = (sh >= -126 && sh <= 127) ? v : ldexpf(acc[i][j][e], sh);
+            } else {
+              acc[i][j][e] = ldexpf(acc[i][j][e], sh);
+            }
           }
         }
     }
