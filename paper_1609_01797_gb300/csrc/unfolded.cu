@@ -33,6 +33,12 @@ struct UfCfg {
 };
 
 
+// 4-byte asynchronous global -> shared copy (completed by cp.async.wait_all).
+__device__ __forceinline__ void uf_cp_async4(float* smem_dst, const float* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
 // Column j of T~ as pairs (T~_kj, T~_k+1,j), zero past k = NB.
 template <int NB>
 struct TPairs {
@@ -194,7 +200,8 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
 
   for (int kc = n_ckpt - 1; kc >= 0; --kc) {
     const int t0 = kc * c, t1 = min(t0 + c, t_max);
-    // L~(t0) from the checkpoint into seg[0] (bucket layout)
+    // L~(t0) from the checkpoint into seg[0] (bucket layout), as asynchronous copies that
+    // are all in flight together.
     {
       const float* in = ckpt + (inst * n_ckpt + kc) * (int64_t)N * N;
       for (int idx = lane; idx < C::MAT; idx += 32) seg[idx] = 0.f;
@@ -203,11 +210,12 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
       int r = lane / N, cc = lane % N;                 // (r, cc) of element e, advanced by 32
       for (int e = lane; e < N * N; e += 32) {
         const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
-        if (bc <= br) seg[tri_off(br) + bc] = in[e];
+        if (bc <= br) uf_cp_async4(seg + tri_off(br) + bc, in + e);
         r += dq;
         cc += dm;
         if (cc >= N) { cc -= N; ++r; }
       }
+      asm volatile("cp.async.wait_all;" ::: "memory");
       __syncwarp();
     }
     // recompute L~(t0+1) .. L~(t1-1) into seg[1..]
