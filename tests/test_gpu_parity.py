@@ -137,7 +137,10 @@ BUILD_CASES = [("mimo_bpsk", 32, 8), ("mimo_bpsk", 7, 3), ("mimo_bpsk", 64, 16),
                ("mimo_qpsk", 128, 16), ("mimo_qpsk", 32, 4), ("mimo_qpsk", 64, 8), ("mimo_qpsk", 13, 5),
                ("mimo_qpsk", 256, 32), ("mimo_qpsk", 200, 12), ("jed_bpsk", 16, 16), ("jed_bpsk", 16, 32),
                ("jed_bpsk", 5, 2), ("jed_bpsk", 40, 9), ("jed_qpsk", 16, 16), ("jed_qpsk", 16, 32),
-               ("jed_qpsk", 5, 2), ("jed_qpsk", 40, 9), ("jed_qpsk", 64, 17)]
+               ("jed_qpsk", 5, 2), ("jed_qpsk", 40, 9), ("jed_qpsk", 64, 17),
+               # 17 complex columns stage 16-row chunks: ragged last chunks (37 = 16 + 16 + 5,
+               # 33 = 16 + 16 + 1), fewer than 32 rows for the scale search (20), one partial chunk (9)
+               ("mimo_qpsk", 37, 16), ("mimo_qpsk", 20, 16), ("mimo_qpsk", 9, 10), ("jed_bpsk", 33, 16)]
 
 
 @pytest.mark.parametrize("kind,B,M", BUILD_CASES)
