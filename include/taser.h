@@ -231,9 +231,10 @@ taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, 
  * sum_n grad_tau[n][t] inv_norm[n] in a fixed reduction order.  Each segment of c
  * iterations is recomputed from ckpt (same arguments as the forward call) and
  * differentiated in reverse; the gradient flows through the soft last row only.
- * Needs 4 (c + 2) M(NB) floats of shared memory per block, NB the bucket of N and M(NB)
- * the packed lower triangle of an (NB + 1)-row matrix whose rows are padded to 4 floats
- * (60 / 180 / 612 at NB = 8 / 16 / 32; c <= 21 at N = 33); larger c is rejected.
+ * Needs (c + 2) M(NB) floats of shared memory per block (one warp, one instance), NB the
+ * bucket of N and M(NB) the packed lower triangle of an (NB + 1)-row matrix whose rows are
+ * padded to 4 floats (60 / 180 / 612 at NB = 8 / 16 / 32; c <= 92 at N = 33); larger c is
+ * rejected.
  */
 taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde, const float* D,
                                      const float* inv_norm, const float* alpha_t, int t_max, int c,

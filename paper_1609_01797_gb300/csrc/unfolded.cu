@@ -29,7 +29,11 @@ __host__ __device__ constexpr int tri_off(int i) { return 4 * ((i >> 2) + 1) * (
 template <int NB>
 struct UfCfg {
   static constexpr int MAT = tri_off(NB + 1);       // one bucket matrix in smem (rows 0..NB)
-  static constexpr int WARPS = 4;
+  static constexpr int WARPS = 4;                   // forward: warps per block
+  // Adjoint: one warp per block, so a block needs only its own (c + 2) packed iterates and
+  // c can reach 92 at N = 33; 12 blocks per SM (3 warps per scheduler) at 168 registers.
+  static constexpr int BWD_WARPS = 1;
+  static constexpr int BWD_MIN_BLOCKS = 12;
 };
 
 
@@ -168,7 +172,7 @@ unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, cons
 }
 
 template <int NB>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(32 * UfCfg<NB>::BWD_WARPS, UfCfg<NB>::BWD_MIN_BLOCKS)
 unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
                          const float* __restrict__ inv_norm, const float* __restrict__ alpha_t, int t_max, int c,
                          const float* __restrict__ ckpt, const float* __restrict__ grad_soft,
@@ -176,7 +180,7 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
   using C = UfCfg<NB>;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
+  const int64_t inst = (int64_t)blockIdx.x * C::BWD_WARPS + warp;
   if (inst >= batch) return;
   // per warp: c + 1 iterates of the segment and the Vbar rows
   float* seg = smem + (int64_t)warp * (c + 2) * C::MAT;
@@ -232,11 +236,16 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
     for (int s = t1; s > t0; --s) {
       const float* Lin = seg + (s - 1 - t0) * C::MAT;
       const float tau = alpha_t[s - 1] * inv;
-      float g[NB + 1], v[NB + 1];
+      // G is not kept: taubar = <Vbar, G> = f (<G, Lbar> - rn proj <G, V>) (Lbar is zero
+      // above the diagonal), so the two sums are taken while G is formed.
+      float v[NB + 1];
+      float gl = 0.f, gv = 0.f;
 #pragma unroll
       for (int i = 0; i <= NB; ++i) {
-        g[i] = (j < NB) ? 2.f * tri_row<NB>(Lin, i, tcol) : 0.f;
-        v[i] = (i >= j && j < NB) ? fmaf(-tau, g[i], Lin[tri_off(i) + (j < NB ? j : 0)]) : 0.f;
+        const float gi = (j < NB) ? 2.f * tri_row<NB>(Lin, i, tcol) : 0.f;
+        v[i] = (i >= j && j < NB) ? fmaf(-tau, gi, Lin[tri_off(i) + (j < NB ? j : 0)]) : 0.f;
+        gl = fmaf(gi, lbar[i], gl);
+        gv = fmaf(gi, v[i], gv);
       }
       float n2 = 0.f;
 #pragma unroll
@@ -247,13 +256,9 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
       for (int i = 0; i <= NB; ++i) proj = fmaf(v[i] * rn, lbar[i], proj);
       const float f = Dj * rn;
       // Vbar overwrites Lbar(s) in place.
-      float tb = 0.f;
 #pragma unroll
-      for (int i = 0; i <= NB; ++i) {
-        lbar[i] = (i >= j) ? f * fmaf(-v[i] * rn, proj, lbar[i]) : 0.f;
-        tb = fmaf(lbar[i], g[i], tb);
-      }
-      tb = -warp_sum(tb);
+      for (int i = 0; i <= NB; ++i) lbar[i] = (i >= j) ? f * fmaf(-v[i] * rn, proj, lbar[i]) : 0.f;
+      const float tb = -warp_sum(f * fmaf(-rn * proj, gv, gl));
       if (lane == 0) grad_tau[inst * t_max + (s - 1)] = tb;
       // Lbar(s-1) = tril(Vbar - tau Vbar (2 T~)): rows of Vbar through shared memory
 #pragma unroll
@@ -304,13 +309,14 @@ static cudaError_t launch_unfolded(bool backward, int64_t batch, int N, const fl
     unfolded_forward_kernel<NB><<<(unsigned)blocks, 128, smem, st>>>(batch, N, Tt, D, inv_norm, alpha_t, t_max, c,
                                                                      ckpt, soft, s_hat);
   } else {
-    const size_t smem = (size_t)C::WARPS * (c + 2) * C::MAT * sizeof(float);
+    const size_t smem = (size_t)C::BWD_WARPS * (c + 2) * C::MAT * sizeof(float);
     if (smem > 227 * 1024) return cudaErrorInvalidValue;
     cudaError_t e = cudaFuncSetAttribute(unfolded_backward_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    unfolded_backward_kernel<NB><<<(unsigned)blocks, 128, smem, st>>>(batch, N, Tt, D, inv_norm, alpha_t, t_max, c,
-                                                                      ckpt, grad_soft, grad_tau);
+    const int64_t bblocks = (batch + C::BWD_WARPS - 1) / C::BWD_WARPS;
+    unfolded_backward_kernel<NB><<<(unsigned)bblocks, 32 * C::BWD_WARPS, smem, st>>>(
+        batch, N, Tt, D, inv_norm, alpha_t, t_max, c, ckpt, grad_soft, grad_tau);
   }
   return cudaGetLastError();
 }
@@ -318,7 +324,7 @@ static cudaError_t launch_unfolded(bool backward, int64_t batch, int N, const fl
 // Shared memory the backward kernel needs for checkpoint spacing c at size N (bytes).
 size_t unfolded_backward_smem(int N, int c) {
   const int NB = bucket_of(N);
-  return (size_t)4 * (c + 2) * tri_off(NB + 1) * sizeof(float);
+  return (size_t)UfCfg<32>::BWD_WARPS * (c + 2) * tri_off(NB + 1) * sizeof(float);
 }
 
 cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,

@@ -97,9 +97,9 @@ def test_checkpoint_spacing_does_not_change_the_gradient(T):
 
 
 def test_wide_checkpoint_spacing_at_n33(T):
-    """At N = 33 the packed shared-memory iterates admit c up to 21 (c + 2 iterates per
-    warp); every spacing gives the same gradient bit for bit, and c = 22 is rejected on the
-    host before any launch."""
+    """At N = 33 the packed shared-memory iterates admit c up to 92 (c + 2 iterates of 612
+    floats for a one-warp block); every spacing gives the same gradient bit for bit, and
+    c = 93 is rejected on the host before any launch."""
     t_max = 21
     Tt, D, inv, alpha, truth = setup(40, 128, 16, "qpsk", t_max, seed=9)
     dT, dD, dinv, dalpha = dev(Tt, D, inv, alpha)
@@ -112,11 +112,11 @@ def test_wide_checkpoint_spacing_at_n33(T):
         if ref is None:
             ref = gt.clone()
         assert torch.equal(gt, ref), c
-    Tt2, D2, inv2, alpha2, _ = setup(8, 128, 16, "qpsk", 22, seed=3)
+    Tt2, D2, inv2, alpha2, _ = setup(8, 128, 16, "qpsk", 93, seed=3)
     a2 = dev(Tt2, D2, inv2, alpha2)
-    soft, _, ckpt = T.unfolded_forward(*a2, 22)
+    soft, _, ckpt = T.unfolded_forward(*a2, 93)
     with pytest.raises(Exception, match="shared memory"):
-        T.unfolded_backward(*a2, 22, ckpt, torch.zeros_like(soft))
+        T.unfolded_backward(*a2, 93, ckpt, torch.zeros_like(soft))
 
 
 def test_unfolded_training_lowers_the_loss(T):
