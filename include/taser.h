@@ -256,9 +256,11 @@ typedef struct {
 /* Per-bucket launch tuning of taser_detect_uneven (buckets N <= 9, 17, 33, 65). */
 typedef struct {
     int32_t blocks_per_sm[4];   /* persistent blocks per SM, 0 = as many as fit */
-    int32_t pop[4];             /* items a warp takes per queue pop in the tensor-core
-                                   N <= 17 and N <= 33 buckets, 0 = 1 (defaults without
-                                   tuning: 4 and 2); the other buckets ignore it */
+    int32_t pop[4];             /* items a warp (pair) takes per queue pop, 0 = the
+                                   default (tensor cores: 4 at N <= 17, 2 at N <= 33, else
+                                   1; FP32: one warp-load); FP32 rounds it up to whole
+                                   warp-loads (4 / 2 / 1 / 1 items at N <= 9 / 17 / 33 /
+                                   65); the fixed-point path ignores it */
 } taser_uneven_tuning;
 
 /* Device workspace (bytes) taser_detect_uneven needs for n_items items. */
@@ -271,8 +273,11 @@ size_t taser_uneven_workspace_bytes(int64_t n_items);
  * a counting sort (three short kernels) builds a size-bucketed work queue in `workspace`
  * (items grouped by bucket N <= 9 / 17 / 33 / 65, then by t_max, longest first), and one
  * persistent kernel per bucket takes its items: from an atomic counter, or (the N <= 65
- * tensor-core bucket) at a fixed stride per warp pair over the sorted list.  Precisions as
- * in taser_detect (tensor cores for N >= 10, FP32 below).
+ * tensor-core bucket) at a fixed stride per warp pair over the sorted list.  The bucket
+ * kernels run on two internal streams forked from and joined back into `stream` (the
+ * N <= 65 bucket at high priority, the others after one another at low priority, filling
+ * the SMs the first frees in its tail); calls from one host thread share these streams.
+ * Precisions as in taser_detect (tensor cores for N >= 10, FP32 below).
  *   items     device array of n_items taser_item.
  *   T_pool, D_pool, tau (float [n_items]), L_pool (may be NULL), s_pool: device pools
  *             addressed by the items' offsets.

@@ -200,7 +200,7 @@ def uneven_workspace_bytes(n_items):
     return int(lib().taser_uneven_workspace_bytes(int(n_items)))
 
 
-def tuning(blocks_per_sm=(0, 0, 0, 0), pop=(1, 1, 1, 1)):
+def tuning(blocks_per_sm=(0, 0, 0, 0), pop=(0, 0, 0, 0)):
     t = UnevenTuning()
     for b in range(4):
         t.blocks_per_sm[b] = int(blocks_per_sm[b])

@@ -216,10 +216,11 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
 }
 
 // Persistent, queue-fed: each warp (each warp pair for NB = 64) pops the next items of
-// its bucket until the queue is empty.
+// its bucket until the queue is empty, `rounds` warp-loads per pop (one atomic per
+// rounds x IPW items: short jobs would otherwise queue on the counter).
 template <int NB>
 __global__ void __launch_bounds__(128, NB == 32 ? 3 : 1)
-detect_fp32_queue_kernel(Queue q, const float* __restrict__ T_pool, const float* __restrict__ D_pool,
+detect_fp32_queue_kernel(Queue q, int rounds, const float* __restrict__ T_pool, const float* __restrict__ D_pool,
                          const float* __restrict__ tau, int literal, float* __restrict__ L_pool,
                          int8_t* __restrict__ s_pool, uint32_t* __restrict__ flags) {
   using C = Fp32Cfg<NB>;
@@ -232,27 +233,32 @@ detect_fp32_queue_kernel(Queue q, const float* __restrict__ T_pool, const float*
   int* pop_slot = reinterpret_cast<int*>(xs + 2);
   const int count = q.count();
   for (;;) {
+    constexpr int PER_ROUND = NB <= 32 ? C::IPW : 1;            // items of one warp-load
     int base;
     if constexpr (NB <= 32) {
       base = 0;
-      if (lane == 0) base = q.pop(C::IPW);
+      if (lane == 0) base = q.pop(PER_ROUND * rounds);
       base = __shfl_sync(TASER_FULL_MASK, base, 0);
     } else {
-      if ((warp % C::WPI) == 0 && lane == 0) *pop_slot = q.pop(1);
+      if ((warp % C::WPI) == 0 && lane == 0) *pop_slot = q.pop(rounds);
       sync_instance<NB>(1 + local_inst);
       base = *pop_slot;
       sync_instance<NB>(1 + local_inst);
     }
     if (base >= count) break;                                   // uniform per warp (pair)
-    const int pos = NB <= 32 ? base + (lane / C::G) : base;
-    const bool active = pos < count;
-    const int idx = active ? q.item_at(pos) : 0;
-    const taser_item it = q.items[idx];
-    const Job jb = item_job(it, idx, T_pool, D_pool, tau, L_pool, s_pool, flags);
-    int t_loop = active ? jb.t_max : 0;
-    if constexpr (NB <= 32) t_loop = __reduce_max_sync(TASER_FULL_MASK, t_loop);
-    fp32_run<NB, (Fp32Cfg<NB>::IPW > 1)>(jb, active, t_loop, Ls, xs, j, lane, warp, 1 + local_inst, literal);
-    sync_instance<NB>(1 + local_inst);
+    for (int r = 0; r < rounds; ++r) {
+      const int b0 = base + r * PER_ROUND;
+      if (b0 >= count) break;                                   // uniform per warp (pair)
+      const int pos = NB <= 32 ? b0 + (lane / C::G) : b0;
+      const bool active = pos < count;
+      const int idx = active ? q.item_at(pos) : 0;
+      const taser_item it = q.items[idx];
+      const Job jb = item_job(it, idx, T_pool, D_pool, tau, L_pool, s_pool, flags);
+      int t_loop = active ? jb.t_max : 0;
+      if constexpr (NB <= 32) t_loop = __reduce_max_sync(TASER_FULL_MASK, t_loop);
+      fp32_run<NB, (Fp32Cfg<NB>::IPW > 1)>(jb, active, t_loop, Ls, xs, j, lane, warp, 1 + local_inst, literal);
+      sync_instance<NB>(1 + local_inst);
+    }
   }
 }
 
@@ -284,9 +290,9 @@ cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, c
 
 // Queue-fed launch for bucket NB with `blocks` persistent blocks.
 template <int NB>
-static cudaError_t launch_fp32_queue(const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
-                                     const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
-                                     cudaStream_t st) {
+static cudaError_t launch_fp32_queue(const Queue& q, int blocks_per_sm, int rounds, const float* T_pool,
+                                     const float* D_pool, const float* tau, int literal, float* L_pool,
+                                     int8_t* s_pool, uint32_t* flags, cudaStream_t st) {
   using C = Fp32Cfg<NB>;
   const size_t smem = C::SMEM_BYTES;
   if (smem > 48 * 1024) {
@@ -300,19 +306,23 @@ static cudaError_t launch_fp32_queue(const Queue& q, int blocks_per_sm, const fl
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_fp32_queue_kernel<NB>, 128, smem);
   if (e != cudaSuccess) return e;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
-  detect_fp32_queue_kernel<NB><<<sms * per_sm, 128, smem, st>>>(q, T_pool, D_pool, tau, literal, L_pool, s_pool,
-                                                               flags);
+  detect_fp32_queue_kernel<NB><<<sms * per_sm, 128, smem, st>>>(q, rounds > 0 ? rounds : 1, T_pool, D_pool, tau,
+                                                               literal, L_pool, s_pool, flags);
   return cudaGetLastError();
 }
 
-cudaError_t detect_fp32_queue(int nb, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
-                              const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
-                              cudaStream_t st) {
+cudaError_t detect_fp32_queue(int nb, const Queue& q, int blocks_per_sm, int rounds, const float* T_pool,
+                              const float* D_pool, const float* tau, int literal, float* L_pool, int8_t* s_pool,
+                              uint32_t* flags, cudaStream_t st) {
   switch (nb) {
-    case 8: return launch_fp32_queue<8>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
-    case 16: return launch_fp32_queue<16>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
-    case 32: return launch_fp32_queue<32>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
-    default: return launch_fp32_queue<64>(q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    case 8:
+      return launch_fp32_queue<8>(q, blocks_per_sm, rounds, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    case 16:
+      return launch_fp32_queue<16>(q, blocks_per_sm, rounds, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    case 32:
+      return launch_fp32_queue<32>(q, blocks_per_sm, rounds, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+    default:
+      return launch_fp32_queue<64>(q, blocks_per_sm, rounds, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
   }
 }
 

@@ -6,14 +6,17 @@
 
 namespace taser {
 
-cudaError_t detect_fp32_queue(int nb, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
-                              const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
-                              cudaStream_t st);
+cudaError_t detect_fp32_queue(int nb, const Queue& q, int blocks_per_sm, int rounds, const float* T_pool,
+                              const float* D_pool, const float* tau, int literal, float* L_pool, int8_t* s_pool,
+                              uint32_t* flags, cudaStream_t st);
 cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm, int pop, const float* T_pool,
                             const float* D_pool, const float* tau, int literal, float* L_pool, int8_t* s_pool,
                             uint32_t* flags, cudaStream_t st);
 
 constexpr int kClasses = 64;               // t_max classes per bucket (64 = 64 and more)
+// Items per queue pop when no tuning is given, per bucket N <= 9 / 17 / 33 / 65.
+constexpr int kTcPopDefault[4] = {1, 4, 2, 1};
+constexpr int kFp32PopDefault[4] = {4, 2, 1, 1};   // one warp-load
 constexpr int kKeys = 4 * kClasses;
 constexpr int kMetaInts = 16;              // start[4], count[4], head[4], spare
 static_assert(kMetaInts * sizeof(int) <= 256, "the queue metadata lives in the 256 bytes after the item list");
@@ -114,6 +117,41 @@ size_t uneven_workspace_bytes(int64_t n_items) {
 cudaError_t detect_fx14_queue(int nb, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
                               const float* tau, float* L_pool, int8_t* s_pool, uint32_t* flags, cudaStream_t st);
 
+namespace {
+// Streams (per host thread and device) on which the bucket kernels run after the sort: the
+// N <= 65 bucket, the longest, on a high-priority stream; the other three back to back on
+// a low-priority one, so their blocks take the SMs that the heavy kernel's blocks free in
+// its tail.  Forked from and joined back into the caller's stream with events, which a
+// CUDA graph capture records as a branch.  Created on first use and kept.
+struct BucketLanes {
+  cudaStream_t hi = nullptr, lo = nullptr;
+  cudaEvent_t fork = nullptr, join_hi = nullptr, join_lo = nullptr;
+};
+cudaError_t bucket_lanes(BucketLanes*& out) {
+  thread_local BucketLanes lanes[64];
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  BucketLanes& b = lanes[dev];
+  if (b.hi == nullptr) {
+    int least = 0, greatest = 0;
+    e = cudaDeviceGetStreamPriorityRange(&least, &greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.hi, cudaStreamNonBlocking, greatest);
+    if (e == cudaSuccess) e = cudaStreamCreateWithPriority(&b.lo, cudaStreamNonBlocking, least);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.fork, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_hi, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b.join_lo, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      b = BucketLanes{};
+      return e;
+    }
+  }
+  out = &b;
+  return cudaSuccess;
+}
+}  // namespace
+
 cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float* T_pool, const float* D_pool,
                           const float* tau, int precision, int literal, float* L_pool, int8_t* s_pool,
                           uint32_t* flags, void* workspace, const taser_uneven_tuning* tuning, cudaStream_t st) {
@@ -132,9 +170,16 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
     bucket_scatter_kernel<<<sort_blocks, kSortThreads, 0, st>>>((int)n_items, items, goffs, list);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
+  BucketLanes* lanes = nullptr;
+  e = bucket_lanes(lanes);
+  if (e == cudaSuccess) e = cudaEventRecord(lanes->fork, st);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(lanes->hi, lanes->fork, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(lanes->lo, lanes->fork, 0);
+  if (e != cudaSuccess) return e;
   const int order[4] = {3, 2, 1, 0};        // the heaviest bucket first
   for (int oi = 0; oi < 4; ++oi) {
     const int b = order[oi];
+    const cudaStream_t bs = b == 3 ? lanes->hi : lanes->lo;
     const int nb = 8 << b;
     Queue q;
     q.items = items;
@@ -142,19 +187,30 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
     q.meta = meta;
     q.b = b;
     const int bps = tuning != nullptr ? tuning->blocks_per_sm[b] : 0;
-    // Default items per pop: short N <= 17 jobs amortise the queue atomic over four items.
-    const int pop = tuning != nullptr ? tuning->pop[b] : (b == 1 ? 4 : b == 2 ? 2 : 1);
+    const bool tc = precision != TASER_FP32 && precision != TASER_FIXED14 && nb >= 16;
+    // Default items per pop (measured on the 200,000-item batch): the short tensor-core
+    // jobs take 4 (N <= 17) or 2 (N <= 33) items per atomic; on the FP32 path larger pops
+    // than one warp-load gained nothing.
+    const int pop_default = tc ? kTcPopDefault[b] : kFp32PopDefault[b];
+    const int pop = tuning != nullptr && tuning->pop[b] > 0 ? tuning->pop[b] : pop_default;
     if (precision == TASER_FIXED14) {
-      e = detect_fx14_queue(nb, q, bps, T_pool, D_pool, tau, L_pool, s_pool, flags, st);
-    } else if (precision != TASER_FP32 && nb >= 16) {
+      e = detect_fx14_queue(nb, q, bps, T_pool, D_pool, tau, L_pool, s_pool, flags, bs);
+    } else if (tc) {
       e = detect_tc_queue(nb, precision == TASER_FP16_TC, q, bps, pop, T_pool, D_pool, tau, literal, L_pool, s_pool,
-                          flags, st);
+                          flags, bs);
     } else {
-      e = detect_fp32_queue(nb, q, bps, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+      // FP32: whole warp-loads per pop (4 / 2 / 1 / 1 items at N <= 9 / 17 / 33 / 65).
+      const int per_load = nb <= 8 ? 4 : (nb == 16 ? 2 : 1);
+      e = detect_fp32_queue(nb, q, bps, (pop + per_load - 1) / per_load, T_pool, D_pool, tau, literal, L_pool,
+                            s_pool, flags, bs);
     }
     if (e != cudaSuccess) return e;
   }
-  return cudaSuccess;
+  e = cudaEventRecord(lanes->join_hi, lanes->hi);
+  if (e == cudaSuccess) e = cudaEventRecord(lanes->join_lo, lanes->lo);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, lanes->join_hi, 0);
+  if (e == cudaSuccess) e = cudaStreamWaitEvent(st, lanes->join_lo, 0);
+  return e;
 }
 
 }  // namespace taser
