@@ -1,7 +1,7 @@
 """Autotuner of the uneven-batch launch (taser_detect_uneven).
 
 Per size bucket (N <= 9, 17, 33, 65) it times the candidate launch shapes (persistent
-blocks per SM; items a warp takes per queue pop on the tensor-core path) on a sample
+blocks per SM; items a warp takes per queue pop, 0 = the library's default) on a sample
 batch with CUDA events, one bucket at a time with the others at their current best, and
 keeps the fastest.  The result is a taser_uneven_tuning (and a JSON-able dict).
 """
@@ -28,10 +28,10 @@ def _time(fn, repeats):
 
 
 def tune_uneven(items, T_pool, D_pool, tau, s_pool, workspace, precision="bf16_tc", blocks_candidates=(1, 2, 3, 4, 0),
-                pop_candidates=(1, 2, 4), repeats=5):
+                pop_candidates=(0, 1, 2, 4, 8), repeats=5):
     """Returns (taser_uneven_tuning, report dict with the timings in ms)."""
     bps = [0, 0, 0, 0]
-    pop = [1, 1, 1, 1]
+    pop = [0, 0, 0, 0]
     report = {"precision": precision, "buckets": {}}
 
     def run():
@@ -42,9 +42,9 @@ def tune_uneven(items, T_pool, D_pool, tau, s_pool, workspace, precision="bf16_t
     report["default_ms"] = base
     for b in (3, 2, 1, 0):
         best = (base, bps[b], pop[b])
-        tc = precision != "fp32" and b in (1, 2)
+        pops = pop_candidates if precision != "fixed14" and b < 3 else (0,)
         for cand_b in blocks_candidates:
-            for cand_p in (pop_candidates if tc else (1,)):
+            for cand_p in pops:
                 bps[b], pop[b] = cand_b, cand_p
                 t = _time(run, repeats)
                 if t < best[0]:
