@@ -263,6 +263,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
     // Inside a diagonal 16 x 16 block the element (row g + 8h, column 2tq + p + 8h') lies
     // above the diagonal iff h' > h, or h' == h and 2tq + p > g.
     const bool up0 = 2 * tq > g, up1 = 2 * tq + 1 > g;
+    const int src_row0 = 4 * (2 * tq) + (g != 0), src_row1 = 4 * (2 * tq + 1) + (g != 0);
 
     for (int t = 0; t < t_max; ++t) {
       // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
@@ -299,13 +300,44 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
 #pragma unroll
           for (int n = 0; n < NT; ++n) TASER_PAIR_APPLY(acc[M][n], 0, f2fma(lnn2, tN2[n], _x));
         }
+        if (M == MT - 1 && KT >= 2) {
+          // Row N as the transposed product T^ L~_N^T (T^ symmetric): KT m-tiles of output
+          // columns against KT k-tiles, KT^2 mma instead of the KT NT of a 16-row tile with
+          // one live row (4 instead of 8 at NB = 32; at NB = 16 the saved mma costs more in
+          // shuffles than it gains, measured).  The A fragments of T^ are the B fragments
+          // already held; the B operand is the packed row N (column 0; rows g != 0 of the
+          // row-N tile are zero).
+          float d[KT][4];
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
-          if (!C::has_tile(M, n)) continue;
+          for (int mt = 0; mt < KT; ++mt) {
 #pragma unroll
-          for (int kt = 0; kt <= C::kmax(M); ++kt) {
-            if (M == MT - 1) mma16816_top<FP16>(acc[M][n], a[kt], bf[kt][n]);
-            else mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+            for (int e = 0; e < 4; ++e) d[mt][e] = 0.f;
+#pragma unroll
+            for (int kt = 0; kt < KT; ++kt) {
+              const uint32_t at[4] = {bf[kt][2 * mt][0], bf[kt][2 * mt + 1][0], bf[kt][2 * mt][1],
+                                      bf[kt][2 * mt + 1][1]};
+              const uint32_t bt[2] = {a[kt][0], a[kt][2]};
+              mma16816<FP16>(d[mt], at, bt);
+            }
+          }
+          // Column c = 8n + 2tq + p of row N sits in D column 0 at lane 4 (c mod 8), element
+          // 2 (n mod 2) of m-tile n / 2; lanes g != 0 read a lane with tq = 1 (D column 2,
+          // zero), so their row-N tile stays zero.
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            const float v0 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row0);
+            const float v1 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row1);
+            TASER_PAIR_APPLY(acc[M][n], 0, f2fma(f2pack(1.f, 1.f), f2pack(v0, v1), _x));
+          }
+        } else {
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            if (!C::has_tile(M, n)) continue;
+#pragma unroll
+            for (int kt = 0; kt <= C::kmax(M); ++kt) {
+              if (M == MT - 1) mma16816_top<FP16>(acc[M][n], a[kt], bf[kt][n]);
+              else mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+            }
           }
         }
       }
