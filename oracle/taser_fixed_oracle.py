@@ -13,7 +13,8 @@ with 5 fraction bits and stays constant (the hardware keeps L~_NN = D_NN, i.e. t
 LUT of 2^11 entries of 14 bits, 13 of them fraction bits, and the scale unit multiplies
 it by D_jj (Sec. IV-A/B).
 
-Readings where the paper is silent (each is listed in the design doc, F1-F7):
+Readings where the paper is silent (F1-F7; the identifiers are shared with the
+project's design notes):
   F1  Numbers are two's complement and saturate to [-2^13, 2^13 - 1].
   F2  Rounding to a narrower format is round-half-up on the integer grid:
       (a + 2^(k-1)) >> k with an arithmetic (flooring) shift.

@@ -16,7 +16,8 @@ the paper's definitions in the paper's order:
   * Algorithm 1 (TASER): L~(0) = D; V = L~ - tril(2 tau L~ T~); L~ = prox(V)
   * decisions  s_k = sign(L~_{N,k}), k < N              (Algorithm 1 outputs)
 
-Readings taken where the paper is silent or ambiguous (each is listed in the design doc):
+Readings taken where the paper is silent or ambiguous (the identifiers are shared with
+the project's design notes):
   R1  QPSK symbols are (+-1 +-j)/sqrt2: T is built from the effective channel H/sqrt2
       so that the relaxed vector is exactly in {+-1}^N.
   R2  The augmented "1" coordinate is the last index N; for JED the pilot column

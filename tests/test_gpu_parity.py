@@ -1,12 +1,20 @@
 """CUDA path vs the FP64 oracle, element by element, through the C ABI.
 
-Tolerances (written here, derived in the design doc):
+Tolerances and where they come from:
   * FP32 iterations: relative Frobenius error of L~ <= 1e-5 per instance; decisions
-    identical wherever |L~_{N,k}| > 1e-3 ||l~_N||.
+    identical wherever |L~_{N,k}| > 1e-3 ||l~_N||.  The inputs themselves are rounded to
+    FP32 (T~ to about 3e-7, tau to about 1e-6 relative), and in FP64 such perturbations
+    move L~(t_max) by at most 4e-7 relative over 20 iterations with alpha <= 0.6; the
+    prox renormalises every column each iteration, so rounding does not accumulate
+    beyond a few units of 2^-24 per step.  1e-5 leaves a factor of about 25.
   * BF16 / FP16 tensor-core iterations: relative Frobenius error <= 3e-2; decisions
-    identical wherever |L~_{N,k}| > 5e-2 ||l~_N||.
+    identical wherever |L~_{N,k}| > 5e-2 ||l~_N||.  The operands of L~ T^ carry 8 (BF16)
+    or 11 (FP16) significant bits, so each product term has a relative error up to
+    2^-8; summed over k with FP32 accumulation the error of a row of V is a few 1e-3 of
+    its norm, and the FP32 prox restores the exact column norms each iteration.
   * T~ (FP32 Gram of B complex rows): |T~_gpu - T~| <= 2e-5, D and tau within 1e-5
-    relative.
+    relative (split FP16/TF32 products keep about 2^-22 relative error per term; the
+    sum over B = 256 antennas and the division by D_i D_j stay below 1e-5).
 """
 import numpy as np
 import pytest

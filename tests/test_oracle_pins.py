@@ -309,6 +309,61 @@ def test_convergence_to_a_fixed_point():
     assert (step < 1e-9).all()
 
 
+def test_literal_prox_of_the_last_column_is_the_nearest_point():
+    """Literal mode (reading R7) on the branch V_NN <= 0.  The last column of a lower-
+    triangular V holds V_NN alone, so its sphere of radius D_NN (Eq. 9) is the two-point
+    set {-D_NN, +D_NN}; the nearest point of a negative V_NN is -D_NN, and at the tie
+    V_NN = 0 the reading sign(0) = +1 picks +D_NN.  Every such step is flagged."""
+    rng = np.random.default_rng(81)
+    N = 5
+    vnn = np.array([-2.5, -1e-9, 0.0, 1e-9, 0.7, -0.3])
+    n = len(vnn)
+    V = np.tril(rng.standard_normal((n, N, N)))
+    V[:, -1, -1] = vnn
+    D = rng.uniform(0.5, 3.0, size=(n, N))
+    P, flags = O.prox(V, D, "literal")
+    cand = np.stack([-D[:, -1], D[:, -1]], axis=1)                       # the 1-D sphere
+    best = cand[np.arange(n), np.argmin(np.abs(cand - vnn[:, None]), axis=1)]
+    tie = vnn == 0.0
+    np.testing.assert_array_equal(P[~tie, -1, -1], best[~tie])
+    np.testing.assert_array_equal(P[tie, -1, -1], D[tie, -1])
+    np.testing.assert_array_equal((flags & O.FLAG_LNN_SIGN) != 0, vnn <= 0.0)
+    Pf, ff = O.prox(V, D, "fixed")
+    np.testing.assert_array_equal(Pf[:, -1, -1], D[:, -1])                # mode C: always +D_NN
+    np.testing.assert_array_equal(ff, flags)
+    np.testing.assert_array_equal(Pf[:, :, :-1], P[:, :, :-1])            # other columns unaffected
+
+
+def test_literal_mode_is_symmetric_under_negating_the_last_row():
+    """S = L^T L (the relaxed SDR variable) does not change when the whole last row of L~
+    is negated (its entries enter S only as products L_Nj L_Nk), and neither do the
+    decisions sign(S_Nk) = sign(L~_NN) sign(L~_Nk) of literal mode.  One literal step maps
+    the negated state to the negated step: the gradient row N is linear in row N, the
+    column norms only see squares, and the last column's prox follows sign(V_NN).  Checked
+    on states of real trajectories in which V_NN <= 0 occurs (the unpinned branch)."""
+    w = make_mimo(64, 8, 6, 0.0, "bpsk", seed=82)                 # N = 7, 0 dB, B = 8
+    r = O.detect("mimo_bpsk", w["H"], w["y"], 0.95, 1)
+    Tt, D, tau = r["T_tilde"], r["D"], r["tau"]
+    L, flags, Ls = O.taser(Tt, D, tau, 12, lnn_mode="literal", history=True)
+    hit = (flags & O.FLAG_LNN_SIGN) != 0
+    assert hit.sum() >= 5
+    assert (np.array([Lt[:, -1, -1] for Lt in Ls]) < 0).any(axis=0)[hit].sum() >= 5
+    for Lt in Ls[1:]:
+        R = Lt.copy()
+        R[:, -1, :] *= -1.0
+        np.testing.assert_allclose(np.matmul(np.transpose(R, (0, 2, 1)), R),
+                                   np.matmul(np.transpose(Lt, (0, 2, 1)), Lt), rtol=0, atol=1e-12)
+        np.testing.assert_array_equal(O.decisions(R, "literal"), O.decisions(Lt, "literal"))
+        step, _ = O.prox(Lt - tau[:, None, None] * O.gradient(Lt, Tt), D, "literal")
+        step_r, _ = O.prox(R - tau[:, None, None] * O.gradient(R, Tt), D, "literal")
+        mirrored = step.copy()
+        mirrored[:, -1, :] *= -1.0
+        # the mirror holds exactly wherever V_NN != 0 (sign(0) = +1 breaks the symmetry)
+        vnn = (Lt - tau[:, None, None] * O.gradient(Lt, Tt))[:, -1, -1]
+        ok = vnn != 0.0
+        np.testing.assert_allclose(step_r[ok], mirrored[ok], rtol=0, atol=1e-12)
+
+
 def test_modes_agree_while_vnn_positive():
     """Reading R7: literal and fixed modes coincide whenever V_NN > 0."""
     w = make_mimo(30, 64, 8, 8.0, "qpsk", seed=43)
