@@ -39,11 +39,16 @@ def parse_args():
     ap.add_argument("--impl", choices=["taser", "reference"], default="taser")
     ap.add_argument("--instances", type=int, default=65536, help="instances per GPU per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample", type=int, default=32768, help="instances timed on the CPU oracle")
-    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff", "unfolded"], default="qpsk128x16",
+    ap.add_argument("--cpu-sample", type=int, default=8192,
+                    help="instances of the workload run through the oracle in one process (1-core rate and the "
+                         "GPU paths' error against FP64)")
+    ap.add_argument("--jed-instances", type=int, default=131072, help="JED instances per SNR point (--workload ber)")
+    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff", "unfolded", "ber"],
+                    default="qpsk128x16",
                     help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20}; tradeoff: SNR "
                          "for 1%% VER vs throughput over t_max = 1..20 for 32x32 BPSK/QPSK; unfolded: training "
-                         "steps of unfolded TASER on batches of 8,192 (none of these is the headline)")
+                         "steps of unfolded TASER on batches of 8,192; ber: BER per SNR point of the GPU paths "
+                         "against the FP64 oracle (none of these is the headline)")
     return ap.parse_args()
 
 
@@ -63,9 +68,9 @@ def build_bytes_per_instance(b, u, n):
 
 def spectral_flops_per_instance(u):
     """Complex Hermitian tridiagonalisation of order n = U + 1 (16/3 n^3 real flops) plus
-    the Sturm multisection (6 rounds x 16 points x n steps x 4 flops)."""
+    the Sturm multisection (5 rounds x 17 points x n steps x 4 flops)."""
     n = u + 1
-    return 16 * n ** 3 // 3 + 6 * 16 * n * 4
+    return 16 * n ** 3 // 3 + 5 * 17 * n * 4
 
 
 KERNEL_SOURCES = {"build": "build_T.cu", "spectral": "spectral.cu", "detect_tc": "detect_tc.cu",
@@ -107,6 +112,194 @@ def clopper_pearson(k, n, conf=0.95):
     lo = 0.0 if k == 0 else float(beta.ppf(a, k, n - k + 1))
     hi = 1.0 if k == n else float(beta.ppf(1 - a, k + 1, n - k))
     return lo, hi
+
+
+# ---------------------------------------------------------------------------------
+# The FP64 oracle on every host core: a pool of spawned processes (safe to create at any
+# time, GPU context or not), each with one BLAS thread.
+# ---------------------------------------------------------------------------------
+def oracle_pool(workers=None):
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    workers = workers or os.cpu_count() or 1
+    return mp.get_context("spawn").Pool(workers), workers
+
+
+BER_CHUNK = 4096
+
+
+def ber_inputs(kind, b, m, snr, n, seed):
+    """Seeded inputs of one chunk: (H or Y, y or None, transmitted signs in decision order)."""
+    from synth import make_jed, make_mimo
+    if kind == "mimo_qpsk":
+        w = make_mimo(n, b, m, snr, "qpsk", seed=seed)
+        return w["H"], w["y"], truth_bits(w)
+    w = make_jed(n, b, m, snr, seed=seed)
+    return w["Y"], None, w["s"][:, 1:]
+
+
+def _oracle_ber_chunk(job):
+    """Pool worker: the oracle on one chunk, compared with the GPU paths' results on the
+    same instances (relative Frobenius error of L~ against FP64, decision agreement)."""
+    from oracle import taser_oracle as O
+    kind, b, m, snr, seed, n, alpha, t_max, gpu = job
+    X, y, truth = ber_inputs(kind, b, m, snr, n, seed)
+    t0 = time.perf_counter()
+    r = O.detect(kind, X, y, alpha, t_max)
+    dt = time.perf_counter() - t0
+    Lo, so = r["L"], r["s_hat"]
+    nrm = np.linalg.norm(Lo, axis=(1, 2))
+    row = Lo[:, -1, :]
+    rown = np.linalg.norm(row, axis=1)
+    out = {"n": n, "oracle_s": dt, "oracle": {"bit_errors": int((so != truth).sum()),
+                                               "vec_errors": int((so != truth).any(axis=1).sum())}}
+    for p, (L, s) in gpu.items():
+        err = np.linalg.norm(L.astype(np.float64) - Lo, axis=(1, 2)) / nrm
+        conf = np.abs(row[:, :-1]) > (1e-3 if p == "fp32" else 5e-2) * rown[:, None]
+        d = s != so
+        out[p] = {"bit_errors": int((s != truth).sum()), "vec_errors": int((s != truth).any(axis=1).sum()),
+                  "discordant_bits": int(d.sum()), "discordant_instances": int(d.any(axis=1).sum()),
+                  "differ_beyond_margin": int(d[conf].sum()), "err": err.astype(np.float32)}
+    return out
+
+
+class OracleTeam:
+    """The FP64 oracle timed on every host core: one spawned process per core, each with
+    its own seeded chunks of the headline workload generated before any timing.  A step
+    releases every worker at once (a barrier) and ends when the last one has finished
+    detect on its chunk, so a step's wall-clock time is that of the slowest core."""
+
+    def __init__(self, workers, per_worker, n_chunks=4, seed=1):
+        import multiprocessing as mp
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[var] = "1"
+        ctx = mp.get_context("spawn")
+        self.workers, self.per_worker = workers, per_worker
+        self.go, self.done = ctx.Barrier(workers + 1), ctx.Barrier(workers + 1)
+        self.procs = [ctx.Process(target=_team_worker, args=(i, per_worker, n_chunks, seed, self.go, self.done),
+                                  daemon=True) for i in range(workers)]
+        for pr in self.procs:
+            pr.start()
+        self.go.wait()            # every worker has generated its chunks
+
+    def step(self):
+        self.go.wait()
+        t0 = time.perf_counter()
+        self.done.wait()
+        return time.perf_counter() - t0
+
+    def close(self):
+        for pr in self.procs:
+            pr.terminate()
+            pr.join()
+
+
+def _team_worker(idx, per_worker, n_chunks, seed, go, done):
+    from oracle import taser_oracle as O
+    chunks = [make_workload(per_worker, seed=seed * 100_003 + 1000 * idx + k) for k in range(n_chunks)]
+    go.wait()
+    k = 0
+    while True:
+        go.wait()
+        w = chunks[k % n_chunks]
+        O.detect("mimo_qpsk", w["H"], w["y"], ALPHA, T_MAX)
+        done.wait()
+        k += 1
+
+
+def run_ber(args):
+    """Equal BER per SNR point (Sec. V-A simulation setup): BER of the FP32, BF16 and FP16
+    GPU paths and of the FP64 oracle on identical seeded instances, with Clopper-Pearson
+    95% intervals, paired discordance counts and each path's relative Frobenius error of
+    L~ against FP64 (max, mean, 99th percentile).  QPSK 128x16, t_max = 20, SNR 0..20 dB
+    (65,536 instances per point by default) and SIMO JED BPSK B = 16, K = 16 and 32,
+    t_max = 20, SNR 0..12 dB (131,072 per point).  The oracle runs on every host core."""
+    pool, workers = oracle_pool()          # spawned before the first GPU call
+    import torch
+    import paper_1609_01797_gb300 as taser
+    dev = torch.device("cuda", 0)
+    n1 = args.instances
+    n2 = args.jed_instances
+    cfgs = [("mimo_qpsk", B, U, np.arange(0.0, 21.0, 2.0), n1, 0),
+            ("jed_bpsk", 16, 16, np.arange(0.0, 13.0, 2.0), n2, 1),
+            ("jed_bpsk", 16, 32, np.arange(0.0, 13.0, 2.0), n2, 2)]
+    paths = ("fp32", "bf16_tc", "fp16_tc")
+    t_start = time.perf_counter()
+    pending = []
+    results = {}
+
+    def collect(block):
+        key, snr, nn, handles = block
+        parts = [h.get() for h in handles]
+        pt = {"snr_db": float(snr), "instances": nn}
+        o_bits = sum(p["oracle"]["bit_errors"] for p in parts)
+        nbits = nn * results[key]["bits_per_instance"]
+        lo, hi = clopper_pearson(o_bits, nbits)
+        pt["oracle"] = {"bit_errors": o_bits, "ber": o_bits / nbits, "ber_ci95": [lo, hi],
+                        "vec_errors": sum(p["oracle"]["vec_errors"] for p in parts),
+                        "oracle_s": sum(p["oracle_s"] for p in parts)}
+        for p in paths:
+            be = sum(q[p]["bit_errors"] for q in parts)
+            err = np.concatenate([q[p]["err"] for q in parts]).astype(np.float64)
+            pt[p] = {"bit_errors": be, "ber": be / nbits, "ber_ci95": list(clopper_pearson(be, nbits)),
+                     "in_oracle_ci95": bool(lo <= be / nbits <= hi),
+                     "vec_errors": sum(q[p]["vec_errors"] for q in parts),
+                     "discordant_bits_vs_oracle": sum(q[p]["discordant_bits"] for q in parts),
+                     "discordant_instances_vs_oracle": sum(q[p]["discordant_instances"] for q in parts),
+                     "decisions_differ_beyond_margin": sum(q[p]["differ_beyond_margin"] for q in parts),
+                     "L_relerr_vs_fp64": {"max": float(err.max()), "mean": float(err.mean()),
+                                          "p99": float(np.quantile(err, 0.99))}}
+        results[key]["points"].append(pt)
+
+    for kind, b, m, snrs, n, ci in cfgs:
+        key = "%s_B%d_%s%d" % (kind, b, "U" if kind == "mimo_qpsk" else "K", m)
+        N = taser.problem_size(kind, m)
+        results[key] = {"kind": kind, "B": b, "U_or_K": m, "N": N, "t_max": T_MAX, "alpha": ALPHA,
+                        "bits_per_instance": N - 1, "points": []}
+        for si, snr in enumerate(snrs):
+            chunks = []
+            for c0 in range(0, n, BER_CHUNK):
+                nc = min(BER_CHUNK, n - c0)
+                seed = 9_000_000 + 100_000 * ci + 1000 * si + c0 // BER_CHUNK
+                chunks.append((c0, nc, seed) + ber_inputs(kind, b, m, float(snr), nc, seed))
+            X = torch.from_numpy(np.concatenate([c[3] for c in chunks])).to(dev)
+            y = torch.from_numpy(np.concatenate([c[4] for c in chunks])).to(dev) if kind == "mimo_qpsk" else None
+            out = taser.build_T(kind, X, y, ALPHA)
+            host = {}
+            for p in paths:
+                s, L, _ = taser.detect(out["T_tilde"], out["D"], out["tau"], T_MAX, p, want_L=True)
+                host[p] = (L.cpu().numpy(), s.cpu().numpy())
+            del X, y, out
+            handles = []
+            for c0, nc, seed, *_ in chunks:
+                gpu = {p: (host[p][0][c0:c0 + nc], host[p][1][c0:c0 + nc]) for p in paths}
+                handles.append(pool.apply_async(_oracle_ber_chunk,
+                                                ((kind, b, m, float(snr), seed, nc, ALPHA, T_MAX, gpu),)))
+            pending.append((key, snr, n, handles))
+            while len(pending) > 2:
+                collect(pending.pop(0))
+    while pending:
+        collect(pending.pop(0))
+    pool.close()
+    pool.join()
+    summary = {}
+    for key, r in results.items():
+        pts = r["points"]
+        summary[key] = {p: {"every_point_in_oracle_ci95": all(pt[p]["in_oracle_ci95"] for pt in pts),
+                            "decisions_differ_beyond_margin": sum(pt[p]["decisions_differ_beyond_margin"]
+                                                                  for pt in pts),
+                            "L_relerr_vs_fp64_max": max(pt[p]["L_relerr_vs_fp64"]["max"] for pt in pts)}
+                        for p in paths}
+    print(json.dumps({"metric": "BER per SNR point: GPU paths vs the FP64 oracle on identical instances "
+                                "(Clopper-Pearson 95%)", "unit": "bit error rate", "n_gpus": 1,
+                      "dtype": "f32, bf16, f16 (GPU); f64 (oracle)", "data": "synthetic",
+                      "config": {"workload": "ber_c1_qpsk128x16_snr0-20_c2_jed16_K16-32_snr0-12",
+                                 "instances_per_snr": {"mimo_qpsk": n1, "jed_bpsk": n2}, "t_max": T_MAX,
+                                 "alpha": ALPHA, "oracle_cores": workers,
+                                 "margins": {"fp32": "1e-3 ||l_N||", "tensor cores": "5e-2 ||l_N||"}},
+                      "wall_s": time.perf_counter() - t_start, "summary": summary, "configs": results}))
+    return 0
 
 
 class ClockSampler:
@@ -178,40 +371,83 @@ def _peak(d, *keys):
     return None
 
 
-def cpu_baseline(w, sample):
-    """The FP64 oracle as it stands, single process, on the first `sample` instances."""
+def cpu_baseline(w, sample, team_per_core=1024):
+    """The FP64 oracle as it stands: on every host core (the reported value: one barrier-
+    synchronised step of `team_per_core` instances per core), and in one process on the
+    first `sample` instances of this workload, whose results also give the GPU path's
+    error against FP64.  Returns (baseline dict, oracle result on the sample)."""
     from oracle import taser_oracle as O
+    workers = os.cpu_count() or 1
+    team = OracleTeam(workers, team_per_core)
+    try:
+        team.step()                      # warm-up (imports, first-touch)
+        t_all = team.step()
+    finally:
+        team.close()
     H, y = w["H"][:sample], w["y"][:sample]
     t0 = time.perf_counter()
-    O.detect("mimo_qpsk", H, y, ALPHA, T_MAX)
+    r = O.detect("mimo_qpsk", H, y, ALPHA, T_MAX)
     dt = time.perf_counter() - t0
-    return {"value": sample / dt, "unit": "detections/s", "cores": 1, "kind": "oracle",
-            "sample": "%d QPSK 128x16 instances of the workload (SNR 0..20 dB), FP64 numpy oracle "
-                      "(T, Jacobi preconditioning, eigvalsh, Algorithm 1), %.1f s" % (sample, dt)}
+    base = {"value": workers * team_per_core / t_all, "unit": "detections/s", "cores": workers, "kind": "oracle",
+            "sample": "%d QPSK 128x16 instances of the workload per host core (%d cores, one process each, "
+                      "inputs generated before timing), FP64 numpy oracle (T, Jacobi preconditioning, eigvalsh, "
+                      "Algorithm 1), %.2f s" % (team_per_core, workers, t_all),
+            "single_core": {"value": sample / dt, "cores": 1,
+                            "sample": "the first %d instances of the workload, one process, %.1f s" % (sample, dt)}}
+    return base, r
+
+
+def error_vs_fp64(taser, bufs, r, sample):
+    """Each GPU path's result against the FP64 oracle on the first `sample` instances of
+    the headline workload (outside the timed region): relative Frobenius error of L~ per
+    instance (max, mean, 99th percentile) and decisions that differ where the oracle's
+    |L~_N,k| exceeds the path's margin (1e-3 ||l~_N|| FP32, 5e-2 ||l~_N|| tensor cores)."""
+    Lo, so = r["L"], r["s_hat"]
+    row = Lo[:, -1, :]
+    rown = np.linalg.norm(row, axis=1)
+    nrm = np.linalg.norm(Lo, axis=(1, 2))
+    res = {"instances": sample}
+    T_s, D_s, tau_s = (bufs[k][:sample].contiguous() for k in ("T_tilde", "D", "tau"))
+    for p in ("bf16_tc", "fp16_tc", "fp32"):
+        s, L, _ = taser.detect(T_s, D_s, tau_s, T_MAX, p, want_L=True)
+        L = L.cpu().numpy().astype(np.float64)
+        s = s.cpu().numpy()
+        err = np.linalg.norm(L - Lo, axis=(1, 2)) / nrm
+        conf = np.abs(row[:, :-1]) > (1e-3 if p == "fp32" else 5e-2) * rown[:, None]
+        res[p] = {"L_relerr_max": float(err.max()), "L_relerr_mean": float(err.mean()),
+                  "L_relerr_p99": float(np.quantile(err, 0.99)),
+                  "decisions_differ_beyond_margin": int((s != so)[conf].sum()),
+                  "discordant_bits": int((s != so).sum())}
+    return res
 
 
 def run_reference(args):
+    """The FP64 oracle as it stands on every host core: each step is one barrier-synchronised
+    pass of 256 instances of the workload per core (inputs generated before timing)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
-    sample = 512
-    w = make_workload(sample * (args.warmup + args.steps), seed=1)
-    from oracle import taser_oracle as O
-    times = []
-    for i in range(args.warmup + args.steps):
-        sl = slice(i * sample, (i + 1) * sample)
-        t0 = time.perf_counter()
-        O.detect("mimo_qpsk", w["H"][sl], w["y"][sl], ALPHA, T_MAX)
-        if i >= args.warmup:
-            times.append(time.perf_counter() - t0)
+    per_core = 256
+    workers = os.cpu_count() or 1
+    team = OracleTeam(workers, per_core)
+    try:
+        times = []
+        for i in range(args.warmup + args.steps):
+            dt = team.step()
+            if i >= args.warmup:
+                times.append(dt)
+    finally:
+        team.close()
+    sample = per_core * workers
     value = sample * len(times) / sum(times)
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "detections/s", "n_gpus": args.gpus,
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
            "data": "synthetic", "config": {"workload": WORKLOAD, "instances_per_step": sample,
                                            "t_max": T_MAX, "alpha": ALPHA},
-           "cpu_baseline": {"value": value, "unit": "detections/s", "cores": 1, "kind": "oracle",
-                            "sample": "%d instances per step, FP64 numpy oracle, one process" % sample},
+           "cpu_baseline": {"value": value, "unit": "detections/s", "cores": workers, "kind": "oracle",
+                            "sample": "%d instances of the workload per core and step, %d cores (one process "
+                                      "each), FP64 numpy oracle" % (per_core, workers)},
            "e2e": {"value": value, "unit": "detections/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
     return 0
@@ -501,6 +737,8 @@ def main():
         return run_tradeoff(args)
     if args.workload == "unfolded":
         return run_unfolded(args)
+    if args.workload == "ber":
+        return run_ber(args)
 
     import torch
     import torch.distributed as dist
@@ -705,7 +943,9 @@ def main():
         "gpu_launches": 3 * args.steps,
     }
     if world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(w, min(args.cpu_sample, n))
+        sample = min(args.cpu_sample, n)
+        out["cpu_baseline"], r = cpu_baseline(w, sample)
+        out["error_vs_fp64"] = error_vs_fp64(taser, bufs, r, sample)
     print(json.dumps(out))
     if world > 1:
         dist.destroy_process_group()

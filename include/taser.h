@@ -86,6 +86,7 @@ typedef enum {
 
 #define TASER_FLAG_BAD_ITEM    (1u << 4) /* uneven batch: item with N or t_max out of range */
 #define TASER_FLAG_SATURATED   (1u << 5) /* TASER_FIXED14: a value saturated to 14 bits    */
+#define TASER_FLAG_ASCENT      (1u << 6) /* taser_detect_monitored: the objective rose      */
 
 /* Largest N supported by the detection kernels. */
 #define TASER_MAX_N 65
@@ -176,6 +177,39 @@ taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int str
 taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const float* D,
                           const float* tau, int t_max, int precision, int lnn_mode,
                           float* L, int8_t* s_hat, uint32_t* flags, void* stream);
+
+/*
+ * taser_detect_monitored -- taser_detect that also watches the objective the iterations
+ * minimise, f(L~) = Tr(L~ T~ L~^T) (Sec. III-B, Eq. 8 after the preconditioning of
+ * Sec. III-C).  Prop. 1 (Sec. III-E) makes forward-backward splitting a descent method
+ * for a small enough step: with the Lipschitz constant 2||T~||_2 of the gradient
+ * tril(2 L~ T~), that is alpha < 1/2; larger alpha (the paper leaves it open) can make f
+ * rise in some iteration.  This call flags such instances.
+ *
+ * f(L~) is the sum over i >= k of L~_ik (L~ T~)_ik, and the gradient step that starts at
+ * L~(t) forms exactly that lower part of L~ T~.  On the FP32 path f(L~(t)) is read off
+ * the step itself, sum L~_ik (L~_ik - V_ik) / (2 tau) with V = L~ - 2 tau tril(L~ T~).
+ * On the tensor cores a single BF16/FP16 product (operand rounding about 2^-9) is too
+ * coarse for a check, so each step also forms L~ T~ as a BF16 split (hi hi + hi lo +
+ * lo hi, about 2^-16 relative error) into scratch registers; the iteration itself is
+ * unchanged.  The sum of an instance is formed in FP32, the ratio, the comparison and
+ * the trace in FP64.  One extra gradient step after the last iteration gives
+ * f(L~(t_max)).  L~, s_hat and the other flags are those of taser_detect with the same
+ * arguments.
+ *
+ *   ascent_tol  >= 0: TASER_FLAG_ASCENT is OR-ed into flags[b] when, for some t in
+ *               1..t_max, f(L~(t)) > f(L~(t-1)) + ascent_tol |f(L~(t-1))|.  A tolerance of
+ *               about 1e-5 (FP32) or 1e-4 (tensor cores) stays above the rounding of f.
+ *   objective   out, double [batch][t_max + 1] = f(L~(t)) for t = 0..t_max, or NULL.
+ *   other arguments as in taser_detect.  Supported: TASER_FP32 for N in [2, 65];
+ *               TASER_BF16_TC / TASER_FP16_TC for N <= 33 (N < 10 runs FP32, as in
+ *               taser_detect); TASER_ERR_UNSUPPORTED for the tensor-core bucket N > 33
+ *               and for TASER_FIXED14.
+ */
+taser_status taser_detect_monitored(int64_t batch, int N, const float* T_tilde, const float* D,
+                                    const float* tau, int t_max, int precision, int lnn_mode,
+                                    float ascent_tol, double* objective, float* L, int8_t* s_hat,
+                                    uint32_t* flags, void* stream);
 
 /*
  * taser_host_workspace_bytes -- bytes of device workspace taser_run_host needs for
@@ -311,8 +345,10 @@ taser_status taser_detect_uneven(int64_t n_items, const taser_item* items, const
  * last call's contents, and all calls share it: calls whose GPU work overlaps (on
  * different streams, or from several threads) race on it and must be serialised by the
  * caller.  The first call on a device looks up the array's device address for that
- * device (cudaGetSymbolAddress, with that device current); make that first call before
- * any stream capture.  Arguments and outputs are as in taser_run_host.
+ * device (cudaGetSymbolAddress, with that device current) and keeps it for the life of
+ * the process; make that first call before any stream capture.  The kept address does
+ * not survive a cudaDeviceReset (or any other teardown of the device's primary context):
+ * calls after one are not supported.  Arguments and outputs are as in taser_run_host.
  */
 #define TASER_STATIC_SCRATCH_BYTES ((size_t)64 << 20)
 

@@ -15,6 +15,8 @@ SIGNATURES = {
     "taser_build_T": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _vp, _vp, _vp, _vp, _vp, _vp]),
     "taser_step_size": (_c_i32, [_c_i64, _c_i32, _vp, _c_i32, _c_f32, _vp, _vp, _vp]),
     "taser_detect": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _c_i32, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
+    "taser_detect_monitored": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _c_i32, _c_i32, _c_i32, _c_f32, _vp, _vp,
+                                        _vp, _vp, _vp]),
     "taser_host_workspace_bytes": (ctypes.c_size_t, [_c_i32, _c_i64, _c_i32, _c_i32]),
     "taser_run_host": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32, _vp,
                                 ctypes.c_size_t, _vp, _vp, _vp]),

@@ -98,6 +98,30 @@ def detect(T_tilde, D, tau, t_max, precision="fp32", lnn_mode="fixed", want_L=Tr
     return s, L, flags
 
 
+FLAG_ASCENT = 1 << 6
+
+
+def detect_monitored(T_tilde, D, tau, t_max, precision="fp32", ascent_tol=1e-5, lnn_mode="fixed", want_L=True,
+                     want_objective=True, flags=None, stream=None):
+    """detect() that also traces f(L~(t)) = Tr(L~ T~ L~^T), t = 0..t_max, and sets
+    FLAG_ASCENT where it rose by more than ascent_tol |f|.  Returns (s_hat, L or None,
+    flags, objective float64 [n, t_max + 1] or None)."""
+    T = _dev(T_tilde, torch.float32, "T_tilde")
+    n, N, _ = T.shape
+    _dev(D, torch.float32, "D")
+    _dev(tau, torch.float32, "tau")
+    s = torch.empty((n, N - 1), device=T.device, dtype=torch.int8)
+    L = torch.empty((n, N, N), device=T.device, dtype=torch.float32) if want_L else None
+    obj = torch.empty((n, int(t_max) + 1), device=T.device, dtype=torch.float64) if want_objective else None
+    if flags is None:
+        flags = torch.zeros((n,), device=T.device, dtype=torch.int32)
+    st = lib().taser_detect_monitored(n, N, _ptr(T), _ptr(D), _ptr(tau), int(t_max), PRECISIONS[precision],
+                                      LNN_MODES[lnn_mode], float(ascent_tol), _ptr(obj), _ptr(L), _ptr(s),
+                                      _ptr(flags), _stream(stream))
+    check(st, "taser_detect_monitored")
+    return s, L, flags, obj
+
+
 def host_workspace_bytes(kind, batch, B, U_or_K):
     return int(lib().taser_host_workspace_bytes(KINDS[kind], int(batch), int(B), int(U_or_K)))
 

@@ -44,9 +44,15 @@ __device__ __forceinline__ void sync_instance(int bar_id) {
 // t_loop: iterations the warp executes (the largest t_max among its instances).  MIXED:
 // instances sharing the warp may have different t_max, so outputs are emitted inside the
 // loop at each instance's own last iteration; otherwise once after the loop.
-template <int NB, bool MIXED>
+// MON: objective monitoring (taser_detect_monitored).  f(L~) = Tr(L~ T~ L~^T) equals
+// sum_{i >= k} L~_ik (L~ T~)_ik, and the gradient step computes exactly that lower part:
+// V = L~ - 2 tau tril(L~ T~), so f(L~(t)) = sum L~(t)_ik (L~(t)_ik - V(t+1)_ik) / (2 tau),
+// accumulated from the iteration's own FP32 values (no extra product).  One more product
+// after the last iteration gives f(L~(t_max)); its V is discarded.
+template <int NB, bool MIXED, bool MON = false>
 __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop, float* Ls, float* xs, int j,
-                                         int lane, int warp, int bar_id, int literal) {
+                                         int lane, int warp, int bar_id, int literal, double* obj = nullptr,
+                                         float ascent_tol = 0.f) {
   using C = Fp32Cfg<NB>;
   const int colbase = NB > 32 ? (warp % C::WPI) * 32 : 0;  // warp-uniform
   const unsigned gmask = C::G == 32 ? TASER_FULL_MASK : (((1u << C::G) - 1u) << ((lane / C::G) * C::G));
@@ -121,11 +127,14 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
     }
   };
 
-  for (int t = 0; t < t_loop; ++t) {
+  double f_prev = 0.0;
+  for (int t = 0; t < t_loop + (MON ? 1 : 0); ++t) {
+    const bool last_pass = MON && t == t_loop;   // only f(L~(t_max)); L~ stays as it is
     // Partial of V_NN = L~_NN (1 - 2 tau T~_NN) - 2 tau sum_k L~_Nk T~_kN from L~(t-1).
     float part = l[NB] * tNB;
 #pragma unroll
     for (int o = C::G / 2; o > 0; o >>= 1) part += __shfl_xor_sync(TASER_FULL_MASK, part, o);
+    float fterm = 0.f;   // MON: this lane's sum of L~_ij (L~_ij - V_ij)
 
     // V = L~ - tril(2 tau L~ T~): row i needs L~_ik, k <= i only (triangular skip).
 #pragma unroll
@@ -144,7 +153,20 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
       }
       float a0, a1;
       f2unpack(acc2, a0, a1);
-      l[i] = (i >= j) ? a0 + a1 : 0.f;  // l now holds column j of V
+      const float v = (i >= j) ? a0 + a1 : 0.f;
+      if constexpr (MON) {
+        fterm = fmaf(l[i], l[i] - v, fterm);
+        if (!last_pass) l[i] = v;
+      } else {
+        l[i] = v;  // l now holds column j of V
+      }
+    }
+    if constexpr (MON) {
+#pragma unroll
+      for (int o = C::G / 2; o > 0; o >>= 1) fterm += __shfl_xor_sync(TASER_FULL_MASK, fterm, o);
+      if constexpr (NB > 32) {
+        if (lane == 0) xs[2 + warp % C::WPI] = fterm;
+      }
     }
     if constexpr (NB > 32) {
       if (lane == 0) xs[warp % C::WPI] = part;
@@ -152,6 +174,19 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
     sync_instance<NB>(bar_id);  // every lane has finished reading L~(t-1)
     if constexpr (NB > 32) part = xs[0] + xs[1];
     const float vnn = fmaf(LNN, tnNN, LNN) + part;
+    if constexpr (MON) {
+      if constexpr (NB > 32) fterm = xs[2] + xs[3];
+      fterm = fmaf(LNN, LNN - vnn, fterm);
+      // f in FP64 from the FP32 sum; ascent when f(L~(t)) > f(L~(t-1)) + tol |f(L~(t-1))|.
+      const double f = tau > 0.f ? (double)fterm / (2.0 * (double)tau) : 0.0;
+      if (t > 0 && f > f_prev + (double)ascent_tol * fabs(f_prev)) fl |= TASER_FLAG_ASCENT;
+      f_prev = f;
+      if (active && obj != nullptr && j == 0 && colbase == 0) obj[t] = f;
+      if (last_pass) {
+        if constexpr (NB > 32) sync_instance<NB>(bar_id);   // xs is read before it is reused
+        break;
+      }
+    }
     if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
     if (literal) LNN = vnn >= 0.f ? DN : -DN;
 
@@ -198,11 +233,12 @@ __device__ __forceinline__ void fp32_lane_layout(int warp, int lane, int& local_
   }
 }
 
-template <int NB>
+template <int NB, bool MON = false>
 __global__ void __launch_bounds__(128, NB == 32 ? 3 : 1)
 detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const float* __restrict__ Dg,
                    const float* __restrict__ tau_g, int t_max, int literal, float* __restrict__ Lout,
-                   int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags) {
+                   int8_t* __restrict__ s_hat, uint32_t* __restrict__ flags, double* __restrict__ obj,
+                   float ascent_tol) {
   using C = Fp32Cfg<NB>;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -212,7 +248,9 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
   const bool active = inst < batch;
   float* Ls = smem + local_inst * C::INST_FLOATS;
   const Job jb = dense_job(active ? inst : 0, N, t_max, Tt, Dg, tau_g, Lout, s_hat, flags);
-  fp32_run<NB, false>(jb, active, t_max, Ls, Ls + (NB + 1) * C::S, j, lane, warp, 1 + local_inst, literal);
+  double* ob = (MON && obj != nullptr) ? obj + (active ? inst : 0) * (int64_t)(t_max + 1) : nullptr;
+  fp32_run<NB, false, MON>(jb, active, t_max, Ls, Ls + (NB + 1) * C::S, j, lane, warp, 1 + local_inst, literal, ob,
+                           ascent_tol);
 }
 
 // Persistent, queue-fed: each warp (each warp pair for NB = 64) pops the next items of
@@ -262,29 +300,41 @@ detect_fp32_queue_kernel(Queue q, int rounds, const float* __restrict__ T_pool, 
   }
 }
 
-template <int NB>
+template <int NB, bool MON>
 static cudaError_t launch_fp32(int64_t batch, int N, const float* Tt, const float* D, const float* tau,
-                               int t_max, int literal, float* L, int8_t* s, uint32_t* flags,
-                               cudaStream_t st) {
+                               int t_max, int literal, float* L, int8_t* s, uint32_t* flags, double* obj,
+                               float ascent_tol, cudaStream_t st) {
   using C = Fp32Cfg<NB>;
   const int64_t blocks = (batch + C::IPC - 1) / C::IPC;
   if (C::SMEM_BYTES > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(detect_fp32_kernel<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(detect_fp32_kernel<NB, MON>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM_BYTES);
     if (e != cudaSuccess) return e;
   }
-  detect_fp32_kernel<NB><<<(unsigned)blocks, 128, C::SMEM_BYTES, st>>>(batch, N, Tt, D, tau, t_max, literal,
-                                                                      L, s, flags);
+  detect_fp32_kernel<NB, MON><<<(unsigned)blocks, 128, C::SMEM_BYTES, st>>>(batch, N, Tt, D, tau, t_max, literal,
+                                                                           L, s, flags, obj, ascent_tol);
   return cudaGetLastError();
 }
 
 cudaError_t detect_fp32(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                         int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
   switch (bucket_of(N)) {
-    case 8: return launch_fp32<8>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
-    case 16: return launch_fp32<16>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
-    case 32: return launch_fp32<32>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
-    default: return launch_fp32<64>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
+    case 8: return launch_fp32<8, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, nullptr, 0.f, st);
+    case 16: return launch_fp32<16, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, nullptr, 0.f, st);
+    case 32: return launch_fp32<32, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, nullptr, 0.f, st);
+    default: return launch_fp32<64, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, nullptr, 0.f, st);
+  }
+}
+
+// taser_detect_monitored on the FP32 kernel: f(L~(t)) per iteration and the ascent flag.
+cudaError_t detect_fp32_monitored(int64_t batch, int N, const float* Tt, const float* D, const float* tau,
+                                  int t_max, int literal, float ascent_tol, double* obj, float* L, int8_t* s,
+                                  uint32_t* flags, cudaStream_t st) {
+  switch (bucket_of(N)) {
+    case 8: return launch_fp32<8, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, obj, ascent_tol, st);
+    case 16: return launch_fp32<16, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, obj, ascent_tol, st);
+    case 32: return launch_fp32<32, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, obj, ascent_tol, st);
+    default: return launch_fp32<64, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, obj, ascent_tol, st);
   }
 }
 

@@ -76,6 +76,15 @@ __device__ __forceinline__ void mma16816_top(float (&d)[4], const uint32_t (&a)[
   }
 }
 
+// BF16 split x = hi + lo of a float pair (hi = bf16(x), lo = bf16(x - hi)): the products
+// hi hi' + hi lo' + lo hi' carry about 2^-16 relative error, where a single BF16 product
+// carries 2^-8.  Used only by the objective monitor, whatever the path's precision.
+__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
+  hi = pack2<false>(x0, x1);
+  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
+  lo = pack2<false>(x0 - h0, x1 - h1);
+}
+
 // Tile bookkeeping for bucket NB (16 or 32).
 template <int NB>
 struct TcCfg {
@@ -112,10 +121,12 @@ struct DenseSource {
   float* L;
   int8_t* s;
   uint32_t* flags;
-  __device__ __forceinline__ bool get(int64_t k, Job& jb) const {  // k-th instance of this warp
+  double* obj;   // objective trace [batch][t_max + 1] (monitored launches), or nullptr
+  __device__ __forceinline__ bool get(int64_t k, Job& jb, double*& ob) const {  // k-th instance of this warp
     const int64_t inst = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5) + k * stride;
     if (inst >= batch) return false;
     jb = dense_job(inst, N, t_max, Tt, Dg, tau, L, s, flags);
+    ob = obj != nullptr ? obj + inst * (int64_t)(t_max + 1) : nullptr;
     return true;
   }
 };
@@ -136,13 +147,16 @@ struct Cursor;
 template <>
 struct Cursor<DenseSource> {
   int64_t k = 0;
-  __device__ __forceinline__ bool next(const DenseSource& src, Job& jb, int) { return src.get(k++, jb); }
+  __device__ __forceinline__ bool next(const DenseSource& src, Job& jb, double*& ob, int) {
+    return src.get(k++, jb, ob);
+  }
 };
 
 template <>
 struct Cursor<QueueSource> {
   int base = 0, left = 0;
-  __device__ __forceinline__ bool next(const QueueSource& src, Job& jb, int lane) {
+  __device__ __forceinline__ bool next(const QueueSource& src, Job& jb, double*& ob, int lane) {
+    ob = nullptr;
     if (left == 0) {
       int b = 0;
       if (lane == 0) b = src.q.pop(src.pop);
@@ -163,38 +177,52 @@ struct Cursor<QueueSource> {
   }
 };
 
+// Shared-memory floats per warp after its staging slot: two job records (JobOut below).
+constexpr int kTcRecFloats = 24;
+
 // Persistent: each warp takes jobs from its source (a fixed stride, or a bucket queue) and
 // prefetches the next job's inputs with cp.async while it iterates on the current one.
-template <int NB, bool FP16, class Src>
-__global__ void __launch_bounds__(128, 4)
-detect_tc_kernel(Src src, int literal, int slot_floats) {
+// MON: objective monitoring of taser_detect_monitored (dense source only).  f(L~) =
+// Tr(L~ T~ L~^T) is the sum over i >= k of L~_ik (L~ T~)_ik, the lower part of L~ T~ that
+// each gradient step forms.  A single BF16 product is too coarse to see a rise of f of a
+// fraction of a percent, so the monitor forms W = L~ T^ (T^ = -2 tau T~) tile by tile a
+// second time as a BF16 split (3 mma per product, about 2^-16 relative error) into
+// scratch accumulators, before the tile's own mma, and sums L~ o W; f = sum / (-2 tau).
+// The iteration itself is unchanged.  One more step after the outputs are written gives
+// f(L~(t_max)).
+template <int NB, bool FP16, class Src, bool MON = false>
+__global__ void __launch_bounds__(128, MON ? 3 : 4)
+detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
   using C = TcCfg<NB>;
   constexpr int KT = C::KT, NT = C::NT, MT = C::MT;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
-  float* slot = smem + warp * (slot_floats + 16);
+  float* slot = smem + warp * (slot_floats + kTcRecFloats);
   // Output pointers and sizes of the current and the next job live in shared memory
   // (two records per warp), not in registers across the iteration loop.
   struct JobOut {
     float* L;
     int8_t* s;
     uint32_t* flag;
+    double* obj;
     int N, t_max;
   };
-  JobOut* outs = reinterpret_cast<JobOut*>(slot + slot_floats);   // 16 floats = 2 records
-  auto park = [&](const Job& jb, int which) {
-    if (lane == 0) outs[which] = JobOut{jb.L, jb.s, jb.flag, jb.N, jb.t_max};
+  static_assert(2 * sizeof(JobOut) <= kTcRecFloats * sizeof(float), "job records must fit");
+  JobOut* outs = reinterpret_cast<JobOut*>(slot + slot_floats);
+  auto park = [&](const Job& jb, double* ob, int which) {
+    if (lane == 0) outs[which] = JobOut{jb.L, jb.s, jb.flag, ob, jb.N, jb.t_max};
   };
   Cursor<Src> cursor;
   int cur_m = 0;
   bool have;
   {
     Job first;
-    have = cursor.next(src, first, lane);
+    double* ob = nullptr;
+    have = cursor.next(src, first, ob, lane);
     if (have) {
       stage_job(slot, first, lane);
-      park(first, 0);
+      park(first, ob, 0);
     }
   }
 
@@ -218,6 +246,18 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
         bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
         bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
       }
+    // MON: T^ = hi + lo in BF16 (B layout of bf).
+    uint32_t mbh[MON ? KT : 1][NT][2], mbl[MON ? KT : 1][NT][2];
+    if constexpr (MON) {
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
+          split_bf16(tval(k0, n), tval(k0 + 1, n), mbh[kt][nt][0], mbl[kt][nt][0]);
+          split_bf16(tval(k0 + 8, n), tval(k0 + 9, n), mbh[kt][nt][1], mbl[kt][nt][1]);
+        }
+    }
     // Row N of T^ at this lane's accumulator columns c = 8n + 2tq + p (FP32).
     float tN[NT][2];
 #pragma unroll
@@ -230,6 +270,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
     uint64_t tN2[NT];   // packed pairs (zero off the lanes g == 0 that hold row N)
 #pragma unroll
     for (int nt = 0; nt < NT; ++nt) tN2[nt] = f2pack(tN[nt][0], tN[nt][1]);
+    auto tN2f = [&](int n, int p) -> float { return tN[n][p]; };
     const float tnNN = m2tau * T[(N - 1) * N + (N - 1)];
     const float DN = Di[N - 1];
     // After the column-sum reduction this lane owns column cown.
@@ -252,10 +293,11 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
     bool have_next;
     {
       Job nxt;
-      have_next = cursor.next(src, nxt, lane);
+      double* ob = nullptr;
+      have_next = cursor.next(src, nxt, ob, lane);
       if (have_next) {
         stage_job(slot, nxt, lane);
-        park(nxt, cur_m ^ 1);
+        park(nxt, ob, cur_m ^ 1);
       }
     }
     float LNN = DN;
@@ -265,7 +307,9 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
     const bool up0 = 2 * tq > g, up1 = 2 * tq + 1 > g;
     const int src_row0 = 4 * (2 * tq) + (g != 0), src_row1 = 4 * (2 * tq + 1) + (g != 0);
 
-    for (int t = 0; t < t_max; ++t) {
+    // One gradient step: acc <- V = L~ - tril(2 tau L~ T~) (kept lower-triangular);
+    // returns V_NN.  MON: fterm += sum of L~_ik W_ik over this lane's elements, W = L~ T^.
+    auto grad_step = [&](float& fterm) -> float {
       // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
       uint64_t part2 = 0ull;
 #pragma unroll
@@ -292,6 +336,63 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           } else {
             a[kt][1] = 0u;
             a[kt][3] = 0u;
+          }
+        }
+        if constexpr (MON) {
+          // W = L~ T^ of this row block as a BF16 split, dotted with L~ (the old values:
+          // every tile's own mma comes later).  Row N: the transposed product T^ l_N^T, whose
+          // columns are moved into the accumulator layout, plus L~_NN T^_{N,c} in FP32.
+          uint32_t ah[KT][4], al[KT][4];
+#pragma unroll
+          for (int kt = 0; kt <= C::kmax(M); ++kt) {
+            split_bf16(acc[M][2 * kt][0], acc[M][2 * kt][1], ah[kt][0], al[kt][0]);
+            split_bf16(acc[M][2 * kt + 1][0], acc[M][2 * kt + 1][1], ah[kt][2], al[kt][2]);
+            if (M < MT - 1) {
+              split_bf16(acc[M][2 * kt][2], acc[M][2 * kt][3], ah[kt][1], al[kt][1]);
+              split_bf16(acc[M][2 * kt + 1][2], acc[M][2 * kt + 1][3], ah[kt][3], al[kt][3]);
+            } else {
+              ah[kt][1] = ah[kt][3] = al[kt][1] = al[kt][3] = 0u;
+            }
+          }
+          if (M < MT - 1) {
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+              if (!C::has_tile(M, n)) continue;
+              float w4[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+              for (int kt = 0; kt <= C::kmax(M); ++kt) {
+                mma16816<false>(w4, ah[kt], mbh[kt][n]);
+                mma16816<false>(w4, ah[kt], mbl[kt][n]);
+                mma16816<false>(w4, al[kt], mbh[kt][n]);
+              }
+#pragma unroll
+              for (int e = 0; e < 4; ++e) fterm = fmaf(acc[M][n][e], w4[e], fterm);
+            }
+          } else {
+            float d[KT][4];
+#pragma unroll
+            for (int mt = 0; mt < KT; ++mt) {
+#pragma unroll
+              for (int e = 0; e < 4; ++e) d[mt][e] = 0.f;
+#pragma unroll
+              for (int kt = 0; kt < KT; ++kt) {
+                const uint32_t th[4] = {mbh[kt][2 * mt][0], mbh[kt][2 * mt + 1][0], mbh[kt][2 * mt][1],
+                                        mbh[kt][2 * mt + 1][1]};
+                const uint32_t tl[4] = {mbl[kt][2 * mt][0], mbl[kt][2 * mt + 1][0], mbl[kt][2 * mt][1],
+                                        mbl[kt][2 * mt + 1][1]};
+                const uint32_t bh2[2] = {ah[kt][0], ah[kt][2]}, bl2[2] = {al[kt][0], al[kt][2]};
+                mma16816<false>(d[mt], th, bh2);
+                mma16816<false>(d[mt], tl, bh2);
+                mma16816<false>(d[mt], th, bl2);
+              }
+            }
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+              const float v0 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row0);
+              const float v1 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row1);
+              fterm = fmaf(acc[M][n][0], fmaf(LNN, tN2f(n, 0), v0), fterm);
+              fterm = fmaf(acc[M][n][1], fmaf(LNN, tN2f(n, 1), v1), fterm);
+            }
           }
         }
         if (M == MT - 1) {
@@ -353,7 +454,26 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
         if (up1) acc[M][2 * M + 1][3] = 0.f;
       }
 
-      const float vnn = fmaf(LNN, tnNN, LNN) + part;
+      return fmaf(LNN, tnNN, LNN) + part;
+    };
+
+    // MON: f(L~(t)) from the step's terms (FP32 sums, FP64 ratio and comparison).
+    double f_prev = 0.0;
+    double* const obj = MON ? outs[cur_m].obj : nullptr;
+    auto monitor = [&](int t, float fterm, float vnn) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) fterm += __shfl_xor_sync(TASER_FULL_MASK, fterm, o);
+      fterm = fmaf(LNN, vnn - LNN, fterm);   // L~_NN W_NN, W_NN = V_NN - L~_NN (FP32)
+      const double f = m2tau < 0.f ? (double)fterm / (double)m2tau : 0.0;
+      if (t > 0 && f > f_prev + (double)ascent_tol * fabs(f_prev)) fl |= TASER_FLAG_ASCENT;
+      f_prev = f;
+      if (lane == 0 && obj != nullptr) obj[t] = f;
+    };
+
+    for (int t = 0; t < t_max; ++t) {
+      float fterm = 0.f;
+      const float vnn = grad_step(fterm);
+      if constexpr (MON) monitor(t, fterm, vnn);
       if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
       if (literal) LNN = vnn >= 0.f ? DN : -DN;
 
@@ -421,10 +541,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
       }
     }
 
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
     const JobOut o = outs[cur_m];
-    if (lane == 0 && o.flag != nullptr && fl) *o.flag |= fl;
 
     // Decisions from row N (lanes g == 0).
     if (g == 0) {
@@ -456,42 +573,54 @@ detect_tc_kernel(Src src, int literal, int slot_floats) {
           }
       for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
     }
+    if constexpr (MON) {   // f(L~(t_max)): one more gradient step, after the outputs
+      float fterm = 0.f;
+      const float vnn = grad_step(fterm);
+      monitor(t_max, fterm, vnn);
+    }
+#pragma unroll
+    for (int ofs = 16; ofs > 0; ofs >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, ofs);
+    if (lane == 0 && o.flag != nullptr && fl) *o.flag |= fl;
     __syncwarp();  // the record of this job is consumed before it is reused
     cur_m ^= 1;
     have = have_next;
   }
 }
 
-template <int NB, bool FP16, class Src>
+template <int NB, bool FP16, class Src, bool MON = false>
 static cudaError_t launch_tc_src(const Src& src, int64_t jobs, int blocks_per_sm, int literal, int slot_floats,
-                                 cudaStream_t st) {
+                                 float ascent_tol, cudaStream_t st) {
   using C = TcCfg<NB>;
-  const size_t smem = (size_t)C::WARPS * (slot_floats + 16) * sizeof(float);
+  const size_t smem = (size_t)C::WARPS * (slot_floats + kTcRecFloats) * sizeof(float);
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, Src>, 32 * C::WARPS, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, Src, MON>, 32 * C::WARPS,
+                                                      smem);
   if (e != cudaSuccess) return e;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
   const int64_t need = (jobs + C::WARPS - 1) / C::WARPS;
   const int64_t resident = (int64_t)sms * per_sm;
   const int64_t blocks = jobs >= 0 && need < resident ? need : resident;
-  detect_tc_kernel<NB, FP16, Src><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(src, literal, slot_floats);
+  detect_tc_kernel<NB, FP16, Src, MON><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(src, literal, slot_floats,
+                                                                                      ascent_tol);
   return cudaGetLastError();
 }
 
-template <int NB, bool FP16>
+template <int NB, bool FP16, bool MON = false>
 static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
-                             int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
+                             int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st,
+                             double* obj = nullptr, float ascent_tol = 0.f) {
   using C = TcCfg<NB>;
   const int slot_floats = ((N * N + N + 1) + 3) & ~3;
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, DenseSource>, 32 * C::WARPS,
-                                                      (size_t)C::WARPS * (slot_floats + 16) * sizeof(float));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, DenseSource, MON>,
+                                                      32 * C::WARPS,
+                                                      (size_t)C::WARPS * (slot_floats + kTcRecFloats) * sizeof(float));
   if (e != cudaSuccess) return e;
   const int64_t need = (batch + C::WARPS - 1) / C::WARPS;
   const int64_t resident = (int64_t)sms * (fit > 0 ? fit : 1);
@@ -506,7 +635,8 @@ static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float*
   src.L = L;
   src.s = s;
   src.flags = flags;
-  return launch_tc_src<NB, FP16>(src, batch, fit, literal, slot_floats, st);
+  src.obj = obj;
+  return launch_tc_src<NB, FP16, DenseSource, MON>(src, batch, fit, literal, slot_floats, ascent_tol, st);
 }
 
 cudaError_t detect_tc64(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
@@ -532,6 +662,23 @@ cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, con
   }
 }
 
+// taser_detect_monitored on the tensor cores (buckets 16 and 32; cudaErrorNotSupported
+// for the two-warp bucket 64).
+cudaError_t detect_tc_monitored(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                                int literal, bool fp16, float ascent_tol, double* obj, float* L, int8_t* s,
+                                uint32_t* flags, cudaStream_t st) {
+  switch (bucket_of(N)) {
+    case 16:
+      return fp16 ? launch_tc<16, true, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st, obj, ascent_tol)
+                  : launch_tc<16, false, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st, obj, ascent_tol);
+    case 32:
+      return fp16 ? launch_tc<32, true, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st, obj, ascent_tol)
+                  : launch_tc<32, false, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st, obj, ascent_tol);
+    default:
+      return cudaErrorNotSupported;
+  }
+}
+
 // Queue-fed launch for bucket nb (16 or 32) of an uneven batch.
 cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm, int pop, const float* T_pool,
                             const float* D_pool, const float* tau, int literal, float* L_pool, int8_t* s_pool,
@@ -550,11 +697,11 @@ cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm
     case 64:
       return detect_tc64_queue(fp16, q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
     case 16:
-      return fp16 ? launch_tc_src<16, true>(src, -1, blocks_per_sm, literal, slot_floats, st)
-                  : launch_tc_src<16, false>(src, -1, blocks_per_sm, literal, slot_floats, st);
+      return fp16 ? launch_tc_src<16, true>(src, -1, blocks_per_sm, literal, slot_floats, 0.f, st)
+                  : launch_tc_src<16, false>(src, -1, blocks_per_sm, literal, slot_floats, 0.f, st);
     case 32:
-      return fp16 ? launch_tc_src<32, true>(src, -1, blocks_per_sm, literal, slot_floats, st)
-                  : launch_tc_src<32, false>(src, -1, blocks_per_sm, literal, slot_floats, st);
+      return fp16 ? launch_tc_src<32, true>(src, -1, blocks_per_sm, literal, slot_floats, 0.f, st)
+                  : launch_tc_src<32, false>(src, -1, blocks_per_sm, literal, slot_floats, 0.f, st);
     default:
       return cudaErrorNotSupported;
   }

@@ -26,6 +26,12 @@ cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, con
                       int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
 cudaError_t detect_fx14(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max, float* L,
                         int8_t* s, uint32_t* flags, cudaStream_t st);
+cudaError_t detect_fp32_monitored(int64_t batch, int N, const float* Tt, const float* D, const float* tau,
+                                  int t_max, int literal, float ascent_tol, double* obj, float* L, int8_t* s,
+                                  uint32_t* flags, cudaStream_t st);
+cudaError_t detect_tc_monitored(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                                int literal, bool fp16, float ascent_tol, double* obj, float* L, int8_t* s,
+                                uint32_t* flags, cudaStream_t st);
 }  // namespace taser
 
 namespace {
@@ -184,6 +190,43 @@ taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const floa
   }
   return from_cuda(taser::detect_fp32(batch, N, T_tilde, D, tau, t_max, literal, L, s_hat, flags, st),
                    "detect_fp32");
+}
+
+taser_status taser_detect_monitored(int64_t batch, int N, const float* T_tilde, const float* D, const float* tau,
+                                    int t_max, int precision, int lnn_mode, float ascent_tol, double* objective,
+                                    float* L, int8_t* s_hat, uint32_t* flags, void* stream) {
+  TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
+  TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
+  TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC ||
+                    precision == TASER_FIXED14,
+                "unknown precision %d", precision);
+  TASER_REQUIRE(lnn_mode == TASER_LNN_FIXED || lnn_mode == TASER_LNN_LITERAL, "unknown lnn_mode %d", lnn_mode);
+  TASER_REQUIRE(ascent_tol >= 0.f, "ascent_tol must be >= 0 (got %g)", (double)ascent_tol);
+  if (precision == TASER_FIXED14)
+    return fail(TASER_ERR_UNSUPPORTED, "objective monitoring is not available for TASER_FIXED14");
+  const bool tc = precision != TASER_FP32 && taser::bucket_of(N) >= 16;
+  if (tc && taser::bucket_of(N) > 32)
+    return fail(TASER_ERR_UNSUPPORTED, "objective monitoring on the tensor cores needs N <= 33 (got %d)", N);
+  if (batch == 0) return ok();
+  TASER_REQUIRE_PTR(T_tilde, "T_tilde");
+  TASER_REQUIRE_PTR(D, "D");
+  TASER_REQUIRE_PTR(tau, "tau");
+  TASER_REQUIRE_PTR(s_hat, "s_hat");
+  if (L != nullptr) TASER_REQUIRE(aligned16(L), "L must be 16-byte aligned");
+  if (flags != nullptr) TASER_REQUIRE(aligned16(flags), "flags must be 16-byte aligned");
+  if (objective != nullptr) TASER_REQUIRE(aligned16(objective), "objective must be 16-byte aligned");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int literal = lnn_mode == TASER_LNN_LITERAL;
+  if (tc) {
+    return from_cuda(taser::detect_tc_monitored(batch, N, T_tilde, D, tau, t_max, literal,
+                                                precision == TASER_FP16_TC, ascent_tol, objective, L, s_hat, flags,
+                                                st),
+                     "detect_tc_monitored");
+  }
+  return from_cuda(taser::detect_fp32_monitored(batch, N, T_tilde, D, tau, t_max, literal, ascent_tol, objective, L,
+                                                s_hat, flags, st),
+                   "detect_fp32_monitored");
 }
 
 }  // extern "C"

@@ -177,7 +177,11 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
   if (e == cudaSuccess) e = cudaStreamWaitEvent(lanes->lo, lanes->fork, 0);
   if (e != cudaSuccess) return e;
   const int order[4] = {3, 2, 1, 0};        // the heaviest bucket first
-  for (int oi = 0; oi < 4; ++oi) {
+  // A failed bucket launch stops the loop but the side streams are still joined back
+  // into `st` below, so a stream capture in progress stays joined and reports the launch
+  // error instead of an unjoined-capture error.
+  cudaError_t launch_err = cudaSuccess;
+  for (int oi = 0; oi < 4 && launch_err == cudaSuccess; ++oi) {
     const int b = order[oi];
     const cudaStream_t bs = b == 3 ? lanes->hi : lanes->lo;
     const int nb = 8 << b;
@@ -204,13 +208,13 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
       e = detect_fp32_queue(nb, q, bps, (pop + per_load - 1) / per_load, T_pool, D_pool, tau, literal, L_pool,
                             s_pool, flags, bs);
     }
-    if (e != cudaSuccess) return e;
+    launch_err = e;
   }
   e = cudaEventRecord(lanes->join_hi, lanes->hi);
   if (e == cudaSuccess) e = cudaEventRecord(lanes->join_lo, lanes->lo);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, lanes->join_hi, 0);
   if (e == cudaSuccess) e = cudaStreamWaitEvent(st, lanes->join_lo, 0);
-  return e;
+  return launch_err != cudaSuccess ? launch_err : e;
 }
 
 }  // namespace taser

@@ -105,3 +105,27 @@ def test_step_size_rejects_invalid_arguments(lib):
     assert lib.taser_step_size(4, 33, P16, 7, 0.5, P16, None, None) == 1
     assert lib.taser_step_size(4, 32, P16, 1, 0.5, P16, None, None) == 1   # QPSK needs odd N
     assert lib.taser_step_size(0, 33, None, -1, 0.5, None, None, None) == 0
+
+
+def _monitored(lib, **kw):
+    a = dict(batch=8, N=33, T=P16, D=P16, tau=P16, t_max=20, prec=0, mode=0, tol=1e-5, obj=None, L=None, s=P16,
+             flags=None)
+    a.update(kw)
+    return lib.taser_detect_monitored(a["batch"], a["N"], a["T"], a["D"], a["tau"], a["t_max"], a["prec"], a["mode"],
+                                      a["tol"], a["obj"], a["L"], a["s"], a["flags"], None)
+
+
+@pytest.mark.parametrize("kw", [dict(N=1), dict(N=66), dict(t_max=0), dict(batch=-1), dict(prec=4), dict(mode=2),
+                                dict(tol=-1.0), dict(T=None), dict(s=None), dict(obj=P4), dict(L=P4)])
+def test_monitored_rejects_invalid_arguments(lib, kw):
+    assert _monitored(lib, **kw) == 1
+    assert lib.taser_last_error()
+
+
+def test_monitored_unsupported_configurations(lib):
+    # the two-warp tensor-core bucket (N > 33) and the fixed-point datapath, even for an empty batch
+    assert _monitored(lib, prec=1, N=65, batch=0) == 2
+    assert b"N <= 33" in lib.taser_last_error()
+    assert _monitored(lib, prec=3) == 2
+    assert _monitored(lib, batch=0, T=None, D=None, tau=None, s=None) == 0
+    assert _monitored(lib, prec=1, N=9, batch=0) == 0          # N < 10 runs the FP32 kernel

@@ -248,6 +248,19 @@ def test_step_size_scale_and_rank(T, scale):
     np.testing.assert_allclose(nrm.cpu().numpy() / scale, O.spectral_norm(Tt), rtol=1e-5)
 
 
+@pytest.mark.parametrize("B,U", [(4, 9), (6, 12), (8, 16), (15, 16), (16, 16)])
+def test_step_size_nearly_singular_qpsk(T, B, U):
+    """QPSK T~ of rank at most 2B + 1 < N = 2U + 1 (fewer antennas than users; B = U is the
+    borderline square case) through the complex Hermitian form with U + 1 <= 17: the one-sided search
+    relies on T~ being positive semidefinite, which the FP32 reduction only keeps to
+    rounding on such matrices.  Five multisection rounds leave at most 7e-7 relative."""
+    n = 64
+    X, y, _ = problem("mimo_qpsk", n, B, U, 10.0, 400 + B)
+    Tt = O.detect("mimo_qpsk", X, y, ALPHA, 1)["T_tilde"].astype(np.float32)
+    tau, nrm = T.step_size(to_dev(Tt)[0], ALPHA, structure="mimo_qpsk")
+    np.testing.assert_allclose(nrm.cpu().numpy(), O.spectral_norm(Tt.astype(np.float64)), rtol=2e-6)
+
+
 @pytest.mark.parametrize("N", [2, 5, 9, 16, 17, 30, 33, 47, 65])
 def test_step_size_matches_oracle(T, N):
     rng = np.random.default_rng(N)

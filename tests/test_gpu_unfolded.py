@@ -3,9 +3,16 @@ hand-written adjoint against the FP64 oracle (whose adjoint is pinned by finite
 differences and the dot-product test on the CPU).
 
 Tolerances: soft outputs and checkpoints within 1e-5 (FP32 iterations, as for the
-detector); dloss/dtau_t within 2e-3 of the largest entry per instance (the adjoint chains
-t_max FP32 steps of prox Jacobians); dloss/dalpha_t within 1e-5 relative of the FP64 sum
-of the GPU's own per-instance gradients.
+detector); dloss/dalpha_t within 1e-5 relative of the FP64 sum of the GPU's own
+per-instance gradients; dloss/dtau_t within 1e-3 of the largest entry per instance.  The
+adjoint walks t_max steps in reverse, and each step multiplies the adjoint by the prox
+Jacobian, whose column factor D_k / ||V_.k|| reaches about 2 when a column of V has
+shrunk to half of D_k (common on these channels: the smallest ratio per instance has a
+median of 0.5 to 0.7), and by I - 2 tau T~ (norm up to 1 + 2 alpha).  A rounding error of
+2^-24 made at a late step therefore reaches the early tau_t amplified by up to ~2^t, while
+the early entries are not the largest.  Measured against the FP64 reverse mode over 5,632
+instances of these five configurations: median 2e-7 to 6e-6, 99th percentile up to 2.5e-4, max
+7.4e-4 (QPSK 32x4, t_max = 10) of the per-instance largest entry.
 """
 import numpy as np
 import pytest
@@ -77,7 +84,7 @@ def test_unfolded_backward_matches_oracle(T, n, B, U, const, t_max, c):
     g_o = O.unfolded_backward(Tt.astype(np.float64), D.astype(np.float64), tau_t, Ls, g_soft.astype(np.float64))
     g = grad_tau.cpu().numpy().astype(np.float64)
     scale = np.abs(g_o).max(axis=1, keepdims=True) + 1e-30
-    assert (np.abs(g - g_o) / scale).max() <= 2e-3, (np.abs(g - g_o) / scale).max()
+    assert (np.abs(g - g_o) / scale).max() <= 1e-3, (np.abs(g - g_o) / scale).max()
     ga = (g * inv[:, None].astype(np.float64)).sum(axis=0)
     np.testing.assert_allclose(grad_alpha.cpu().numpy(), ga, rtol=1e-5, atol=1e-7 * np.abs(ga).max())
 
@@ -139,3 +146,40 @@ def test_unfolded_training_lowers_the_loss(T):
         losses.append(loss.item())
     assert alpha.grad is not None and torch.isfinite(alpha.grad).all()
     assert np.mean(losses[-3:]) < losses[0]
+
+
+def test_alpha_gradient_matches_gpu_central_differences():
+    """d loss / d alpha_t of the GPU adjoint at N = 9 (QPSK 32x4, FP32 kernels) against
+    central differences of the loss taken in FP64 on the host from two GPU forward calls
+    per t (alpha_t +- h, h = 1e-3 alpha_t).  Averaging over 8,192 instances brings the
+    rounding noise of the FP32 soft outputs in the loss to about 1e-9, so the differences
+    carry about 1e-6 absolute error; the truncation error is O(h^2)."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1609_01797_gb300 as taser
+    n, t_max, c = 8192, 6, 3
+    Tt, D, inv, _, truth = setup(n, 32, 4, "qpsk", t_max, seed=77)
+    alpha = np.array([0.55, 0.35, 0.62, 0.48, 0.41, 0.58], dtype=np.float32)
+    dT, dD, dinv = dev(Tt, D, inv)
+
+    def loss(a):
+        soft, _, _ = taser.unfolded_forward(dT, dD, dinv, dev(a.astype(np.float32))[0], c, want_ckpt=False)
+        x = soft.cpu().numpy().astype(np.float64)
+        return np.mean((x - truth) ** 2), x
+
+    _, x = loss(alpha)
+    g_soft = (2.0 * (x - truth) / x.size).astype(np.float32)
+    soft, _, ckpt = taser.unfolded_forward(dT, dD, dinv, dev(alpha)[0], c)
+    _, g_alpha = taser.unfolded_backward(dT, dD, dinv, dev(alpha)[0], c, ckpt, dev(g_soft)[0])
+    g = g_alpha.cpu().numpy().astype(np.float64)
+    fd = np.zeros(t_max)
+    for t in range(t_max):
+        h = 1e-3 * alpha[t]
+        ap, am = alpha.astype(np.float64).copy(), alpha.astype(np.float64).copy()
+        ap[t] += h
+        am[t] -= h
+        # the steps actually used are the FP32-rounded ones
+        hp = np.float32(ap[t]) - np.float32(alpha[t])
+        hm = np.float32(alpha[t]) - np.float32(am[t])
+        fd[t] = (loss(ap)[0] - loss(am)[0]) / (float(hp) + float(hm))
+    assert np.abs(g - fd).max() <= 2e-3 * np.abs(fd).max() + 1e-7, (g, fd)

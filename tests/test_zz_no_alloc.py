@@ -68,3 +68,36 @@ def test_static_scratch_matches_workspace_entry_point(taser, kind, precision, t_
         assert torch.all(s_static.abs() == 1), call
         np.testing.assert_array_equal(s_static.numpy(), s_ref.numpy())
         np.testing.assert_array_equal(f_static.numpy(), f_ref.numpy())
+
+
+@pytest.mark.gpu
+def test_static_scratch_largest_batch_that_fits(taser):
+    """The largest QPSK 128x16 batch whose scratch fits the static array, so the last
+    chunk's buffers (decisions and flags) end at the array's end: the same decisions and
+    flags as taser_run_host with a caller-allocated workspace of that size."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1609_01797_gb300._native import STATIC_SCRATCH_BYTES
+    lo, hi = 1, 1 << 16
+    while lo < hi:                       # largest n with host_workspace_bytes(n) <= the array
+        mid = (lo + hi + 1) // 2
+        if taser.host_workspace_bytes("mimo_qpsk", mid, 128, 16) <= STATIC_SCRATCH_BYTES:
+            lo = mid
+        else:
+            hi = mid - 1
+    n = lo
+    assert taser.host_workspace_bytes("mimo_qpsk", n + 1, 128, 16) > STATIC_SCRATCH_BYTES
+    X, y, M = _inputs("mimo_qpsk", n, 33)
+    Xh, yh = torch.from_numpy(X).pin_memory(), torch.from_numpy(y).pin_memory()
+    s_static = torch.full((n, 32), 7, dtype=torch.int8).pin_memory()
+    f_static = torch.full((n,), -1, dtype=torch.int32).pin_memory()
+    taser.run_host_static("mimo_qpsk", Xh, yh, 0.5, 20, "bf16_tc", s_static, flags=f_static)
+    torch.cuda.synchronize()
+    ws = torch.empty(taser.host_workspace_bytes("mimo_qpsk", n, 128, 16), device="cuda", dtype=torch.uint8)
+    s_ref = torch.empty((n, 32), dtype=torch.int8).pin_memory()
+    f_ref = torch.empty((n,), dtype=torch.int32).pin_memory()
+    taser.run_host("mimo_qpsk", Xh, yh, 0.5, 20, "bf16_tc", ws, s_ref, flags=f_ref)
+    torch.cuda.synchronize()
+    assert torch.all(s_static.abs() == 1)
+    np.testing.assert_array_equal(s_static.numpy(), s_ref.numpy())
+    np.testing.assert_array_equal(f_static.numpy(), f_ref.numpy())
