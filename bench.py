@@ -43,6 +43,10 @@ def parse_args():
                     help="instances of the workload run through the oracle in one process (1-core rate and the "
                          "GPU paths' error against FP64)")
     ap.add_argument("--jed-instances", type=int, default=131072, help="JED instances per SNR point (--workload ber)")
+    ap.add_argument("--train-steps", type=int, default=400, help="training steps before the held-out BER "
+                                                                 "(--workload unfolded)")
+    ap.add_argument("--unfolded-precision", choices=["fp32", "bf16_tc", "fp16_tc"], default="fp32",
+                    help="arithmetic of the unfolded forward and adjoint products (--workload unfolded)")
     ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff", "unfolded", "ber"],
                     default="qpsk128x16",
                     help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20}; tradeoff: SNR "
@@ -540,30 +544,6 @@ def run_uneven(args):
     return 0
 
 
-def _device_mimo(n, b, u, snr_db, constellation, gen, dev):
-    """Seeded MU-MIMO instances drawn on the GPU with the recipe of synth.make_mimo:
-    H i.i.d. CN(0, 1), unit-energy BPSK / QPSK symbols, noise CN(0, N0), N0 = U / SNR."""
-    import torch
-    half = 0.5 ** 0.5
-
-    def cn(shape):
-        return torch.complex(torch.randn(shape, generator=gen, device=dev),
-                             torch.randn(shape, generator=gen, device=dev)) * half
-
-    H = cn((n, b, u))
-    bre = torch.randint(0, 2, (n, u), generator=gen, device=dev, dtype=torch.int8) * 2 - 1
-    if constellation == "qpsk":
-        bim = torch.randint(0, 2, (n, u), generator=gen, device=dev, dtype=torch.int8) * 2 - 1
-        s = torch.complex(bre.float(), bim.float()) * half
-        truth = torch.cat([bre, bim], dim=1)
-    else:
-        s = torch.complex(bre.float(), torch.zeros_like(bre, dtype=torch.float32))
-        truth = bre
-    n0 = u / 10.0 ** (snr_db / 10.0)
-    y = torch.einsum("nbu,nu->nb", H, s) + cn((n, b)) * n0 ** 0.5
-    return H.contiguous(), y.contiguous(), truth
-
-
 def run_tradeoff(args):
     """Throughput vs the SNR needed for 1% VER as t_max goes from 1 to 20, for 32-user
     systems (B = 32, U = 32, BPSK N = 33 and QPSK N = 65): the GPU counterpart of the
@@ -574,6 +554,7 @@ def run_tradeoff(args):
     figures, which exclude the preprocessing) at each t_max."""
     import torch
     import paper_1609_01797_gb300 as taser
+    from synth import make_mimo_device
     dev = torch.device("cuda", 0)
     n = args.instances
     t_list = list(range(1, 21))
@@ -596,14 +577,13 @@ def run_tradeoff(args):
         kind = "mimo_" + const
         nn = 2 * u + 1 if const == "qpsk" else u + 1
         bits = u * (2 if const == "qpsk" else 1)
-        gen = torch.Generator(device=dev)
-        gen.manual_seed(17 if const == "bpsk" else 18)
         keys = [(p, a) for p in precisions for a in alphas]
         ver = {(p, a, t): [] for p, a in keys for t in t_list}
         done = {k: False for k in keys}
         tau = torch.empty(n, device=dev)
-        for snr in snrs:
-            H, y, truth = _device_mimo(n, b, u, float(snr), const, gen, dev)
+        for si, snr in enumerate(snrs):
+            H, y, truth = make_mimo_device(n, b, u, float(snr), const, seed=(17 if const == "bpsk" else 18) * 1000 + si,
+                                           device=dev)
             out = taser.build_T(kind, H, y, 0.5, with_tau=False)
             for a in alphas:
                 taser.step_size(out["T_tilde"], a, structure=kind, tau=tau)
@@ -650,60 +630,96 @@ def run_tradeoff(args):
 
 
 def run_unfolded(args):
-    """Unfolded TASER training (learnable per-iteration steps, hand-written adjoint): one
-    step = taser_build_T on a fresh batch of 8,192 QPSK 128x16 instances (SNR uniform in
-    [4, 14] dB; eight pre-generated batches resident in HBM, cycled) + the forward with
-    checkpoints every 4 iterations (t_max = 10) + the MSE loss gradient + the adjoint +
-    one Adam update of alpha_t.  Reports training instances/s and the forward and adjoint
-    kernels against the FP32 pipe."""
+    """Unfolded TASER training (learnable per-iteration steps, hand-written adjoint).  One
+    step = a fresh seeded batch of 8,192 QPSK 128x16 instances drawn on the GPU (SNR uniform
+    in [4, 14] dB, a new seed every step) + taser_build_T + the forward with checkpoints
+    every 4 iterations (t_max = 10) + the MSE loss gradient + the adjoint + one Adam update
+    of alpha_t.  Reports training instances/s and the forward and adjoint kernels against
+    the FP32 pipe, then trains on to --train-steps and judges the trained alpha_t by BER
+    against fixed-tau TASER (alpha = 0.5, the same t_max) on 65,536 held-out instances."""
     import torch
     import paper_1609_01797_gb300 as taser
-    from synth import make_mimo
+    from synth import make_mimo_device
     dev = torch.device("cuda", 0)
     n, t_max, c = 8192, 10, 4
-    batches = []
-    for k in range(8):
-        w = make_mimo(n, B, U, np.random.default_rng(100 + k).uniform(4, 14, n), "qpsk", seed=4000 + k)
-        truth = torch.from_numpy(truth_bits(w).astype(np.float32)).to(dev)
-        batches.append((torch.from_numpy(w["H"]).to(dev), torch.from_numpy(w["y"]).to(dev), truth))
     alpha = torch.full((t_max,), ALPHA, device=dev, requires_grad=True)
     opt = torch.optim.Adam([alpha], lr=0.02)
     stream = torch.cuda.current_stream(dev)
+    precision = args.unfolded_precision
 
     def step(i, ev=None):
-        H, y, truth = batches[i % len(batches)]
+        if ev is not None:
+            ev[0].record(stream)
+        H, y, truth = make_mimo_device(n, B, U, (4.0, 14.0), "qpsk", seed=40_000 + i, device=dev)
+        truth = truth.float()
+        if ev is not None:
+            ev[1].record(stream)
         out = taser.build_T("mimo_qpsk", H, y, ALPHA)
         inv = 1.0 / out["spec_norm"]
         if ev is not None:
-            ev[0].record(stream)
-        soft, _, ckpt = taser.unfolded_forward(out["T_tilde"], out["D"], inv, alpha.detach(), c)
-        if ev is not None:
-            ev[1].record(stream)
-        g_soft = 2.0 * (soft - truth) / soft.numel()
-        if ev is not None:
             ev[2].record(stream)
-        _, g_alpha = taser.unfolded_backward(out["T_tilde"], out["D"], inv, alpha.detach(), c, ckpt, g_soft)
+        soft, _, ckpt = taser.unfolded_forward(out["T_tilde"], out["D"], inv, alpha.detach(), c,
+                                               precision=precision)
         if ev is not None:
             ev[3].record(stream)
+        g_soft = 2.0 * (soft - truth) / soft.numel()
+        if ev is not None:
+            ev[4].record(stream)
+        _, g_alpha = taser.unfolded_backward(out["T_tilde"], out["D"], inv, alpha.detach(), c, ckpt, g_soft,
+                                             precision=precision)
+        if ev is not None:
+            ev[5].record(stream)
         alpha.grad = g_alpha
         opt.step()
         return soft, truth
 
     for i in range(args.warmup):
         step(i)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(6)] for _ in range(args.steps)]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize(dev)
     e0.record(stream)
     for i in range(args.steps):
-        step(i, ev[i])
+        step(args.warmup + i, ev[i])
     e1.record(stream)
     torch.cuda.synchronize(dev)
     ms = e0.elapsed_time(e1) / args.steps
-    fwd_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
-    bwd_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
-    soft, truth = step(args.steps)
-    loss = float(torch.mean((soft - truth) ** 2))
+    gen_ms = sum(e[0].elapsed_time(e[1]) for e in ev) / args.steps
+    fwd_ms = sum(e[2].elapsed_time(e[3]) for e in ev) / args.steps
+    bwd_ms = sum(e[4].elapsed_time(e[5]) for e in ev) / args.steps
+    losses = []
+    for i in range(args.warmup + args.steps, args.train_steps):
+        soft, truth = step(i)
+        if i % 50 == 0 or i == args.train_steps - 1:
+            losses.append((i, float(torch.mean((soft - truth) ** 2))))
+    trained = alpha.detach().clone()
+
+    # BER of the trained steps against fixed-tau TASER on held-out instances: the training
+    # distribution (SNR uniform in [4, 14] dB), and fixed low SNRs where errors are frequent
+    # enough to separate the two.
+    n_eval, chunk = 65536, 8192
+
+    def heldout(snr, seed0):
+        err = {"trained": 0, "fixed": 0, "discordant": 0}
+        for k in range(n_eval // chunk):
+            H, y, truth = make_mimo_device(chunk, B, U, snr, "qpsk", seed=seed0 + k, device=dev)
+            out = taser.build_T("mimo_qpsk", H, y, ALPHA)
+            _, s_tr, _ = taser.unfolded_forward(out["T_tilde"], out["D"], 1.0 / out["spec_norm"], trained, c,
+                                                want_ckpt=False, precision=precision)
+            s_fx, _, _ = taser.detect(out["T_tilde"], out["D"], out["tau"], t_max, precision, want_L=False)
+            err["trained"] += int((s_tr != truth).sum())
+            err["fixed"] += int((s_fx != truth).sum())
+            err["discordant"] += int((s_tr != s_fx).sum())
+        nbits = n_eval * (N - 1)
+        r = {k: {"bit_errors": err[k], "ber": err[k] / nbits, "ber_ci95": list(clopper_pearson(err[k], nbits))}
+             for k in ("trained", "fixed")}
+        return {"instances": n_eval, "snr_db": snr if isinstance(snr, float) else "uniform %g..%g" % tuple(snr),
+                "trained_alpha_t": r["trained"], "fixed_alpha_0.5": r["fixed"], "discordant_bits": err["discordant"],
+                "trained_better": r["trained"]["ber_ci95"][1] < r["fixed"]["ber_ci95"][0],
+                "fixed_better": r["fixed"]["ber_ci95"][1] < r["trained"]["ber_ci95"][0]}
+
+    held = [heldout((4.0, 14.0), 90_000)] + [heldout(float(snr), 91_000 + 100 * i)
+                                             for i, snr in enumerate((0.0, 2.0, 4.0))]
     props = torch.cuda.get_device_properties(dev)
     fp32_peak = props.multi_processor_count * 128 * 2 * 2070.0e6 / 1e12
     P = N * (N + 1) * (2 * N + 1) // 6
@@ -715,11 +731,14 @@ def run_unfolded(args):
     print(json.dumps({
         "metric": "unfolded TASER training instances/s, QPSK 128x16 (N = 33), t_max = 10, batch 8,192",
         "value": n / (ms * 1e-3), "unit": "instances/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": ms, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+        "ms_per_step": ms, "higher_is_better": True, "dtype": "f32" if precision == "fp32" else "bf16",
+        "data": "synthetic, a fresh seeded batch drawn on the GPU every step",
         "config": {"workload": "unfolded_qpsk128x16_tmax10_c4_batch8192", "instances_per_step": n, "t_max": t_max,
-                   "checkpoint_every": c, "step": "build_T + forward + loss gradient + adjoint + Adam"},
-        "forward_ms": fwd_ms, "backward_ms": bwd_ms, "loss_after": loss,
-        "alpha_t": [round(float(a), 4) for a in alpha.detach().cpu()],
+                   "checkpoint_every": c, "precision": precision,
+                   "step": "draw batch + build_T + forward + loss gradient + adjoint + Adam"},
+        "draw_ms": gen_ms, "forward_ms": fwd_ms, "backward_ms": bwd_ms, "train_steps": args.train_steps,
+        "loss_trace": losses, "alpha_t": [round(float(a), 4) for a in trained.cpu()],
+        "heldout_ber": held,
         "roofline_forward": {"bound": "alu", "achieved": fwd_tf, "peak": fp32_peak, "unit": "TFLOP/s",
                              "frac": fwd_tf / fp32_peak, "algorithmic_flops_per_instance": fwd_fl},
         "roofline_backward": {"bound": "alu", "achieved": bwd_tf, "peak": fp32_peak, "unit": "TFLOP/s",

@@ -242,12 +242,17 @@ taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const vo
 /*
  * taser_unfolded_forward -- unfolded TASER: Algorithm 1 with one step size per
  * iteration, tau_t = alpha_t / ||T~||_2, learnable alpha_t shared by all instances
- * (mode TASER_LNN_FIXED, FP32).  Forward pass of the training path.
+ * (mode TASER_LNN_FIXED).  Forward pass of the training path.
  *   T_tilde, D  as in taser_detect; N in [2, 33].
  *   inv_norm    float [batch] = 1 / ||T~||_2 (from spec_norm of taser_build_T).
  *   alpha_t     float [t_max].
  *   c           checkpoint spacing, 1 <= c <= t_max (ceil(sqrt(t_max)) balances memory
  *               and recomputation).
+ *   precision   TASER_FP32, or TASER_BF16_TC / TASER_FP16_TC: the triangular products on
+ *               the tensor cores (operands of -2 tau_t L~ and T~ in BF16/FP16, FP32
+ *               accumulation) with the master iterates and the prox in FP32, for
+ *               18 <= N <= 33; smaller N runs FP32.  TASER_FIXED14 returns
+ *               TASER_ERR_UNSUPPORTED.  Pass the same precision to the backward call.
  *   ckpt        out float [batch][ceil(t_max / c)][N][N]: L~(k c) for k = 0, 1, ..., or
  *               NULL when no backward pass follows.
  *   soft        out float [batch][N-1]: x_k = L~(t_max)_{N,k} / D_k, the last row of the
@@ -256,7 +261,8 @@ taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const vo
  */
 taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, const float* D,
                                     const float* inv_norm, const float* alpha_t, int t_max, int c,
-                                    float* ckpt, float* soft, int8_t* s_hat, void* stream);
+                                    int precision, float* ckpt, float* soft, int8_t* s_hat,
+                                    void* stream);
 
 /*
  * taser_unfolded_backward -- adjoint of taser_unfolded_forward.  Given grad_soft =
@@ -265,15 +271,17 @@ taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, 
  * sum_n grad_tau[n][t] inv_norm[n] in a fixed reduction order.  Each segment of c
  * iterations is recomputed from ckpt (same arguments as the forward call) and
  * differentiated in reverse; the gradient flows through the soft last row only.
- * Needs (c + 2) M(NB) floats of shared memory per block (one warp, one instance), NB the
- * bucket of N and M(NB) the packed lower triangle of an (NB + 1)-row matrix whose rows are
- * padded to 4 floats (60 / 180 / 612 at NB = 8 / 16 / 32; c <= 92 at N = 33); larger c is
- * rejected.
+ * The tensor-core precisions differentiate the tensor-core forward (the products of the
+ * recomputed steps and Vbar (2 T~) on the tensor cores, the prox Jacobian in FP32).
+ * Shared memory per block (one warp, one instance): FP32, (c + 2) M(NB) floats, NB the
+ * bucket of N and M(NB) the packed lower triangle of an (NB + 1)-row matrix whose rows
+ * are padded to 4 floats (60 / 180 / 612 at NB = 8 / 16 / 32; c <= 92 at N = 33); tensor
+ * cores, 1,280 c + 1,248 floats (c <= 44).  Larger c is rejected.
  */
 taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde, const float* D,
                                      const float* inv_norm, const float* alpha_t, int t_max, int c,
-                                     const float* ckpt, const float* grad_soft, float* grad_tau,
-                                     float* grad_alpha, void* stream);
+                                     int precision, const float* ckpt, const float* grad_soft,
+                                     float* grad_tau, float* grad_alpha, void* stream);
 
 /*
  * Uneven batches.  One item per detection problem; the items share pooled buffers.

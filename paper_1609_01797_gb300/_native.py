@@ -22,9 +22,10 @@ SIGNATURES = {
                                 ctypes.c_size_t, _vp, _vp, _vp]),
     "taser_run_host_static": (_c_i32, [_c_i32, _c_i64, _c_i32, _c_i32, _vp, _vp, _c_f32, _c_i32, _c_i32, _c_i32,
                                        _vp, _vp, _vp]),
-    "taser_unfolded_forward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp]),
-    "taser_unfolded_backward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp,
-                                         _vp]),
+    "taser_unfolded_forward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _c_i32, _vp, _vp, _vp,
+                                        _vp]),
+    "taser_unfolded_backward": (_c_i32, [_c_i64, _c_i32, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _c_i32, _vp, _vp, _vp,
+                                         _vp, _vp]),
     "taser_uneven_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
     "taser_detect_uneven": (_c_i32, [_c_i64, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                      _vp, _vp]),

@@ -156,7 +156,7 @@ def run_host_static(kind, H_or_Y, y, alpha, t_max, precision, s_hat, flags=None,
     check(st, "taser_run_host_static")
 
 
-def unfolded_forward(T_tilde, D, inv_norm, alpha_t, c, want_ckpt=True, stream=None):
+def unfolded_forward(T_tilde, D, inv_norm, alpha_t, c, want_ckpt=True, precision="fp32", stream=None):
     """Unfolded TASER forward (tau_t = alpha_t * inv_norm).  Returns (soft, s_hat, ckpt)."""
     T = _dev(T_tilde, torch.float32, "T_tilde")
     n, N, _ = T.shape
@@ -168,11 +168,12 @@ def unfolded_forward(T_tilde, D, inv_norm, alpha_t, c, want_ckpt=True, stream=No
     soft = torch.empty((n, N - 1), device=T.device, dtype=torch.float32)
     s_hat = torch.empty((n, N - 1), device=T.device, dtype=torch.int8)
     check(lib().taser_unfolded_forward(n, N, _ptr(T), _ptr(D), _ptr(inv_norm), _ptr(alpha_t), t_max, int(c),
-                                       _ptr(ckpt), _ptr(soft), _ptr(s_hat), _stream(stream)), "taser_unfolded_forward")
+                                       PRECISIONS[precision], _ptr(ckpt), _ptr(soft), _ptr(s_hat), _stream(stream)),
+          "taser_unfolded_forward")
     return soft, s_hat, ckpt
 
 
-def unfolded_backward(T_tilde, D, inv_norm, alpha_t, c, ckpt, grad_soft, stream=None):
+def unfolded_backward(T_tilde, D, inv_norm, alpha_t, c, ckpt, grad_soft, precision="fp32", stream=None):
     """Adjoint of unfolded_forward.  Returns (grad_tau [n, t_max], grad_alpha [t_max])."""
     T = _dev(T_tilde, torch.float32, "T_tilde")
     n, N, _ = T.shape
@@ -181,29 +182,30 @@ def unfolded_backward(T_tilde, D, inv_norm, alpha_t, c, ckpt, grad_soft, stream=
     grad_tau = torch.empty((n, t_max), device=T.device, dtype=torch.float32)
     grad_alpha = torch.empty((t_max,), device=T.device, dtype=torch.float32)
     check(lib().taser_unfolded_backward(n, N, _ptr(T), _ptr(D), _ptr(inv_norm), _ptr(alpha_t), t_max, int(c),
-                                        _ptr(ckpt), _ptr(grad_soft), _ptr(grad_tau), _ptr(grad_alpha),
-                                        _stream(stream)), "taser_unfolded_backward")
+                                        PRECISIONS[precision], _ptr(ckpt), _ptr(grad_soft), _ptr(grad_tau),
+                                        _ptr(grad_alpha), _stream(stream)), "taser_unfolded_backward")
     return grad_tau, grad_alpha
 
 
 class UnfoldedTASER(torch.autograd.Function):
-    """soft = UnfoldedTASER.apply(alpha_t, T_tilde, D, inv_norm, c): the soft last row of
-    unfolded TASER with learnable per-iteration steps alpha_t (gradient to alpha_t only;
-    the decisions sign(soft) stay hard).  Checkpoints every c iterations."""
+    """soft = UnfoldedTASER.apply(alpha_t, T_tilde, D, inv_norm, c[, precision]): the soft
+    last row of unfolded TASER with learnable per-iteration steps alpha_t (gradient to
+    alpha_t only; the decisions sign(soft) stay hard).  Checkpoints every c iterations."""
 
     @staticmethod
-    def forward(ctx, alpha_t, T_tilde, D, inv_norm, c):
+    def forward(ctx, alpha_t, T_tilde, D, inv_norm, c, precision="fp32"):
         a = alpha_t.detach().contiguous()
-        soft, _, ckpt = unfolded_forward(T_tilde, D, inv_norm, a, c, want_ckpt=True)
+        soft, _, ckpt = unfolded_forward(T_tilde, D, inv_norm, a, c, want_ckpt=True, precision=precision)
         ctx.save_for_backward(a, T_tilde, D, inv_norm, ckpt)
         ctx.c = c
+        ctx.precision = precision
         return soft
 
     @staticmethod
     def backward(ctx, grad_soft):
         a, T_tilde, D, inv_norm, ckpt = ctx.saved_tensors
-        _, grad_alpha = unfolded_backward(T_tilde, D, inv_norm, a, ctx.c, ckpt, grad_soft)
-        return grad_alpha, None, None, None, None
+        _, grad_alpha = unfolded_backward(T_tilde, D, inv_norm, a, ctx.c, ckpt, grad_soft, precision=ctx.precision)
+        return grad_alpha, None, None, None, None, None
 
 
 # taser_item of include/taser.h (40 bytes, naturally aligned).

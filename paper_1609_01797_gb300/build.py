@@ -14,7 +14,7 @@ INCLUDE = os.path.join(ROOT, "include")
 LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libtaser.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["taser_api.cu", "build_T.cu", "spectral.cu", "detect_fp32.cu", "detect_tc.cu", "detect_tc64.cu", "detect_fx14.cu", "static_scratch.cu", "unfolded.cu", "uneven.cu"]
+SOURCES = ["taser_api.cu", "build_T.cu", "spectral.cu", "detect_fp32.cu", "detect_tc.cu", "detect_tc64.cu", "detect_fx14.cu", "static_scratch.cu", "unfolded.cu", "unfolded_tc.cu", "uneven.cu"]
 
 
 def _nvcc():
@@ -34,7 +34,8 @@ def _flags(verbose_ptxas=False):
 def _stale(obj, src):
     if not os.path.exists(obj):
         return True
-    deps = [src, os.path.join(CSRC, "common.cuh"), os.path.join(INCLUDE, "taser.h"), __file__]
+    deps = [src, os.path.join(INCLUDE, "taser.h"), __file__] + [
+        os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")]
     return any(os.path.getmtime(d) > os.path.getmtime(obj) for d in deps)
 
 

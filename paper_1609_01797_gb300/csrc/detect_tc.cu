@@ -15,96 +15,19 @@
 // m-tile whose only live row is row NB; its L~_NN T^_{N,c} term is added in FP32.
 // The tensor-core instruction is the warp-level mma.sync: the per-instance operand B
 // changes with every instance and M is 33 rows, below the 64/128-row tiles of tcgen05.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-
-#include "common.cuh"
+#include "mma_tc.cuh"
 
 namespace taser {
-
-template <bool FP16>
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
-  if constexpr (FP16) {
-    __half2 h = __floats2half2_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&h);
-  } else {
-    __nv_bfloat162 b = __floats2bfloat162_rn(lo, hi);
-    return *reinterpret_cast<uint32_t*>(&b);
-  }
-}
-
-template <bool FP16>
-__device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  if constexpr (FP16) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  } else {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  }
-}
-
-// The packed f32x2 operations (common.cuh) handle the two columns (2tq, 2tq + 1) an
-// accumulator register pair holds with one instruction.
-// acc[e], acc[e + 1] = f(acc[e], acc[e + 1]) for a packed operation f.
-#define TASER_PAIR_APPLY(arr, e, expr)          \
-  do {                                          \
-    const uint64_t _x = f2pack(arr[e], arr[e + 1]); \
-    const uint64_t _y = (expr);                 \
-    f2unpack(_y, arr[e], arr[e + 1]);           \
-  } while (0)
-
-// The same mma for the m-tile of row N, whose rows g + 8 are identically zero: their
-// accumulators are fed zeros and discarded, so they occupy no registers across iterations.
-template <bool FP16>
-__device__ __forceinline__ void mma16816_top(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  float z2 = 0.f, z3 = 0.f;
-  if constexpr (FP16) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(z2), "+f"(z3)
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  } else {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(z2), "+f"(z3)
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  }
-}
-
-// BF16 split x = hi + lo of a float pair (hi = bf16(x), lo = bf16(x - hi)): the products
-// hi hi' + hi lo' + lo hi' carry about 2^-16 relative error, where a single BF16 product
-// carries 2^-8.  Used only by the objective monitor, whatever the path's precision.
-__device__ __forceinline__ void split_bf16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  hi = pack2<false>(x0, x1);
-  const float h0 = __uint_as_float(hi << 16), h1 = __uint_as_float(hi & 0xffff0000u);
-  lo = pack2<false>(x0 - h0, x1 - h1);
-}
-
-// Tile bookkeeping for bucket NB (16 or 32).
-template <int NB>
-struct TcCfg {
-  static constexpr int KT = NB / 16;     // k-tiles over the variable columns
-  static constexpr int NT = NB / 8;      // n-tiles over the variable columns
-  static constexpr int MT = KT + 1;      // m-tiles; the last holds row NB only
-  static constexpr int NV = 2 * NT;      // column-sum values per lane before reduction
-  static constexpr int WARPS = 4;
-  __host__ __device__ static constexpr bool has_tile(int M, int n) {
-    return M == MT - 1 ? true : n <= 2 * M + 1;
-  }
-  __host__ __device__ static constexpr int kmax(int M) { return M == MT - 1 ? KT - 1 : M; }
-};
 
 __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
-// Stage T~ (N x N), D (N) and tau of one job into the warp's shared slot.
+// Stage T~ (N x N), D (N) and tau of one job into the warp's shared slot.  (Staging only
+// the lower triangle was measured: the DRAM bytes stayed at 4,490 per instance, because
+// rows of N = 33 floats are not aligned to the 128-byte lines, so nearly every line still
+// holds a part of the triangle; the triangle walk only added instructions.)
 __device__ __forceinline__ void stage_job(float* slot, const Job& jb, int lane) {
   const int N = jb.N, nn = N * N;
   for (int i = lane; i < nn; i += 32) cp_async4(slot + i, jb.T + i);
@@ -496,7 +419,12 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
         }
         f2unpack(v2, s[2 * n], s[2 * n + 1]);
       }
-      // Transpose-reduce over lane bits 4, 3, 2: each step halves the values a lane keeps.
+      // Transpose-reduce over lane bits 4, 3, 2 (each step halves the values a lane keeps),
+      // then a shuffle broadcast of the scales.  (An exchange of the partials and scales
+      // through shared memory was measured at bucket 32, together with the triangle
+      // staging above: 4,890 instead of 4,182 warp instructions per instance, 0.440 instead
+      // of 0.391 ms per 65,536; the FMA-pipe count rose by 18 per iteration, the register
+      // moves that assemble the 16-byte stores and the addressing.)
       {
         int len = C::NV;
 #pragma unroll

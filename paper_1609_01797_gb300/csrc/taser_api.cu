@@ -12,10 +12,11 @@ cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, int hin
                      cudaStream_t st);
 cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, int sign, float alpha, float* tau, float* nrm,
                           cudaStream_t st);
-cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,
-                     const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
-                     const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st);
+cudaError_t unfolded(bool backward, int precision, int64_t batch, int N, const float* Tt, const float* D,
+                     const float* inv_norm, const float* alpha_t, int t_max, int c, float* ckpt, float* soft,
+                     int8_t* s_hat, const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st);
 size_t unfolded_backward_smem(int N, int c);
+size_t unfolded_tc_backward_smem(int c);
 size_t uneven_workspace_bytes(int64_t n_items);
 cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float* T_pool, const float* D_pool,
                           const float* tau, int precision, int literal, float* L_pool, int8_t* s_pool,
@@ -370,13 +371,23 @@ taser_status report(taser_status st, const char* msg) { return fail(st, "%s", ms
 
 extern "C" {
 
+namespace {
+bool unfolded_tc_path(int precision, int N) {
+  return (precision == TASER_BF16_TC || precision == TASER_FP16_TC) && taser::bucket_of(N) == 32;
+}
+}  // namespace
+
 taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, const float* D, const float* inv_norm,
-                                    const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
-                                    void* stream) {
+                                    const float* alpha_t, int t_max, int c, int precision, float* ckpt, float* soft,
+                                    int8_t* s_hat, void* stream) {
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= 33, "unfolded TASER supports 2 <= N <= 33 (got %d)", N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
   TASER_REQUIRE(c >= 1 && c <= t_max, "checkpoint spacing c must lie in [1, t_max] (got %d)", c);
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC ||
+                    precision == TASER_FIXED14,
+                "unknown precision %d", precision);
+  if (precision == TASER_FIXED14) return fail(TASER_ERR_UNSUPPORTED, "unfolded TASER has no fixed-point datapath");
   if (batch == 0) return ok();
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(D, "D");
@@ -385,22 +396,29 @@ taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, 
   TASER_REQUIRE_PTR(soft, "soft");
   if (ckpt != nullptr) TASER_REQUIRE(aligned16(ckpt), "ckpt must be 16-byte aligned");
   if (s_hat != nullptr) TASER_REQUIRE(aligned16(s_hat), "s_hat must be 16-byte aligned");
-  return from_cuda(taser::unfolded(false, batch, N, T_tilde, D, inv_norm, alpha_t, t_max, c, ckpt, soft, s_hat,
-                                   nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream)),
+  return from_cuda(taser::unfolded(false, precision, batch, N, T_tilde, D, inv_norm, alpha_t, t_max, c, ckpt, soft,
+                                   s_hat, nullptr, nullptr, nullptr, static_cast<cudaStream_t>(stream)),
                    "unfolded_forward");
 }
 
 taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde, const float* D,
-                                     const float* inv_norm, const float* alpha_t, int t_max, int c,
+                                     const float* inv_norm, const float* alpha_t, int t_max, int c, int precision,
                                      const float* ckpt, const float* grad_soft, float* grad_tau, float* grad_alpha,
                                      void* stream) {
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= 33, "unfolded TASER supports 2 <= N <= 33 (got %d)", N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
   TASER_REQUIRE(c >= 1 && c <= t_max, "checkpoint spacing c must lie in [1, t_max] (got %d)", c);
-  TASER_REQUIRE(taser::unfolded_backward_smem(N, c) <= 227 * 1024,
-                "checkpoint spacing c = %d needs %zu bytes of shared memory per block (limit 232448)", c,
-                taser::unfolded_backward_smem(N, c));
+  TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC ||
+                    precision == TASER_FIXED14,
+                "unknown precision %d", precision);
+  if (precision == TASER_FIXED14) return fail(TASER_ERR_UNSUPPORTED, "unfolded TASER has no fixed-point datapath");
+  {
+    const size_t need = unfolded_tc_path(precision, N) ? taser::unfolded_tc_backward_smem(c)
+                                                       : taser::unfolded_backward_smem(N, c);
+    TASER_REQUIRE(need <= 227 * 1024,
+                  "checkpoint spacing c = %d needs %zu bytes of shared memory per block (limit 232448)", c, need);
+  }
   if (batch == 0) return ok();
   TASER_REQUIRE_PTR(T_tilde, "T_tilde");
   TASER_REQUIRE_PTR(D, "D");
@@ -410,8 +428,8 @@ taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde,
   TASER_REQUIRE_PTR(grad_soft, "grad_soft");
   TASER_REQUIRE_PTR(grad_tau, "grad_tau");
   if (grad_alpha != nullptr) TASER_REQUIRE(aligned16(grad_alpha), "grad_alpha must be 16-byte aligned");
-  return from_cuda(taser::unfolded(true, batch, N, T_tilde, D, inv_norm, alpha_t, t_max, c, const_cast<float*>(ckpt),
-                                   nullptr, nullptr, grad_soft, grad_tau, grad_alpha,
+  return from_cuda(taser::unfolded(true, precision, batch, N, T_tilde, D, inv_norm, alpha_t, t_max, c,
+                                   const_cast<float*>(ckpt), nullptr, nullptr, grad_soft, grad_tau, grad_alpha,
                                    static_cast<cudaStream_t>(stream)),
                    "unfolded_backward");
 }

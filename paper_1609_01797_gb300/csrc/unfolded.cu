@@ -327,11 +327,22 @@ size_t unfolded_backward_smem(int N, int c) {
   return (size_t)UfCfg<32>::BWD_WARPS * (c + 2) * tri_off(NB + 1) * sizeof(float);
 }
 
-cudaError_t unfolded(bool backward, int64_t batch, int N, const float* Tt, const float* D, const float* inv_norm,
-                     const float* alpha_t, int t_max, int c, float* ckpt, float* soft, int8_t* s_hat,
-                     const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st) {
+cudaError_t unfolded_tc(bool backward, bool fp16, int64_t batch, int N, const float* Tt, const float* D,
+                        const float* inv_norm, const float* alpha_t, int t_max, int c, float* ckpt, float* soft,
+                        int8_t* s_hat, const float* grad_soft, float* grad_tau, cudaStream_t st);
+
+// precision: TASER_FP32, or TASER_BF16_TC / TASER_FP16_TC (tensor-core kernels for bucket 32;
+// smaller N runs the FP32 kernels).
+cudaError_t unfolded(bool backward, int precision, int64_t batch, int N, const float* Tt, const float* D,
+                     const float* inv_norm, const float* alpha_t, int t_max, int c, float* ckpt, float* soft,
+                     int8_t* s_hat, const float* grad_soft, float* grad_tau, float* grad_alpha, cudaStream_t st) {
   cudaError_t e;
-  switch (bucket_of(N)) {
+  const bool tc = precision != TASER_FP32 && bucket_of(N) == 32;
+  switch (tc ? -1 : bucket_of(N)) {
+    case -1:
+      e = unfolded_tc(backward, precision == TASER_FP16_TC, batch, N, Tt, D, inv_norm, alpha_t, t_max, c, ckpt, soft,
+                      s_hat, grad_soft, grad_tau, st);
+      break;
     case 8:
       e = launch_unfolded<8>(backward, batch, N, Tt, D, inv_norm, alpha_t, t_max, c, ckpt, soft, s_hat, grad_soft,
                              grad_tau, st);

@@ -1,7 +1,8 @@
 """Seeded synthetic workloads for TASER detection experiments.
 
-This module only draws random channels, symbols and noise (numpy PCG64); it holds
-none of the detector's arithmetic, so both the FP64 oracle and the CUDA path can
+This module only draws random channels, symbols and noise (numpy PCG64, or a seeded
+torch generator on the GPU for workloads that need fresh instances at every step); it
+holds none of the detector's arithmetic, so both the FP64 oracle and the CUDA path can
 consume the same inputs.
 
 Models (Sec. II-A and II-B of the paper):
@@ -15,7 +16,7 @@ Arrays are complex64 (what the C-ABI consumes). Bits are returned as +-1 int8.
 """
 import numpy as np
 
-__all__ = ["rng_for", "make_mimo", "make_jed", "make_uneven", "UNEVEN_SHAPES"]
+__all__ = ["rng_for", "make_mimo", "make_jed", "make_uneven", "UNEVEN_SHAPES", "make_mimo_device"]
 
 
 def rng_for(seed):
@@ -123,3 +124,42 @@ def make_uneven(n, seed=0, shapes=UNEVEN_SHAPES, snr_range=(4.0, 16.0), t_max_ch
         per_shape.append(w)
     return {"shape_idx": shape_idx, "snr_db": snr_db, "t_max": t_max, "per_shape": per_shape,
             "shapes": tuple(shapes)}
+
+
+def make_mimo_device(n, B, U, snr_db, constellation="qpsk", seed=0, device="cuda"):
+    """make_mimo's recipe drawn on a CUDA device with a seeded torch generator, for
+    workloads that need fresh instances at every step (a different random stream from
+    make_mimo's PCG64, same distributions).
+
+    snr_db: a scalar, or a (lo, hi) pair for SNRs drawn uniformly per instance.  Returns
+    H complex64 [n, B, U], y complex64 [n, B] and the transmitted signs int8 [n, M] in
+    decision order (BPSK: M = U; QPSK: real parts then imaginary parts, M = 2U), all on
+    the device.
+    """
+    import torch
+    if constellation not in ("bpsk", "qpsk"):
+        raise ValueError("constellation must be 'bpsk' or 'qpsk'")
+    gen = torch.Generator(device=device)
+    gen.manual_seed(int(seed))
+    half = 0.5 ** 0.5
+
+    def cn(shape):
+        return torch.view_as_complex(torch.normal(0.0, half, tuple(shape) + (2,), generator=gen, device=device))
+
+    if isinstance(snr_db, (tuple, list)):
+        lo, hi = snr_db
+        snr = lo + (hi - lo) * torch.rand((n,), generator=gen, device=device, dtype=torch.float64)
+    else:
+        snr = torch.full((n,), float(snr_db), device=device, dtype=torch.float64)
+    H = cn((n, B, U))
+    bre = torch.randint(0, 2, (n, U), generator=gen, device=device, dtype=torch.int8) * 2 - 1
+    if constellation == "qpsk":
+        bim = torch.randint(0, 2, (n, U), generator=gen, device=device, dtype=torch.int8) * 2 - 1
+        s = torch.complex(bre.float(), bim.float()) * half
+        truth = torch.cat([bre, bim], dim=1)
+    else:
+        s = torch.complex(bre.float(), torch.zeros_like(bre, dtype=torch.float32))
+        truth = bre
+    n0 = (U / 10.0 ** (snr / 10.0)).float()
+    y = torch.bmm(H, s.unsqueeze(2)).squeeze(2) + cn((n, B)) * n0.sqrt()[:, None]
+    return H.contiguous(), y.contiguous(), truth

@@ -129,3 +129,12 @@ def test_monitored_unsupported_configurations(lib):
     assert _monitored(lib, prec=3) == 2
     assert _monitored(lib, batch=0, T=None, D=None, tau=None, s=None) == 0
     assert _monitored(lib, prec=1, N=9, batch=0) == 0          # N < 10 runs the FP32 kernel
+
+
+def test_unfolded_rejects_fixed_point_and_unknown_precision(lib):
+    f = lambda prec: lib.taser_unfolded_forward(1, 33, P16, P16, P16, P16, 10, 4, prec, P16, P16, None, None)
+    assert f(3) == 2 and b"fixed-point" in lib.taser_last_error()
+    assert f(7) == 1
+    b = lambda prec, c: lib.taser_unfolded_backward(1, 33, P16, P16, P16, P16, 100, c, prec, P16, P16, P16, None, None)
+    assert b(1, 45) == 1 and b"shared memory" in lib.taser_last_error()     # tensor cores: c <= 44
+    assert b(0, 93) == 1 and b"shared memory" in lib.taser_last_error()     # FP32: c <= 92

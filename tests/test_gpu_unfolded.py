@@ -183,3 +183,96 @@ def test_alpha_gradient_matches_gpu_central_differences():
         hm = np.float32(alpha[t]) - np.float32(am[t])
         fd[t] = (loss(ap)[0] - loss(am)[0]) / (float(hp) + float(hm))
     assert np.abs(g - fd).max() <= 2e-3 * np.abs(fd).max() + 1e-7, (g, fd)
+
+
+# Tensor-core unfolded TASER (BF16/FP16 products, FP32 master iterates and prox), bucket 32.
+TC_CASES = [(96, 128, 16, "qpsk", 10, 4, "bf16_tc"), (64, 24, 12, "qpsk", 7, 3, "bf16_tc"),
+            (80, 40, 20, "bpsk", 10, 4, "fp16_tc"), (48, 64, 32, "bpsk", 12, 5, "bf16_tc"),
+            (40, 128, 16, "qpsk", 20, 5, "fp16_tc")]
+
+
+@pytest.mark.parametrize("n,B,U,const,t_max,c,precision", TC_CASES)
+def test_unfolded_tensor_core_forward(T, n, B, U, const, t_max, c, precision):
+    """Soft outputs within 1e-2 and checkpoints within the detector's tensor-core tolerance
+    (3e-2 relative Frobenius) of the FP64 oracle; decisions equal wherever |x_k| exceeds
+    5e-2 ||x||."""
+    Tt, D, inv, alpha, _ = setup(n, B, U, const, t_max, seed=200 + U)
+    tau_t = alpha[None, :].astype(np.float64) * inv[:, None].astype(np.float64)
+    L, Ls = O.unfolded_forward(Tt.astype(np.float64), D.astype(np.float64), tau_t)
+    soft_o = O.soft_output(L, D.astype(np.float64))
+    soft, s_hat, ckpt = T.unfolded_forward(*dev(Tt, D, inv, alpha), c, precision=precision)
+    torch.cuda.synchronize()
+    assert np.abs(soft.cpu().numpy() - soft_o).max() <= 1e-2
+    conf = np.abs(soft_o) > 5e-2 * np.linalg.norm(soft_o, axis=1, keepdims=True)
+    np.testing.assert_array_equal(s_hat.cpu().numpy()[conf], np.where(soft_o >= 0, 1, -1)[conf])
+    ck = ckpt.cpu().numpy().astype(np.float64)
+    for k in range(ck.shape[1]):
+        ref = Ls[k * c]
+        err = np.linalg.norm(ck[:, k] - ref, axis=(1, 2)) / np.linalg.norm(ref, axis=(1, 2))
+        assert err.max() <= 3e-2, (k, err.max())
+
+
+@pytest.mark.parametrize("n,B,U,const,t_max,c,precision", TC_CASES)
+def test_unfolded_tensor_core_backward(T, n, B, U, const, t_max, c, precision):
+    """dloss/dtau_t of the tensor-core adjoint against the FP64 reverse mode (on the FP64
+    forward): the adjoint differentiates the tensor-core forward, whose products carry
+    about 2^-8 relative error, so the entries agree to 5e-2 of the batch's largest entry
+    (not of each instance's: where an instance has converged to an exact sign pattern its
+    FP64 gradient is ~1e-13 and the tensor-core iterates' rounding noise, ~1e-7, is all
+    that remains), and dloss/dalpha_t, the sum over the batch, to 5e-2 of its largest entry."""
+    Tt, D, inv, alpha, truth = setup(n, B, U, const, t_max, seed=300 + U)
+    dT, dD, dinv, dalpha = dev(Tt, D, inv, alpha)
+    soft, _, ckpt = T.unfolded_forward(dT, dD, dinv, dalpha, c, precision=precision)
+    x = soft.cpu().numpy().astype(np.float64)
+    g_soft = (2.0 * (x - truth) / x.size).astype(np.float32)
+    grad_tau, grad_alpha = T.unfolded_backward(dT, dD, dinv, dalpha, c, ckpt, dev(g_soft)[0], precision=precision)
+    torch.cuda.synchronize()
+    tau_t = alpha[None, :].astype(np.float64) * inv[:, None].astype(np.float64)
+    _, Ls = O.unfolded_forward(Tt.astype(np.float64), D.astype(np.float64), tau_t)
+    g_o = O.unfolded_backward(Tt.astype(np.float64), D.astype(np.float64), tau_t, Ls, g_soft.astype(np.float64))
+    g = grad_tau.cpu().numpy().astype(np.float64)
+    assert np.abs(g - g_o).max() <= 5e-2 * np.abs(g_o).max(), np.abs(g - g_o).max() / np.abs(g_o).max()
+    ga = (g * inv[:, None].astype(np.float64)).sum(axis=0)
+    ga_o = (g_o * inv[:, None].astype(np.float64)).sum(axis=0)
+    assert np.abs(ga - ga_o).max() <= 5e-2 * np.abs(ga_o).max(), (ga, ga_o)
+    np.testing.assert_allclose(grad_alpha.cpu().numpy(), ga, rtol=1e-5, atol=1e-7 * np.abs(ga).max())
+
+
+def test_unfolded_tensor_core_checkpoint_spacing_and_small_n(T):
+    """Every checkpoint spacing gives the same tensor-core gradient bit for bit; below the
+    tensor-core bucket (N <= 17) the tensor-core precisions run the FP32 kernels."""
+    Tt, D, inv, alpha, truth = setup(50, 128, 16, "qpsk", 12, seed=7)
+    dT, dD, dinv, dalpha = dev(Tt, D, inv, alpha)
+    g_soft = dev((np.random.default_rng(3).standard_normal((50, 32)) * 1e-3).astype(np.float32))[0]
+    ref = None
+    for c in (1, 3, 4, 12):
+        soft, _, ckpt = T.unfolded_forward(dT, dD, dinv, dalpha, c, precision="bf16_tc")
+        gt, _ = T.unfolded_backward(dT, dD, dinv, dalpha, c, ckpt, g_soft, precision="bf16_tc")
+        torch.cuda.synchronize()
+        if ref is None:
+            ref = gt.clone()
+        assert torch.equal(gt, ref), c
+    Tt, D, inv, alpha, _ = setup(30, 32, 8, "qpsk", 6, seed=8)        # N = 17
+    a = dev(Tt, D, inv, alpha)
+    s32, _, _ = T.unfolded_forward(*a, 3, precision="fp32")
+    stc, _, _ = T.unfolded_forward(*a, 3, precision="bf16_tc")
+    assert torch.equal(s32, stc)
+
+
+def test_unfolded_tensor_core_training_lowers_the_loss(T):
+    t_max, c = 10, 4
+    alpha = torch.full((t_max,), 0.5, device="cuda", requires_grad=True)
+    opt = torch.optim.Adam([alpha], lr=0.05)
+    losses = []
+    for step in range(12):
+        w = make_mimo(1024, 128, 16, np.random.default_rng(step).uniform(4, 14, 1024), "qpsk", seed=800 + step)
+        out = T.build_T("mimo_qpsk", *dev(w["H"], w["y"]), alpha=0.5)
+        truth = dev(np.concatenate([w["bits_re"], w["bits_im"]], 1).astype(np.float32))[0]
+        soft = T.UnfoldedTASER.apply(alpha, out["T_tilde"], out["D"], 1.0 / out["spec_norm"], c, "bf16_tc")
+        loss = torch.mean((soft - truth) ** 2)
+        opt.zero_grad()
+        loss.backward()
+        opt.step()
+        losses.append(loss.item())
+    assert torch.isfinite(alpha.grad).all()
+    assert np.mean(losses[-3:]) < losses[0]
