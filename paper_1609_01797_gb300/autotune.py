@@ -59,3 +59,15 @@ def tune_uneven(items, T_pool, D_pool, tau, s_pool, workspace, precision="bf16_t
 def save(report, path):
     with open(path, "w") as f:
         json.dump(report, f, indent=1)
+
+
+def load(path):
+    """The taser_uneven_tuning of a report written by save() (checkpoint of a tuning run)."""
+    with open(path) as f:
+        report = json.load(f)
+    bps, pop = [0, 0, 0, 0], [0, 0, 0, 0]
+    for b in range(4):
+        entry = report["buckets"].get(str(8 << b))
+        if entry is not None:
+            bps[b], pop[b] = int(entry["blocks_per_sm"]), int(entry["pop"])
+    return make_tuning(bps, pop)

@@ -3,6 +3,8 @@
 #include <cstdio>
 #include <cstring>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "common.cuh"
 
 namespace taser {
@@ -59,6 +61,16 @@ taser_status from_cuda(cudaError_t e, const char* where) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
+// NVTX range over an entry point (host side: argument checks and the enqueue of its
+// kernels), so timelines and ncu's --nvtx filters can attribute the kernels to the call.
+// Without an attached tool the NVTX calls return at once.
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
+
 #define TASER_REQUIRE(cond, ...)                                  \
   do {                                                            \
     if (!(cond)) return fail(TASER_ERR_INVALID_ARG, __VA_ARGS__); \
@@ -102,6 +114,7 @@ const char* taser_last_error(void) { return g_err; }
 taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y, const void* y,
                            float alpha, float* T_tilde, float* D, float* tau, float* spec_norm, uint32_t* flags,
                            void* stream) {
+  const CallRange nvtx_range("taser_build_T");
   TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK ||
                     kind == TASER_SIMO_JED_QPSK,
                 "unknown problem kind %d", kind);
@@ -136,6 +149,7 @@ taser_status taser_build_T(int kind, int64_t batch, int B, int U_or_K, const voi
 
 taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int structure, float alpha, float* tau,
                              float* spec_norm, void* stream) {
+  const CallRange nvtx_range("taser_step_size");
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
   TASER_REQUIRE(alpha > 0.f && alpha < 1.f, "alpha must lie in (0, 1) (got %g)", (double)alpha);
@@ -163,6 +177,7 @@ taser_status taser_step_size(int64_t batch, int N, const float* T_tilde, int str
 
 taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const float* D, const float* tau, int t_max,
                           int precision, int lnn_mode, float* L, int8_t* s_hat, uint32_t* flags, void* stream) {
+  const CallRange nvtx_range("taser_detect");
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
@@ -196,6 +211,7 @@ taser_status taser_detect(int64_t batch, int N, const float* T_tilde, const floa
 taser_status taser_detect_monitored(int64_t batch, int N, const float* T_tilde, const float* D, const float* tau,
                                     int t_max, int precision, int lnn_mode, float ascent_tol, double* objective,
                                     float* L, int8_t* s_hat, uint32_t* flags, void* stream) {
+  const CallRange nvtx_range("taser_detect_monitored");
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= TASER_MAX_N, "N = %d outside [2, %d]", N, TASER_MAX_N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
@@ -296,6 +312,7 @@ size_t taser_host_workspace_bytes(int kind, int64_t batch, int B, int U_or_K) {
 taser_status taser_run_host(int kind, int64_t batch, int B, int U_or_K, const void* H_or_Y, const void* y,
                             float alpha, int t_max, int precision, int lnn_mode, void* workspace,
                             size_t workspace_bytes, int8_t* s_hat, uint32_t* flags, void* stream) {
+  const CallRange nvtx_range("taser_run_host");
   TASER_REQUIRE(kind == TASER_MIMO_BPSK || kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_BPSK ||
                     kind == TASER_SIMO_JED_QPSK,
                 "unknown problem kind %d", kind);
@@ -380,6 +397,7 @@ bool unfolded_tc_path(int precision, int N) {
 taser_status taser_unfolded_forward(int64_t batch, int N, const float* T_tilde, const float* D, const float* inv_norm,
                                     const float* alpha_t, int t_max, int c, int precision, float* ckpt, float* soft,
                                     int8_t* s_hat, void* stream) {
+  const CallRange nvtx_range("taser_unfolded_forward");
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= 33, "unfolded TASER supports 2 <= N <= 33 (got %d)", N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
@@ -405,6 +423,7 @@ taser_status taser_unfolded_backward(int64_t batch, int N, const float* T_tilde,
                                      const float* inv_norm, const float* alpha_t, int t_max, int c, int precision,
                                      const float* ckpt, const float* grad_soft, float* grad_tau, float* grad_alpha,
                                      void* stream) {
+  const CallRange nvtx_range("taser_unfolded_backward");
   TASER_REQUIRE(batch >= 0, "batch must be >= 0 (got %lld)", (long long)batch);
   TASER_REQUIRE(N >= 2 && N <= 33, "unfolded TASER supports 2 <= N <= 33 (got %d)", N);
   TASER_REQUIRE(t_max >= 1, "t_max must be >= 1 (got %d)", t_max);
@@ -447,6 +466,7 @@ taser_status taser_detect_uneven(int64_t n_items, const taser_item* items, const
                                  const float* tau, int precision, int lnn_mode, float* L_pool, int8_t* s_pool,
                                  uint32_t* flags, void* workspace, size_t workspace_bytes,
                                  const taser_uneven_tuning* tuning, void* stream) {
+  const CallRange nvtx_range("taser_detect_uneven");
   TASER_REQUIRE(n_items >= 0 && n_items <= 0x7fffffff, "n_items must lie in [0, 2^31) (got %lld)",
                 (long long)n_items);
   TASER_REQUIRE(precision == TASER_FP32 || precision == TASER_BF16_TC || precision == TASER_FP16_TC ||
