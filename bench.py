@@ -81,11 +81,12 @@ KERNEL_SOURCES = {"build": "build_T.cu", "spectral": "spectral.cu", "detect_tc":
                   "detect_fp32": "detect_fp32.cu", "detect_fx14": "detect_fx14.cu"}
 
 
-def measured_traffic():
-    """DRAM bytes per instance per kernel from the committed ncu summary, kept only while
-    the kernel's source is unchanged since the counters were taken (sha1 match)."""
+def measured_traffic(name="dram_traffic.txt"):
+    """Per-kernel figures from a committed ncu summary (DRAM bytes per instance, or the
+    tensor-pipe active fraction), kept only while the kernel's source is unchanged since
+    the counters were taken (sha1 match)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    path = os.path.join(ROOT, "profiles", name)
     out = {}
     if not os.path.exists(path):
         return out
@@ -897,6 +898,14 @@ def main():
         return traffic[key] * n if key in traffic else None
 
     det_tc = n / (head["detect_ms"] * 1e-3) / 1e12 * fl                      # TFLOP/s per GPU
+    padded_tf = n / (head["detect_ms"] * 1e-3) / 1e12 * (14 * 4096 * T_MAX)
+    prox_fl = T_MAX * (3 * N * (N + 1) // 2 + N)
+    in_bytes = 4 * (N * (N - 1) // 2 + N + 1)
+    bounds = {"tensor": bf16_peak * 1e12 / fl, "fp32_prox": fp32_peak * 1e12 / prox_fl,
+              "hbm": hbm_peak * 1e9 / in_bytes}
+    composite_by = min(bounds, key=bounds.get)
+    composite = bounds[composite_by]
+    pipe_util = measured_traffic("pipe_util.txt")
     build_gbs = n * build_bytes_per_instance(B, U, N) / (head["build_ms"] * 1e-3) / 1e9
     spec_tf = n * spectral_flops_per_instance(U) / (head["spectral_ms"] * 1e-3) / 1e12
     roofs = {
@@ -904,7 +913,17 @@ def main():
             "kernel": "detect_tc_kernel<32,bf16> (mma.sync m16n8k16)", "bound": "tensor", "achieved": det_tc,
             "peak": bf16_peak, "unit": "TFLOP/s", "frac": det_tc / bf16_peak, "traffic": tr("detect_tc"),
             "peak_source": peak_src, "algorithmic_flops_per_launch": fl * n, "ms_per_launch": head["detect_ms"],
-            "fp32_pipe_frac": det_tc / fp32_peak}),
+            "fp32_pipe_frac": det_tc / fp32_peak,
+            # the mma.sync work actually issued: 14 m16n8k16 per iteration at N = 33 (row blocks
+            # 0 and 1: 2 + 8, row N as the transposed product: 4), 4,096 flops each
+            "padded_issue": {"flops_per_instance": 14 * 4096 * T_MAX, "achieved": padded_tf, "unit": "TFLOP/s",
+                             "frac": padded_tf / bf16_peak},
+            # min(tensor pipe at the algorithmic flops, FP32 pipe at the prox's flops, HBM at the
+            # algorithmic input bytes of T~ lower off-diagonal, D and tau) in detections/s
+            "composite_bound": {"det_per_s": composite, "limited_by": composite_by,
+                                "achieved_det_per_s": n / (head["detect_ms"] * 1e-3),
+                                "frac": n / (head["detect_ms"] * 1e-3) / composite},
+            "tensor_pipe_active_ncu": pipe_util.get("detect_tc")}),
         "build": (head["build_ms"], {
             "kernel": "build_T_kernel<17> (FP16 split mma.sync Gram)", "bound": "hbm", "achieved": build_gbs,
             "peak": hbm_peak, "unit": "GB/s", "frac": build_gbs / hbm_peak, "traffic": tr("build"),

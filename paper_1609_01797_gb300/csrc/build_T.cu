@@ -142,12 +142,20 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   };
 
   float acc[MT][NT][4];
+  // Exponent e_q of the power-of-two scale of complex column q = 4j + tq (FP16 Gram only):
+  // the accumulators hold Gamma'_pq = 2^(e_p + e_q) Gamma_pq.
+  int exq[NT];
+#pragma unroll
+  for (int j = 0; j < NT; ++j) exq[j] = 0;
   if constexpr (C::F16) {
     // Per-column power-of-two scales: this lane's columns 8j + g are multiplied by 2^ex[j]
-    // before the FP16 split, chosen from the first 32 antenna rows so that their largest
-    // magnitude lands in [2^6, 2^7).  A later value beyond FP16's range (65504) becomes an
-    // infinite high part and a non-finite accumulator; the whole Gram then restarts with every
-    // scale 2^-9 smaller.
+    // before the FP16 split, chosen from the first 32 antenna rows so that the largest
+    // magnitude of the complex column (its real and imaginary parts share one scale) lands in
+    // [2^6, 2^7).  A later value beyond FP16's range (65504) becomes an infinite high part and
+    // a non-finite accumulator; the whole Gram then restarts with every scale 2^-9 smaller.
+    // Sharing the scale within a complex column makes Gamma'_pq = 2^(e_p + e_q) Gamma_pq, so
+    // the normalised T~_pq = Gamma'_pq / (D'_p D'_q) needs no unscaling (the powers of two
+    // cancel exactly) and only D_p = D'_p 2^-e_p does.
     int ex[NT];
     float sc[NT];
   #pragma unroll
@@ -196,6 +204,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
             for (int r = 0; r < 32 / 4; ++r) m = fmaxf(m, fabsf(Ws[(tq + 4 * r) * WS + 8 * j + g]));
             m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 1));
             m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 2));
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 4));   // re and im of one column
             const int e2 = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;   // floor(log2 m), m normal
             ex[j] = (m > 0.f && e2 > -127) ? min(max(6 - e2, -100), 100) : 0;
           }
@@ -256,34 +265,9 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   #pragma unroll
       for (int j = 0; j < NT; ++j) ex[j] -= 9;
     }
-    // Undo the scales: G'[m][n] was computed as 2^(ex_m + ex_n) G'[m][n].  Row m = 16i + g + 8h
-    // is this lane's column of n-tile 2i + h; column n = 8j + 2tq + p is held by lane 4 (2tq + p).
-    {
-      int exc[NT][2];
-  #pragma unroll
-      for (int j = 0; j < NT; ++j)
-  #pragma unroll
-        for (int p = 0; p < 2; ++p) exc[j][p] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq + p));
-  #pragma unroll
-      for (int i = 0; i < MT; ++i)
-  #pragma unroll
-        for (int j = 0; j < NT; ++j) {
-          if (!C::tile(i, j)) continue;
-  #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int h = e >> 1;
-            const int er = 2 * i + h < NT ? ex[2 * i + h < NT ? 2 * i + h : 0] : 0;
-            const int sh = -(er + exc[j][e & 1]);
-            if constexpr (MP == 17) {
-              // 2^sh as one exact multiply while it is a normal float, else ldexpf.
-              const float v = acc[i][j][e] * pow2i(min(max(sh, -126), 127));
-              acc[i][j][e] = (sh >= -126 && sh <= 127) ? v : ldexpf(acc[i][j][e], sh);
-            } else {
-              acc[i][j][e] = ldexpf(acc[i][j][e], sh);
-            }
-          }
-        }
-    }
+    // The exponent of complex column q = 4j + tq is that of its real column 2q = 8j + 2tq.
+#pragma unroll
+    for (int j = 0; j < NT; ++j) exq[j] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq));
   } else {   // 3xTF32 on m16n8k8: no range handling needed, cheaper for few columns
   #pragma unroll
     for (int i = 0; i < MT; ++i)
@@ -388,14 +372,16 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
         const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
         if (holder && p == q && (p < P || p == MP - 1)) {
           const bool aug = p == MP - 1;
-          const float taa = fabsf(gre[i][j][h]) * (qpsk && !aug ? 0.5f : 1.f);
+          const float taa = fabsf(gre[i][j][h]) * (qpsk && !aug ? 0.5f : 1.f);   // 2^(2 e_p) |T_pp|
           if (!isfinite(gre[i][j][h])) fl |= TASER_FLAG_NONFINITE;
-          float da = sqrtf(taa);
+          float da = sqrtf(taa);                                                  // D'_p = 2^e_p D_p
+          float dtrue = ldexpf(da, -exq[j]);
           if (taa == 0.f) {
             da = 1.f;
+            dtrue = 1.f;
             fl |= TASER_FLAG_ZERO_DIAG;
           }
-          Dc[p] = da;
+          Dc[p] = dtrue;
           rDc[p] = 1.f / da;
         }
       }
