@@ -24,16 +24,38 @@ __device__ __forceinline__ void cp_async4(void* smem_dst, const void* gsrc) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(gsrc) : "memory");
 }
 
-// Stage T~ (N x N), D (N) and tau of one job into the warp's shared slot.  (Staging only
-// the lower triangle was measured: the DRAM bytes stayed at 4,490 per instance, because
-// rows of N = 33 floats are not aligned to the 128-byte lines, so nearly every line still
-// holds a part of the triangle; the triangle walk only added instructions.)
-__device__ __forceinline__ void stage_job(float* slot, const Job& jb, int lane) {
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+
+// Slot layout of a staged job: T~ at slot + shift (shift = 0..3, see stage_job), D at
+// slot + N^2 + 4, tau after D.  Returns the floats a slot needs for size N.
+__host__ __device__ constexpr int tc_slot_floats(int N) { return ((N * N + 4 + N + 1) + 3) & ~3; }
+
+// Stage T~ (N x N), D (N) and tau of one job into the warp's shared slot.  An instance's T~
+// starts at any 4-byte boundary (N^2 floats per instance), so it is placed `shift` floats
+// into the slot, shift = (address / 4) mod 4: then its 16-byte groups in global and shared
+// memory coincide, and all but at most 3 + 3 of the N^2 floats move as 16-byte copies
+// (9 instead of 35 copies per lane at N = 33).  Returns shift.  (Staging only the lower
+// triangle was measured: the DRAM bytes stayed at 4,490 per instance, because rows of
+// N = 33 floats are not aligned to the 128-byte lines, so nearly every line still holds a
+// part of the triangle; the triangle walk only added instructions.)
+__device__ __forceinline__ int stage_job(float* slot, const Job& jb, int lane) {
   const int N = jb.N, nn = N * N;
-  for (int i = lane; i < nn; i += 32) cp_async4(slot + i, jb.T + i);
-  for (int i = lane; i < N; i += 32) cp_async4(slot + nn + i, jb.D + i);
-  if (lane == 0) cp_async4(slot + nn + N, jb.tau);
+  const int shift = (int)((reinterpret_cast<uintptr_t>(jb.T) >> 2) & 3u);
+  float* dst = slot + shift;
+  const int head = (4 - shift) & 3;
+  const int nvec = nn > head ? (nn - head) >> 2 : 0;
+  const int tail0 = head + 4 * nvec;
+  if (lane < head && lane < nn) cp_async4(dst + lane, jb.T + lane);
+  for (int v = lane; v < nvec; v += 32) cp_async16(dst + head + 4 * v, jb.T + head + 4 * v);
+  for (int i = tail0 + lane; i < nn; i += 32) cp_async4(dst + i, jb.T + i);
+  float* dd = slot + nn + 4;
+  for (int i = lane; i < N; i += 32) cp_async4(dd + i, jb.D + i);
+  if (lane == 0) cp_async4(dd + N, jb.tau);
   asm volatile("cp.async.commit_group;" ::: "memory");
+  return shift;
 }
 
 // Instances at a fixed stride (the dense batch of taser_detect).
@@ -129,12 +151,12 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
     int8_t* s;
     uint32_t* flag;
     double* obj;
-    int N, t_max;
+    int N, t_max, shift;
   };
   static_assert(2 * sizeof(JobOut) <= kTcRecFloats * sizeof(float), "job records must fit");
   JobOut* outs = reinterpret_cast<JobOut*>(slot + slot_floats);
-  auto park = [&](const Job& jb, double* ob, int which) {
-    if (lane == 0) outs[which] = JobOut{jb.L, jb.s, jb.flag, ob, jb.N, jb.t_max};
+  auto park = [&](const Job& jb, double* ob, int shift, int which) {
+    if (lane == 0) outs[which] = JobOut{jb.L, jb.s, jb.flag, ob, jb.N, jb.t_max, shift};
   };
   Cursor<Src> cursor;
   int cur_m = 0;
@@ -144,8 +166,8 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
     double* ob = nullptr;
     have = cursor.next(src, first, ob, lane);
     if (have) {
-      stage_job(slot, first, lane);
-      park(first, ob, 0);
+      const int shift = stage_job(slot, first, lane);
+      park(first, ob, shift, 0);
     }
   }
 
@@ -153,22 +175,36 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncwarp();
     const int N = outs[cur_m].N, t_max = outs[cur_m].t_max;
-    const float* T = slot;
-    const float* Di = slot + N * N;
-    const float m2tau = -2.f * slot[N * N + N];
+    const float* T = slot + outs[cur_m].shift;
+    const float* Di = slot + N * N + 4;
+    const float m2tau = -2.f * Di[N];
     auto tval = [&](int k, int n) -> float {  // -2 tau T~ at bucket indices (k, n < NB)
       return (k < N - 1 && n < N - 1) ? m2tau * T[k * N + n] : 0.f;
     };
     // B operand: B[k][n] = -2 tau T~[k][n]; lane holds rows 2tq..2tq+1 and +8, column g.
+    // A problem that fills the bucket (N = NB + 1, e.g. QPSK 128x16 at N = 33) has no padding
+    // rows or columns, so its values need no bounds test.
     uint32_t bf[KT][NT][2];
+    if (N == NB + 1) {
 #pragma unroll
-    for (int kt = 0; kt < KT; ++kt)
+      for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-      for (int nt = 0; nt < NT; ++nt) {
-        const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
-        bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
-        bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
-      }
+        for (int nt = 0; nt < NT; ++nt) {
+          const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
+          const float* c0 = T + k0 * (NB + 1) + n;
+          bf[kt][nt][0] = pack2<FP16>(m2tau * c0[0], m2tau * c0[NB + 1]);
+          bf[kt][nt][1] = pack2<FP16>(m2tau * c0[8 * (NB + 1)], m2tau * c0[9 * (NB + 1)]);
+        }
+    } else {
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt)
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
+          bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
+          bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
+        }
+    }
     // MON: T^ = hi + lo in BF16 (B layout of bf).
     uint32_t mbh[MON ? KT : 1][NT][2], mbl[MON ? KT : 1][NT][2];
     if constexpr (MON) {
@@ -219,8 +255,8 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
       double* ob = nullptr;
       have_next = cursor.next(src, nxt, ob, lane);
       if (have_next) {
-        stage_job(slot, nxt, lane);
-        park(nxt, ob, cur_m ^ 1);
+        const int shift = stage_job(slot, nxt, lane);
+        park(nxt, ob, shift, cur_m ^ 1);
       }
     }
     float LNN = DN;
@@ -541,7 +577,7 @@ static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float*
                              int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st,
                              double* obj = nullptr, float ascent_tol = 0.f) {
   using C = TcCfg<NB>;
-  const int slot_floats = ((N * N + N + 1) + 3) & ~3;
+  const int slot_floats = tc_slot_floats(N);
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -620,7 +656,7 @@ cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm
   src.L_pool = L_pool;
   src.s_pool = s_pool;
   src.flags = flags;
-  const int slot_floats = (((nb + 1) * (nb + 1) + (nb + 1) + 1) + 3) & ~3;
+  const int slot_floats = tc_slot_floats(nb + 1);
   switch (nb) {
     case 64:
       return detect_tc64_queue(fp16, q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
