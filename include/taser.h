@@ -68,7 +68,10 @@ typedef enum {
 typedef enum {
     TASER_FP32 = 0,      /* FP32 FMA pipe                                              */
     TASER_BF16_TC = 1,   /* tensor cores, BF16 operands, FP32 accumulation             */
-    TASER_FP16_TC = 2,   /* tensor cores, FP16 operands, FP32 accumulation             */
+    TASER_FP16_TC = 2,   /* tensor cores, FP16 operands, FP32 accumulation; the operands
+                            are L~ (|L~_ik| <= D_kk) and -2 tau T~ (|.| <= 2 alpha), so D must
+                            stay inside FP16's normal range (about 1e-4 .. 6e4); BF16 has
+                            FP32's range                                                */
     TASER_FIXED14 = 3    /* 14-bit fixed point of Sec. IV-D, exact integer emulation   */
 } taser_precision;
 

@@ -91,6 +91,12 @@ __device__ __forceinline__ void split_f16(float x0, float x1, uint32_t& hi, uint
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
 
+// An int known at compile time, usable where a runtime int is expected.
+template <int V>
+struct CInt {
+  __host__ __device__ constexpr operator int() const { return V; }
+};
+
 // 2^e as a float for -126 <= e <= 127.
 __device__ __forceinline__ float pow2i(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
@@ -390,74 +396,82 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
   if (lane == 0 && flags != nullptr) flags[inst] = fl;
   __syncwarp();
-  // Off-diagonal and diagonal entries of T~ into the staging tile.
-  const int NU = P;                   // users / data columns
-  const int Nr = N;
+  // Off-diagonal and diagonal entries of T~ into the staging tile, then a coalesced copy of
+  // T~ and D to global memory.  NU = users / data columns, Nr = N.  A QPSK problem that
+  // fills the column bucket (U = MP - 1, e.g. 128x16) runs this with both as compile-time
+  // constants, so every address of the scatter is a lane base plus an immediate offset.
   const float dsg = jed ? -1.f : 1.f;   // sign of T_aa
+  auto scatter_and_store = [&](auto nu_c, auto nr_c) {
+    const int NU = nu_c, Nr = nr_c;
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      if (!C::tile(i, j)) continue;
+      for (int j = 0; j < NT; ++j) {
+        if (!C::tile(i, j)) continue;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
-        const bool pv = p < NU, qv = q < NU, qa = q == MP - 1, pa = p == MP - 1;
-        if (!holder || p > q || !(pv || pa) || !(qv || qa)) continue;
-        const float re = gre[i][j][h], im = gim[i][j][h];
-        const float sc = rDc[p] * rDc[q];
-        const int ap = pa ? Nr - 1 : p, aq = qa ? Nr - 1 : q;     // real index of the Re part
-        if (p == q) {
-          const float dv = re == 0.f ? 0.f : dsg;
-          Ts[ap * Nr + ap] = dv;
-          if (qpsk && !pa) {
-            Ts[(NU + p) * Nr + (NU + p)] = dv;
-            Ts[p * Nr + (NU + p)] = 0.f;
-            Ts[(NU + p) * Nr + p] = 0.f;
+        for (int h = 0; h < 2; ++h) {
+          const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
+          const bool pv = p < NU, qv = q < NU, qa = q == MP - 1, pa = p == MP - 1;
+          if (!holder || p > q || !(pv || pa) || !(qv || qa)) continue;
+          const float re = gre[i][j][h], im = gim[i][j][h];
+          const float sc = rDc[p] * rDc[q];
+          const int ap = pa ? Nr - 1 : p, aq = qa ? Nr - 1 : q;     // real index of the Re part
+          if (p == q) {
+            const float dv = re == 0.f ? 0.f : dsg;
+            Ts[ap * Nr + ap] = dv;
+            if (qpsk && !pa) {
+              Ts[(NU + p) * Nr + (NU + p)] = dv;
+              Ts[p * Nr + (NU + p)] = 0.f;
+              Ts[(NU + p) * Nr + p] = 0.f;
+            }
+            continue;
           }
-          continue;
-        }
-        if (kind == TASER_SIMO_JED_BPSK) {
-          const float v = -re * sc;
-          Ts[ap * Nr + aq] = v;
-          Ts[aq * Nr + ap] = v;
-        } else if (kind == TASER_MIMO_BPSK) {
-          const float v = (qa ? -re : re) * sc;
-          Ts[ap * Nr + aq] = v;
-          Ts[aq * Nr + ap] = v;
-        } else if (qa) {
-          // user p with the augmented column: -c [Re z; Im z].  JED QPSK: the pilot column
-          // is y_0 s_0 with s_0 = (1 + j)/sqrt2, so z = s_0 (Y_r^H y_0) (and A = [Hbar, +ybar]
-          // with T = -A^T A gives the same sign as MIMO's A = [Hbar, -ybar], T = A^T A).
-          const float c = 0.70710678118654752f;
-          const float zr = jq ? c * (re - im) : re, zi = jq ? c * (re + im) : im;
-          const float vr = -c * zr * sc, vi = -c * zi * sc;
-          Ts[p * Nr + aq] = vr;
-          Ts[aq * Nr + p] = vr;
-          Ts[(NU + p) * Nr + aq] = vi;
-          Ts[aq * Nr + (NU + p)] = vi;
-        } else {
-          // users p < q: [[Re G, -Im G], [Im G, Re G]] / 2 (negated for JED: T = -A^T A)
-          const float h = jq ? -0.5f : 0.5f;
-          const float vr = h * re * sc, vi = h * im * sc;
-          Ts[p * Nr + q] = vr;
-          Ts[q * Nr + p] = vr;
-          Ts[(NU + p) * Nr + (NU + q)] = vr;
-          Ts[(NU + q) * Nr + (NU + p)] = vr;
-          Ts[p * Nr + (NU + q)] = -vi;
-          Ts[(NU + q) * Nr + p] = -vi;
-          Ts[(NU + p) * Nr + q] = vi;
-          Ts[q * Nr + (NU + p)] = vi;
+          if (kind == TASER_SIMO_JED_BPSK) {
+            const float v = -re * sc;
+            Ts[ap * Nr + aq] = v;
+            Ts[aq * Nr + ap] = v;
+          } else if (kind == TASER_MIMO_BPSK) {
+            const float v = (qa ? -re : re) * sc;
+            Ts[ap * Nr + aq] = v;
+            Ts[aq * Nr + ap] = v;
+          } else if (qa) {
+            // user p with the augmented column: -c [Re z; Im z].  JED QPSK: the pilot column
+            // is y_0 s_0 with s_0 = (1 + j)/sqrt2, so z = s_0 (Y_r^H y_0) (and A = [Hbar, +ybar]
+            // with T = -A^T A gives the same sign as MIMO's A = [Hbar, -ybar], T = A^T A).
+            const float c = 0.70710678118654752f;
+            const float zr = jq ? c * (re - im) : re, zi = jq ? c * (re + im) : im;
+            const float vr = -c * zr * sc, vi = -c * zi * sc;
+            Ts[p * Nr + aq] = vr;
+            Ts[aq * Nr + p] = vr;
+            Ts[(NU + p) * Nr + aq] = vi;
+            Ts[aq * Nr + (NU + p)] = vi;
+          } else {
+            // users p < q: [[Re G, -Im G], [Im G, Re G]] / 2 (negated for JED: T = -A^T A)
+            const float hh = jq ? -0.5f : 0.5f;
+            const float vr = hh * re * sc, vi = hh * im * sc;
+            Ts[p * Nr + q] = vr;
+            Ts[q * Nr + p] = vr;
+            Ts[(NU + p) * Nr + (NU + q)] = vr;
+            Ts[(NU + q) * Nr + (NU + p)] = vr;
+            Ts[p * Nr + (NU + q)] = -vi;
+            Ts[(NU + q) * Nr + p] = -vi;
+            Ts[(NU + p) * Nr + q] = vi;
+            Ts[q * Nr + (NU + p)] = vi;
+          }
         }
       }
+    __syncwarp();
+    float* To = Tt + inst * (int64_t)Nr * Nr;
+    for (int e = lane; e < Nr * Nr; e += 32) To[e] = Ts[e];
+    for (int a = lane; a < Nr; a += 32) {
+      const int p = a == Nr - 1 ? MP - 1 : (qpsk && a >= NU ? a - NU : a);
+      Dout[inst * Nr + a] = Dc[p];
     }
-  __syncwarp();
-  // Coalesced copy of T~ and D to global memory.
-  float* To = Tt + inst * (int64_t)Nr * Nr;
-  for (int e = lane; e < Nr * Nr; e += 32) To[e] = Ts[e];
-  for (int a = lane; a < Nr; a += 32) {
-    const int p = a == Nr - 1 ? MP - 1 : (qpsk && a >= NU ? a - NU : a);
-    Dout[inst * Nr + a] = Dc[p];
+  };
+  if (qpsk && P == MP - 1 && N == 2 * MP - 1) {
+    scatter_and_store(CInt<MP - 1>{}, CInt<2 * MP - 1>{});
+  } else {
+    scatter_and_store(P, N);
   }
 }
 
