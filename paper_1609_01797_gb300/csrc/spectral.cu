@@ -54,6 +54,12 @@ __device__ __forceinline__ int scale_exponent(float m) {
 }
 __device__ __forceinline__ float pow2f(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
+// An int known at compile time, usable where a runtime int is expected.
+template <int V>
+struct SpecInt {
+  __host__ __device__ constexpr operator int() const { return V; }
+};
+
 // Below this squared norm (relative to the scaled matrix, largest entry about 1) the
 // column is already eliminated: the rest is rounding residue far under FP32's resolution.
 constexpr float kTinyNorm2 = 0x1p-100f;
@@ -328,30 +334,36 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
   float4* wd = xd + VB;
   float* db = reinterpret_cast<float*>(wd + VB);
   float* eb2 = db + VB;
-  const int N = 2 * U + 1;
-  const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
-  // NEG reads the negative semidefinite JED form as its (positive semidefinite) negation;
-  // the norm is the same.
-  auto t = [&](int a, int b) -> float {
-    const float v = active ? T[(int64_t)a * N + b] : 0.f;
-    return NEG ? -v : v;
-  };
-
-  // col[j] = M~[j][c], c = gl + 1; index UV is the augmented coordinate.
+  // col[j] = M~[j][c], c = gl + 1; index UV is the augmented coordinate.  A problem that
+  // fills the bucket (U = UV, e.g. QPSK 128x16) reads with compile-time sizes (addresses
+  // are a base plus immediates).
   const int c = gl + 1;
-  const bool cu = c < UV && c < U, ca = c == UV;
   float2 col[NP];
+  float m00 = 0.f;
+  auto load = [&](auto u_c) {
+    const int Uc = u_c, N = 2 * Uc + 1;
+    const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
+    // NEG reads the negative semidefinite JED form as its (positive semidefinite) negation;
+    // the norm is the same.
+    auto t = [&](int a, int b) -> float {
+      const float v = active ? T[a * N + b] : 0.f;
+      return NEG ? -v : v;
+    };
+    const bool cu = c < UV && c < Uc, ca = c == UV;
 #pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const bool ju = j < UV && j < U, ja = j == UV;
-    float2 v = make_float2(0.f, 0.f);
-    if (ju && cu) v = make_float2(t(j, c), t(U + j, c));
-    else if (ju && ca) v = make_float2(t(j, 2 * U), t(U + j, 2 * U));
-    else if (ja && cu) v = make_float2(t(c, 2 * U), -t(U + c, 2 * U));
-    else if (ja && ca) v = make_float2(t(2 * U, 2 * U), 0.f);
-    col[j] = v;
-  }
-  float m00 = U >= 1 ? t(0, 0) : 0.f;
+    for (int j = 0; j < NP; ++j) {
+      const bool ju = j < UV && j < Uc, ja = j == UV;
+      float2 v = make_float2(0.f, 0.f);
+      if (ju && cu) v = make_float2(t(j, c), t(Uc + j, c));
+      else if (ju && ca) v = make_float2(t(j, 2 * Uc), t(Uc + j, 2 * Uc));
+      else if (ja && cu) v = make_float2(t(c, 2 * Uc), -t(Uc + c, 2 * Uc));
+      else if (ja && ca) v = make_float2(t(2 * Uc, 2 * Uc), 0.f);
+      col[j] = v;
+    }
+    m00 = Uc >= 1 ? t(0, 0) : 0.f;
+  };
+  if (U == UV) load(SpecInt<UV>{});
+  else load(U);
   float amax = fabsf(m00);
 #pragma unroll
   for (int j = 0; j < NP; ++j) amax = fmaxf(amax, fmaxf(fabsf(col[j].x), fabsf(col[j].y)));
