@@ -82,11 +82,18 @@ __device__ __forceinline__ void mma_f16(float (&d)[4], const uint32_t (&a)[4], u
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-// Splits a pair of (scaled) floats into FP16 high and low parts: x = hi + lo + O(2^-22 x).
-__device__ __forceinline__ void split_f16(float x0, float x1, uint32_t& hi, uint32_t& lo) {
-  const __half2 h = __floats2half2_rn(x0, x1);
+// Scales a pair of floats of one column by sc2 = {2^e, 2^e} (exact) and splits it into FP16
+// high and low parts: x = hi + lo + O(2^-22 x).  The scaling and the residual x - hi run as
+// packed f32x2 operations.
+__device__ __forceinline__ void split_f16(float x0, float x1, uint64_t sc2, uint32_t& hi, uint32_t& lo) {
+  const uint64_t xs = f2mul(f2pack(x0, x1), sc2);
+  float a, b;
+  f2unpack(xs, a, b);
+  const __half2 h = __floats2half2_rn(a, b);
   const float2 hf = __half22float2(h);
-  const __half2 l = __floats2half2_rn(x0 - hf.x, x1 - hf.y);
+  float r0, r1;
+  f2unpack(f2fma(f2pack(hf.x, hf.y), f2pack(-1.f, -1.f), xs), r0, r1);
+  const __half2 l = __floats2half2_rn(r0, r1);
   hi = *reinterpret_cast<const uint32_t*>(&h);
   lo = *reinterpret_cast<const uint32_t*>(&l);
 }
@@ -227,10 +234,9 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
           const float* rp = buf + (16 * ks + tq) * WS + g;
   #pragma unroll
           for (int j = 0; j < NT; ++j) {
-            const float x0 = rp[8 * j] * sc[j], x1 = rp[4 * WS + 8 * j] * sc[j];
-            const float x2 = rp[8 * WS + 8 * j] * sc[j], x3 = rp[12 * WS + 8 * j] * sc[j];
-            split_f16(x0, x1, bh[j][0], bl[j][0]);
-            split_f16(x2, x3, bh[j][1], bl[j][1]);
+            const uint64_t sc2 = f2pack(sc[j], sc[j]);
+            split_f16(rp[8 * j], rp[4 * WS + 8 * j], sc2, bh[j][0], bl[j][0]);
+            split_f16(rp[8 * WS + 8 * j], rp[12 * WS + 8 * j], sc2, bh[j][1], bl[j][1]);
           }
   #pragma unroll
           for (int i = 0; i < MT; ++i) {
