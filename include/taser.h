@@ -327,7 +327,8 @@ size_t taser_uneven_workspace_bytes(int64_t n_items);
  *   T_pool, D_pool, tau (float [n_items]), L_pool (may be NULL), s_pool: device pools
  *             addressed by the items' offsets.
  *   flags     uint32 [n_items] or NULL: OR-ed flag bits; items with N or t_max out of range
- *             are skipped and get TASER_FLAG_BAD_ITEM.
+ *             are skipped and get TASER_FLAG_BAD_ITEM (the bounds-checked debug build
+ *             treats items with a negative offset the same way).
  *   workspace device buffer of taser_uneven_workspace_bytes(n_items) bytes, 256-byte aligned.
  *   tuning    per-bucket launch parameters (from the autotuner), or NULL for defaults.
  * Items are independent: their results do not depend on the queue order.
@@ -367,6 +368,28 @@ taser_status taser_run_host_static(int kind, int64_t batch, int B, int U_or_K,
                                    const void* H_or_Y, const void* y, float alpha, int t_max,
                                    int precision, int lnn_mode, int8_t* s_hat,
                                    uint32_t* flags, void* stream);
+
+/*
+ * taser_debug_report -- counters of the bounds-checked debug build.
+ *
+ * libtaser_debug.so is the same library compiled with -DTASER_DEBUG.  The paper has no
+ * counterpart: the build stands in for a device memory checker.  Every kernel tests the
+ * global and shared-memory indices it computes at run time against the extents its
+ * arguments imply (batch x per-instance sizes, the staging slots, the queue list) and
+ * against the instance's own N x N, N or N - 1 elements; an access that fails is counted
+ * and skipped.  Nothing traps and nothing waits.  Pools of taser_detect_uneven have no
+ * stated extent, so there only the offsets' signs and each item's own indices are
+ * checked.  The build also counts non-finite output values (T~, D, ||T~||, L~, the
+ * decisions' row, the unfolded soft outputs and gradients).
+ *   fails      failed index checks since the last report (all kernels, current device)
+ *   first      the first recorded failure as (source file number << 56) |
+ *              (source line << 32) | (low 32 bits of the index), or 0 if none
+ *   nonfinite  non-finite output values since the last report
+ * The three pointers are HOST pointers and must not be NULL.  Reading the counters
+ * (cudaMemcpyFromSymbol) waits for the device and clears them.  The release library
+ * (libtaser.so) returns TASER_ERR_UNSUPPORTED and leaves the outputs unchanged.
+ */
+taser_status taser_debug_report(uint64_t* fails, uint64_t* first, uint64_t* nonfinite);
 
 #ifdef __cplusplus
 }

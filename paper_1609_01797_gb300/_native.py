@@ -1,9 +1,16 @@
 """ctypes loader of libtaser.so.  There is no fallback: if the library is missing the
-import fails loudly, because every step of the detector runs in its CUDA kernels."""
+import fails loudly, because every step of the detector runs in its CUDA kernels.
+
+TASER_LIBRARY=debug in the environment loads the bounds-checked libtaser_debug.so
+instead (same ABI; see taser_debug_report in include/taser.h)."""
 import ctypes
 import os
 
-LIB_PATH = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib", "libtaser.so")
+_LIBDIR = os.path.join(os.path.dirname(os.path.abspath(__file__)), "lib")
+VARIANT = os.environ.get("TASER_LIBRARY", "release")
+if VARIANT not in ("release", "debug"):
+    raise ImportError("TASER_LIBRARY must be 'release' or 'debug' (got %r)" % VARIANT)
+LIB_PATH = os.path.join(_LIBDIR, "libtaser_debug.so" if VARIANT == "debug" else "libtaser.so")
 
 _c_i32, _c_i64, _c_f32, _vp = ctypes.c_int, ctypes.c_int64, ctypes.c_float, ctypes.c_void_p
 
@@ -29,6 +36,7 @@ SIGNATURES = {
     "taser_uneven_workspace_bytes": (ctypes.c_size_t, [_c_i64]),
     "taser_detect_uneven": (_c_i32, [_c_i64, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                      _vp, _vp]),
+    "taser_debug_report": (_c_i32, [_vp, _vp, _vp]),
 }
 
 
@@ -47,8 +55,8 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise ImportError(
-                "libtaser.so not found at %s; build it with paper_1609_01797_gb300.build.build() "
-                "(the detector has no CPU fallback)" % LIB_PATH)
+                "%s not found; build it with paper_1609_01797_gb300.build.build(%s) "
+                "(the detector has no CPU fallback)" % (LIB_PATH, "debug=True" if VARIANT == "debug" else ""))
         handle = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             fn = getattr(handle, name)

@@ -249,3 +249,18 @@ def detect_uneven(items, T_pool, D_pool, tau, s_pool, workspace, precision="fp32
                                    workspace.numel(), ctypes.byref(tune) if tune is not None else None,
                                    _stream(stream))
     check(st, "taser_detect_uneven")
+
+
+def debug_report():
+    """Counters of the bounds-checked library (TASER_LIBRARY=debug), read and cleared:
+    {"fails", "nonfinite", "first": None or {"source", "line", "index"}}.  Raises
+    TaserError (TASER_ERR_UNSUPPORTED) on the release library."""
+    from .build import source_of
+    fails, first, nonfinite = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().taser_debug_report(ctypes.byref(fails), ctypes.byref(first), ctypes.byref(nonfinite)),
+          "taser_debug_report")
+    rec = None
+    if fails.value:
+        f = first.value
+        rec = {"source": source_of(f >> 56), "line": (f >> 32) & 0xffffff, "index": f & 0xffffffff}
+    return {"fails": fails.value, "nonfinite": nonfinite.value, "first": rec}

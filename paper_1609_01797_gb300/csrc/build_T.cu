@@ -49,6 +49,13 @@ struct BuildCfg {
   static constexpr bool F16 = MP >= 17;
   __host__ __device__ static constexpr bool tile(int i, int j) { return j >= 2 * i && j < NT; }
 };
+// The Gram loop's shared-memory reads use compile-time offsets: rows below CH of a chunk,
+// columns below 8 NT, and (scale search) rows below 32 of the first two chunks.
+static_assert((BuildCfg<9>::CH - 1) * BuildCfg<9>::WS + 8 * BuildCfg<9>::NT <= BuildCfg<9>::BUF_FLOATS, "");
+static_assert((BuildCfg<17>::CH - 1) * BuildCfg<17>::WS + 8 * BuildCfg<17>::NT <= BuildCfg<17>::BUF_FLOATS, "");
+static_assert((BuildCfg<33>::CH - 1) * BuildCfg<33>::WS + 8 * BuildCfg<33>::NT <= BuildCfg<33>::BUF_FLOATS, "");
+static_assert(31 * BuildCfg<17>::WS + 8 * BuildCfg<17>::NT <= 2 * BuildCfg<17>::BUF_FLOATS, "");
+static_assert(31 * BuildCfg<33>::WS + 8 * BuildCfg<33>::NT <= BuildCfg<33>::BUF_FLOATS, "");
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
   const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
@@ -142,14 +149,23 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
     const int rows = min(CH, B - r0);
     if (crow < rows_per_iter) {
       for (int r = crow; r < rows; r += rows_per_iter) {
+        const int64_t xe = (inst * B + r0 + r) * src_cols;   // complex element of the row in X
         const float2* src = Xi + (int64_t)(r0 + r) * src_cols;
-        if (pairs) cp_async16(buf + r * WS + 4 * cu, src + 2 * cu);
-        else cp_async8(buf + r * WS + 2 * cu, src + (jed ? cu + 1 : cu));
+        if (pairs) {
+          if (TASER_IN(r * WS + 4 * cu + 3, C::BUF_FLOATS) && TASER_IN(xe + 2 * cu + 1, batch * B * src_cols))
+            cp_async16(buf + r * WS + 4 * cu, src + 2 * cu);
+        } else {
+          const int sc = jed ? cu + 1 : cu;
+          if (TASER_IN(r * WS + 2 * cu + 1, C::BUF_FLOATS) && TASER_IN(xe + sc, batch * B * src_cols))
+            cp_async8(buf + r * WS + 2 * cu, src + sc);
+        }
       }
     }
     for (int r = lane; r < rows; r += 32) {
       const float2* src = jed ? Xi + (int64_t)(r0 + r) * src_cols : yi + (r0 + r);
-      cp_async8(buf + r * WS + 2 * (MP - 1), src);
+      const int64_t se = jed ? (inst * B + r0 + r) * src_cols : inst * B + r0 + r;
+      if (TASER_IN(r * WS + 2 * (MP - 1) + 1, C::BUF_FLOATS) && TASER_IN(se, batch * B * (jed ? src_cols : 1)))
+        cp_async8(buf + r * WS + 2 * (MP - 1), src);
     }
     cp_async_commit();
   };
@@ -393,14 +409,16 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
             dtrue = 1.f;
             fl |= TASER_FLAG_ZERO_DIAG;
           }
-          Dc[p] = dtrue;
-          rDc[p] = 1.f / da;
+          if (TASER_IN(p, 72)) {
+            Dc[p] = dtrue;
+            rDc[p] = 1.f / da;
+          }
         }
       }
     }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, o);
-  if (lane == 0 && flags != nullptr) flags[inst] = fl;
+  if (lane == 0 && flags != nullptr && TASER_IN(inst, batch)) flags[inst] = fl;
   __syncwarp();
   // Off-diagonal and diagonal entries of T~ into the staging tile, then a coalesced copy of
   // T~ and D to global memory.  NU = users / data columns, Nr = N.  A QPSK problem that
@@ -409,6 +427,10 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   const float dsg = jed ? -1.f : 1.f;   // sign of T_aa
   auto scatter_and_store = [&](auto nu_c, auto nr_c) {
     const int NU = nu_c, Nr = nr_c;
+    // Ts[a] = v (a debug build checks a against the N x N tile).
+    auto put = [&](int a, float v) {
+      if (TASER_IN(a, Nr * Nr)) Ts[a] = v;
+    };
 #pragma unroll
     for (int i = 0; i < MT; ++i)
 #pragma unroll
@@ -420,26 +442,26 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
           const bool pv = p < NU, qv = q < NU, qa = q == MP - 1, pa = p == MP - 1;
           if (!holder || p > q || !(pv || pa) || !(qv || qa)) continue;
           const float re = gre[i][j][h], im = gim[i][j][h];
-          const float sc = rDc[p] * rDc[q];
+          const float sc = (TASER_IN(p, 72) && TASER_IN(q, 72)) ? rDc[p] * rDc[q] : 0.f;
           const int ap = pa ? Nr - 1 : p, aq = qa ? Nr - 1 : q;     // real index of the Re part
           if (p == q) {
             const float dv = re == 0.f ? 0.f : dsg;
-            Ts[ap * Nr + ap] = dv;
+            put(ap * Nr + ap, dv);
             if (qpsk && !pa) {
-              Ts[(NU + p) * Nr + (NU + p)] = dv;
-              Ts[p * Nr + (NU + p)] = 0.f;
-              Ts[(NU + p) * Nr + p] = 0.f;
+              put((NU + p) * Nr + (NU + p), dv);
+              put(p * Nr + (NU + p), 0.f);
+              put((NU + p) * Nr + p, 0.f);
             }
             continue;
           }
           if (kind == TASER_SIMO_JED_BPSK) {
             const float v = -re * sc;
-            Ts[ap * Nr + aq] = v;
-            Ts[aq * Nr + ap] = v;
+            put(ap * Nr + aq, v);
+            put(aq * Nr + ap, v);
           } else if (kind == TASER_MIMO_BPSK) {
             const float v = (qa ? -re : re) * sc;
-            Ts[ap * Nr + aq] = v;
-            Ts[aq * Nr + ap] = v;
+            put(ap * Nr + aq, v);
+            put(aq * Nr + ap, v);
           } else if (qa) {
             // user p with the augmented column: -c [Re z; Im z].  JED QPSK: the pilot column
             // is y_0 s_0 with s_0 = (1 + j)/sqrt2, so z = s_0 (Y_r^H y_0) (and A = [Hbar, +ybar]
@@ -447,31 +469,37 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
             const float c = 0.70710678118654752f;
             const float zr = jq ? c * (re - im) : re, zi = jq ? c * (re + im) : im;
             const float vr = -c * zr * sc, vi = -c * zi * sc;
-            Ts[p * Nr + aq] = vr;
-            Ts[aq * Nr + p] = vr;
-            Ts[(NU + p) * Nr + aq] = vi;
-            Ts[aq * Nr + (NU + p)] = vi;
+            put(p * Nr + aq, vr);
+            put(aq * Nr + p, vr);
+            put((NU + p) * Nr + aq, vi);
+            put(aq * Nr + (NU + p), vi);
           } else {
             // users p < q: [[Re G, -Im G], [Im G, Re G]] / 2 (negated for JED: T = -A^T A)
             const float hh = jq ? -0.5f : 0.5f;
             const float vr = hh * re * sc, vi = hh * im * sc;
-            Ts[p * Nr + q] = vr;
-            Ts[q * Nr + p] = vr;
-            Ts[(NU + p) * Nr + (NU + q)] = vr;
-            Ts[(NU + q) * Nr + (NU + p)] = vr;
-            Ts[p * Nr + (NU + q)] = -vi;
-            Ts[(NU + q) * Nr + p] = -vi;
-            Ts[(NU + p) * Nr + q] = vi;
-            Ts[q * Nr + (NU + p)] = vi;
+            put(p * Nr + q, vr);
+            put(q * Nr + p, vr);
+            put((NU + p) * Nr + (NU + q), vr);
+            put((NU + q) * Nr + (NU + p), vr);
+            put(p * Nr + (NU + q), -vi);
+            put((NU + q) * Nr + p, -vi);
+            put((NU + p) * Nr + q, vi);
+            put(q * Nr + (NU + p), vi);
           }
         }
       }
     __syncwarp();
     float* To = Tt + inst * (int64_t)Nr * Nr;
-    for (int e = lane; e < Nr * Nr; e += 32) To[e] = Ts[e];
+    for (int e = lane; e < Nr * Nr; e += 32) {
+      if (TASER_IN(inst * Nr * Nr + e, batch * Nr * Nr)) To[e] = Ts[e];
+      TASER_FINITE(Ts[e]);
+    }
     for (int a = lane; a < Nr; a += 32) {
       const int p = a == Nr - 1 ? MP - 1 : (qpsk && a >= NU ? a - NU : a);
-      Dout[inst * Nr + a] = Dc[p];
+      if (TASER_IN(inst * Nr + a, batch * Nr) && TASER_IN(p, 72)) {
+        Dout[inst * Nr + a] = Dc[p];
+        TASER_FINITE(Dc[p]);
+      }
     }
   };
   if (qpsk && P == MP - 1 && N == 2 * MP - 1) {
@@ -513,3 +541,5 @@ cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X,
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(build_T)

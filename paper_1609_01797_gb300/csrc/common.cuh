@@ -8,6 +8,66 @@
 
 #define TASER_FULL_MASK 0xffffffffu
 
+// Bounds-checked debug build (compiled with -DTASER_DEBUG, libtaser_debug.so).
+//   TASER_IN(i, n)   is true when 0 <= i < n.  Otherwise it counts a failure, records the
+//                    first failing translation unit, line and index, and is false, so that
+//                    the access it guards is skipped.  Nothing traps or waits.
+//   TASER_FINITE(v)  counts a non-finite output value.
+// Each translation unit has its own counters (TASER_TU numbers it); the host collects them
+// through taser_debug_report.  In release builds TASER_IN is the constant true and
+// TASER_FINITE nothing, so the compiler removes every check.
+#ifndef TASER_TU
+#define TASER_TU 0
+#endif
+#ifdef TASER_DEBUG
+namespace taser {
+namespace dbg {
+struct Word {
+  unsigned long long fails;      // failed index checks
+  unsigned long long first;      // TU << 56 | line << 32 | (index & 0xffffffff) of the first
+  unsigned long long nonfinite;  // non-finite output values
+};
+static __device__ Word word;
+static __device__ __noinline__ void record(int line, long long idx) {
+  const unsigned long long prior = atomicAdd(&word.fails, 1ull);
+  if (prior == 0ull)
+    word.first = ((unsigned long long)TASER_TU << 56) | ((unsigned long long)(line & 0xffffff) << 32) |
+                 ((unsigned long long)idx & 0xffffffffull);
+}
+static __device__ __forceinline__ bool in(long long i, long long n, int line) {
+  if (i >= 0 && i < n) return true;
+  record(line, i);
+  return false;
+}
+static __device__ __forceinline__ void finite(float v) {
+  if (!isfinite(v)) atomicAdd(&word.nonfinite, 1ull);
+}
+}  // namespace dbg
+}  // namespace taser
+#define TASER_IN(i, n) (taser::dbg::in((long long)(i), (long long)(n), __LINE__))
+#define TASER_FINITE(v) taser::dbg::finite(v)
+// Host: copies this translation unit's counters into out[3] and clears them.
+#define TASER_DEBUG_COLLECTOR(name)                                                        \
+  namespace taser {                                                                        \
+  namespace dbg {                                                                          \
+  cudaError_t take_##name(unsigned long long* out) {                                       \
+    Word w{};                                                                              \
+    cudaError_t e = cudaMemcpyFromSymbol(&w, word, sizeof(Word));                          \
+    if (e != cudaSuccess) return e;                                                        \
+    out[0] += w.fails;                                                                     \
+    if (out[1] == 0ull) out[1] = w.first;                                                  \
+    out[2] += w.nonfinite;                                                                 \
+    const Word zero{};                                                                     \
+    return cudaMemcpyToSymbol(word, &zero, sizeof(Word));                                  \
+  }                                                                                        \
+  }                                                                                        \
+  }
+#else
+#define TASER_IN(i, n) true
+#define TASER_FINITE(v) ((void)0)
+#define TASER_DEBUG_COLLECTOR(name)
+#endif
+
 namespace taser {
 
 // Bucket of variable columns used by the detection and spectral kernels: a problem
@@ -54,6 +114,10 @@ __device__ __forceinline__ Job dense_job(int64_t inst, int N, int t_max, const f
 __device__ __forceinline__ Job item_job(const taser_item& it, int64_t idx, const float* T_pool, const float* D_pool,
                                         const float* tau, float* L_pool, int8_t* s_pool, uint32_t* flags) {
   Job j;
+  // The pools' extents are not passed in: a debug build checks that the offsets are
+  // non-negative (the instance's own indices are checked where they are used).
+  (void)(TASER_IN(it.t_off, INT64_MAX) && TASER_IN(it.d_off, INT64_MAX) && TASER_IN(it.s_off, INT64_MAX) &&
+         TASER_IN(it.l_off + 1, INT64_MAX));
   j.T = T_pool + it.t_off;
   j.D = D_pool + it.d_off;
   j.tau = tau + idx;
@@ -72,9 +136,14 @@ struct Queue {
   const int* list;
   int* meta;
   int b;
+  int64_t n;   // items of the call (the length of list and items)
   __device__ __forceinline__ int count() const { return *((volatile const int*)meta + 4 + b); }
   __device__ __forceinline__ int pop(int k) const { return atomicAdd(meta + 8 + b, k); }
-  __device__ __forceinline__ int item_at(int pos) const { return list[meta[b] + pos]; }
+  __device__ __forceinline__ int item_at(int pos) const {
+    const int at = meta[b] + pos;
+    const int idx = TASER_IN(at, n) ? list[at] : 0;
+    return TASER_IN(idx, n) ? idx : 0;
+  }
 };
 
 // Packed FP32 pairs for the f32x2 FMA/multiply instructions: a pair lives in one 64-bit

@@ -75,21 +75,21 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
       float v = 0.f;
       if (k <= NB) {
         const int kr = bucket_to_real(k, N, NB);
-        if (active && jr >= 0 && kr >= 0) v = jb.T[(int64_t)kr * N + jr];
+        if (active && jr >= 0 && kr >= 0 && TASER_IN(kr * N + jr, N * N)) v = jb.T[(int64_t)kr * N + jr];
       }
       v2[h] = m2tau * v;
       if (k == NB) tNB = v2[h];
     }
     tn2[p] = f2pack(v2[0], v2[1]);
   }
-  const float Dj = (active && jr >= 0) ? jb.D[jr] : 0.f;
+  const float Dj = (active && jr >= 0 && TASER_IN(jr, N)) ? jb.D[jr] : 0.f;
   const float DN = active ? jb.D[N - 1] : 0.f;
   const float tnNN = m2tau * (active ? jb.T[(int64_t)(N - 1) * N + (N - 1)] : 0.f);
 
   // L~(0) = D (Algorithm 1 initialisation).
   for (int idx = j; idx < C::INST_FLOATS; idx += (NB <= 32 ? C::G : 64)) Ls[idx] = 0.f;
   sync_instance<NB>(bar_id);
-  Ls[j * C::S + j] = Dj;
+  if (TASER_IN(j * C::S + j, C::INST_FLOATS)) Ls[j * C::S + j] = Dj;
   if (j == 0) Ls[NB * C::S + NB] = DN;
   float l[NB + 1];
 #pragma unroll
@@ -111,8 +111,9 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
       if (lane == 0 && jb.flag != nullptr && f) atomicOr(jb.flag, f);
     }
     // Decisions s_k = sign(L~_{N,k}) (sign(0) = +1), times sign(L~_NN) in literal mode.
-    if (jr >= 0) {
+    if (jr >= 0 && TASER_IN(jr, N - 1)) {
       float r = l[NB];
+      TASER_FINITE(r);
       if (literal && LNN < 0.f) r = -r;
       jb.s[jr] = (r >= 0.f) ? int8_t(1) : int8_t(-1);
     }
@@ -121,8 +122,11 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
       for (int i = 0; i <= NB; ++i) {
         const int ir = bucket_to_real(i, N, NB);
         if (ir < 0) continue;
-        if (jr >= 0) jb.L[(int64_t)ir * N + jr] = l[i];
-        if (j == 0) jb.L[(int64_t)ir * N + (N - 1)] = (ir == N - 1) ? LNN : 0.f;
+        if (jr >= 0 && TASER_IN(ir * N + jr, N * N)) {
+          jb.L[(int64_t)ir * N + jr] = l[i];
+          TASER_FINITE(l[i]);
+        }
+        if (j == 0 && TASER_IN(ir * N + N - 1, N * N)) jb.L[(int64_t)ir * N + (N - 1)] = (ir == N - 1) ? LNN : 0.f;
       }
     }
   };
@@ -181,7 +185,7 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
       const double f = tau > 0.f ? (double)fterm / (2.0 * (double)tau) : 0.0;
       if (t > 0 && f > f_prev + (double)ascent_tol * fabs(f_prev)) fl |= TASER_FLAG_ASCENT;
       f_prev = f;
-      if (active && obj != nullptr && j == 0 && colbase == 0) obj[t] = f;
+      if (active && obj != nullptr && j == 0 && colbase == 0 && TASER_IN(t, t_loop + 1)) obj[t] = f;
       if (last_pass) {
         if constexpr (NB > 32) sync_instance<NB>(bar_id);   // xs is read before it is reused
         break;
@@ -207,7 +211,7 @@ __device__ __forceinline__ void fp32_run(const Job& jb, bool active, int t_loop,
     for (int i = 0; i <= NB; ++i) {
       if (NB > 32 && i < 32 && colbase != 0) continue;
       l[i] *= sc;
-      Ls[i * C::S + j] = l[i];
+      if (TASER_IN(i * C::S + j, C::INST_FLOATS)) Ls[i * C::S + j] = l[i];
     }
     if (literal && j == 0) Ls[NB * C::S + NB] = LNN;
     sync_instance<NB>(bar_id);
@@ -247,6 +251,7 @@ detect_fp32_kernel(int64_t batch, int N, const float* __restrict__ Tt, const flo
   const int64_t inst = (int64_t)blockIdx.x * C::IPC + local_inst;
   const bool active = inst < batch;
   float* Ls = smem + local_inst * C::INST_FLOATS;
+  if (!TASER_IN(local_inst, C::IPC)) return;
   const Job jb = dense_job(active ? inst : 0, N, t_max, Tt, Dg, tau_g, Lout, s_hat, flags);
   double* ob = (MON && obj != nullptr) ? obj + (active ? inst : 0) * (int64_t)(t_max + 1) : nullptr;
   fp32_run<NB, false, MON>(jb, active, t_max, Ls, Ls + (NB + 1) * C::S, j, lane, warp, 1 + local_inst, literal, ob,
@@ -377,3 +382,5 @@ cudaError_t detect_fp32_queue(int nb, const Queue& q, int blocks_per_sm, int rou
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(detect_fp32)

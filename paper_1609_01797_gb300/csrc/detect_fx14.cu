@@ -87,10 +87,13 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
     const bool real = j < nv;
 #pragma unroll
     for (int k = 0; k < NB; ++k)
-      tc[c][k] = (real && k < nv) ? fx_quant(__fmul_rn(tau2, T[(int64_t)k * N + j]), 4096.f, sat) : 0;
-    tNj[c] = real ? fx_quant(__fmul_rn(tau2, T[(int64_t)nv * N + j]), 4096.f, sat) : 0;
-    tjN[c] = real ? fx_quant(__fmul_rn(tau2, T[(int64_t)j * N + nv]), 4096.f, sat) : 0;
-    dq[c] = real ? fx_quant(jb.D[j], 256.f, sat) : 0;
+      tc[c][k] = (real && k < nv && TASER_IN(k * N + j, N * N))
+                     ? fx_quant(__fmul_rn(tau2, T[(int64_t)k * N + j]), 4096.f, sat)
+                     : 0;
+    const bool ok = real && TASER_IN(nv * N + j, N * N) && TASER_IN(j * N + nv, N * N) && TASER_IN(j, N);
+    tNj[c] = ok ? fx_quant(__fmul_rn(tau2, T[(int64_t)nv * N + j]), 4096.f, sat) : 0;
+    tjN[c] = ok ? fx_quant(__fmul_rn(tau2, T[(int64_t)j * N + nv]), 4096.f, sat) : 0;
+    dq[c] = ok ? fx_quant(jb.D[j], 256.f, sat) : 0;
   }
   const int tNN = fx_quant(__fmul_rn(tau2, T[(int64_t)nv * N + nv]), 4096.f, sat);
   const int lnn = fx_quant(jb.D[nv], 32.f, sat);
@@ -102,7 +105,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     const int j = lane + 32 * c;
-    if (j < nv) Lq[j * NB + j] = dq[c];
+    if (j < nv && TASER_IN(j * NB + j, NB * NB)) Lq[j * NB + j] = dq[c];
   }
   __syncwarp();
 
@@ -155,7 +158,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
 #pragma unroll
       for (int c = 0; c < CPL; ++c) {
         const int j = lane + 32 * c;
-        if (j <= i) {
+        if (j <= i && TASER_IN(i * NB + j, NB * NB)) {
           row[j] = v[c];
           x[c] += (long long)(v[c] * v[c]);
         }
@@ -211,12 +214,13 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
         const unsigned long long ux = (unsigned long long)x[c];
         const int e = (63 - __clzll(x[c])) & ~1;
         const unsigned long long idx = e >= 9 ? (ux >> (e - 9)) : (ux << (9 - e));
-        cs = dq[c] * (int)lut[idx];
+        cs = TASER_IN(idx, 2048) ? dq[c] * (int)lut[idx] : 0;
         sh = 13 + (e >> 1);
       } else {
         fl |= TASER_FLAG_ZERO_COLUMN;
       }
       for (int i = j; i < nv; ++i) {
+        if (!TASER_IN(i * NB + j, NB * NB)) continue;
         int* p = Lq + i * NB + j;
         *p = fx_sat(fx_round_shift((long long)(*p) * cs, sh), sat);
       }
@@ -233,7 +237,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
 #pragma unroll
   for (int c = 0; c < CPL; ++c) {
     const int j = lane + 32 * c;
-    if (j < nv) jb.s[j] = rowN[j] >= 0 ? int8_t(1) : int8_t(-1);
+    if (j < nv && TASER_IN(j, N - 1)) jb.s[j] = rowN[j] >= 0 ? int8_t(1) : int8_t(-1);
   }
   if (jb.L != nullptr) {
     for (int e = lane; e < N * N; e += 32) {
@@ -241,7 +245,7 @@ __device__ __forceinline__ void fx_run(const Job& jb, int* Lq, const unsigned sh
       float val = 0.f;
       if (cc <= r) {
         if (r == nv) val = cc == nv ? (float)lnn * (1.f / 32.f) : (float)rowN[cc] * (1.f / 128.f);
-        else val = (float)Lq[r * NB + cc] * (1.f / 256.f);
+        else val = TASER_IN(r * NB + cc, NB * NB) ? (float)Lq[r * NB + cc] * (1.f / 256.f) : 0.f;
       }
       jb.L[e] = val;
     }
@@ -347,3 +351,5 @@ cudaError_t detect_fx14_queue(int nb, const Queue& q, int blocks_per_sm, const f
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(detect_fx14)

@@ -41,19 +41,25 @@ __host__ __device__ constexpr int tc_slot_floats(int N) { return ((N * N + 4 + N
 // triangle was measured: the DRAM bytes stayed at 4,490 per instance, because rows of
 // N = 33 floats are not aligned to the 128-byte lines, so nearly every line still holds a
 // part of the triangle; the triangle walk only added instructions.)
-__device__ __forceinline__ int stage_job(float* slot, const Job& jb, int lane) {
+// A debug build checks every copy against the instance's N^2 floats and the slot's
+// slot_floats.
+__device__ __forceinline__ int stage_job(float* slot, const Job& jb, int lane, int slot_floats) {
   const int N = jb.N, nn = N * N;
   const int shift = (int)((reinterpret_cast<uintptr_t>(jb.T) >> 2) & 3u);
   float* dst = slot + shift;
   const int head = (4 - shift) & 3;
   const int nvec = nn > head ? (nn - head) >> 2 : 0;
   const int tail0 = head + 4 * nvec;
-  if (lane < head && lane < nn) cp_async4(dst + lane, jb.T + lane);
-  for (int v = lane; v < nvec; v += 32) cp_async16(dst + head + 4 * v, jb.T + head + 4 * v);
-  for (int i = tail0 + lane; i < nn; i += 32) cp_async4(dst + i, jb.T + i);
+  if (lane < head && lane < nn && TASER_IN(shift + lane, slot_floats)) cp_async4(dst + lane, jb.T + lane);
+  for (int v = lane; v < nvec; v += 32)
+    if (TASER_IN(head + 4 * v + 3, nn) && TASER_IN(shift + head + 4 * v + 3, slot_floats))
+      cp_async16(dst + head + 4 * v, jb.T + head + 4 * v);
+  for (int i = tail0 + lane; i < nn; i += 32)
+    if (TASER_IN(shift + i, slot_floats)) cp_async4(dst + i, jb.T + i);
   float* dd = slot + nn + 4;
-  for (int i = lane; i < N; i += 32) cp_async4(dd + i, jb.D + i);
-  if (lane == 0) cp_async4(dd + N, jb.tau);
+  for (int i = lane; i < N; i += 32)
+    if (TASER_IN(nn + 4 + i, slot_floats)) cp_async4(dd + i, jb.D + i);
+  if (lane == 0 && TASER_IN(nn + 4 + N, slot_floats)) cp_async4(dd + N, jb.tau);
   asm volatile("cp.async.commit_group;" ::: "memory");
   return shift;
 }
@@ -166,7 +172,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
     double* ob = nullptr;
     have = cursor.next(src, first, ob, lane);
     if (have) {
-      const int shift = stage_job(slot, first, lane);
+      const int shift = stage_job(slot, first, lane, slot_floats);
       park(first, ob, shift, 0);
     }
   }
@@ -192,6 +198,10 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
         for (int nt = 0; nt < NT; ++nt) {
           const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
           const float* c0 = T + k0 * (NB + 1) + n;
+          if (!TASER_IN((k0 + 9) * (NB + 1) + n, N * N)) {
+            bf[kt][nt][0] = bf[kt][nt][1] = 0u;
+            continue;
+          }
           bf[kt][nt][0] = pack2<FP16>(m2tau * c0[0], m2tau * c0[NB + 1]);
           bf[kt][nt][1] = pack2<FP16>(m2tau * c0[8 * (NB + 1)], m2tau * c0[9 * (NB + 1)]);
         }
@@ -224,7 +234,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int c = 8 * nt + 2 * tq + p;
-        tN[nt][p] = (g == 0 && c < N - 1) ? m2tau * T[(N - 1) * N + c] : 0.f;
+        tN[nt][p] = (g == 0 && c < N - 1 && TASER_IN((N - 1) * N + c, N * N)) ? m2tau * T[(N - 1) * N + c] : 0.f;
       }
     uint64_t tN2[NT];   // packed pairs (zero off the lanes g == 0 that hold row N)
 #pragma unroll
@@ -255,7 +265,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
       double* ob = nullptr;
       have_next = cursor.next(src, nxt, ob, lane);
       if (have_next) {
-        const int shift = stage_job(slot, nxt, lane);
+        const int shift = stage_job(slot, nxt, lane, slot_floats);
         park(nxt, ob, shift, cur_m ^ 1);
       }
     }
@@ -426,7 +436,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
       const double f = m2tau < 0.f ? (double)fterm / (double)m2tau : 0.0;
       if (t > 0 && f > f_prev + (double)ascent_tol * fabs(f_prev)) fl |= TASER_FLAG_ASCENT;
       f_prev = f;
-      if (lane == 0 && obj != nullptr) obj[t] = f;
+      if (lane == 0 && obj != nullptr && TASER_IN(t, t_max + 1)) obj[t] = f;
     };
 
     for (int t = 0; t < t_max; ++t) {
@@ -514,8 +524,9 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
           const int c = 8 * n + 2 * tq + p;
-          if (c < N - 1) {
+          if (c < N - 1 && TASER_IN(c, N - 1)) {
             float r = acc[MT - 1][n][p];
+            TASER_FINITE(r);
             if (literal && LNN < 0.f) r = -r;
             o.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
           }
@@ -532,10 +543,12 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
             if (M == MT - 1 && e >= 2) continue;
             const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
             const int rr = bucket_to_real(r, N, NB);
-            if (rr < 0 || c >= N - 1) continue;
+            if (rr < 0 || c >= N - 1 || !TASER_IN(rr * N + c, N * N)) continue;
             Lo[(int64_t)rr * N + c] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
+            TASER_FINITE(Lo[(int64_t)rr * N + c]);
           }
-      for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+      for (int rr = lane; rr < N; rr += 32)
+        if (TASER_IN(rr * N + N - 1, N * N)) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
     }
     if constexpr (MON) {   // f(L~(t_max)): one more gradient step, after the outputs
       float fterm = 0.f;
@@ -672,3 +685,5 @@ cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(detect_tc)

@@ -103,9 +103,11 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
   for (int s = 0; s < S; ++s) {
     const int c = lane + 1 + 32 * s;
 #pragma unroll
-    for (int r = 0; r < NP; ++r) col[s][r] = (r < N && c < N) ? T[(int64_t)r * N + c] : 0.f;
+    for (int r = 0; r < NP; ++r)
+      col[s][r] = (r < N && c < N && TASER_IN(inst * N * N + r * N + c, batch * N * N)) ? T[(int64_t)r * N + c]
+                                                                                        : 0.f;
   }
-  float d0 = T[0];
+  float d0 = TASER_IN(inst * N * N, batch * N * N) ? T[0] : 0.f;
   float amax = fabsf(d0);
 #pragma unroll
   for (int s = 0; s < S; ++s)
@@ -172,8 +174,8 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
         const int c = lane + 1 + 32 * s;
         const bool live = c > k && c <= NV;
         vi[s] = live ? (c == k + 1 ? ck[s] - ah : ck[s]) : 0.f;
-        if (c <= NV) xb[c] = vi[s];
-        if (c == k) db[k] = ck[s];
+        if (c <= NV && TASER_IN(c, VB)) xb[c] = vi[s];
+        if (c == k && TASER_IN(k, VB)) db[k] = ck[s];
       }
       __syncwarp();
       float x[VB];
@@ -201,9 +203,9 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
       for (int s = 0; s < S; ++s) {
         const int c = lane + 1 + 32 * s;
         w[s] = fmaf(-kk, vi[s], p[s]);
-        if (c <= NV) wb[c] = w[s];
+        if (c <= NV && TASER_IN(c, VB)) wb[c] = w[s];
       }
-      if (lane == 0) eb[k] = ah;
+      if (lane == 0 && TASER_IN(k, VB)) eb[k] = ah;
       __syncwarp();
       float wv[VB];
 #pragma unroll
@@ -274,9 +276,10 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
   float nrm = 0.5f * (lo + hi);
   if (two) nrm = fmaxf(nrm, __shfl_xor_sync(TASER_FULL_MASK, nrm, 16));
   nrm *= pow2f(ex);
-  if (lane == 0) {
+  if (lane == 0 && TASER_IN(inst, batch)) {
     tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
     if (nrm_out != nullptr) nrm_out[inst] = nrm;
+    TASER_FINITE(nrm);
   }
 }
 
@@ -346,7 +349,7 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
     // NEG reads the negative semidefinite JED form as its (positive semidefinite) negation;
     // the norm is the same.
     auto t = [&](int a, int b) -> float {
-      const float v = active ? T[a * N + b] : 0.f;
+      const float v = active && TASER_IN(inst * N * N + a * N + b, batch * N * N) ? T[a * N + b] : 0.f;
       return NEG ? -v : v;
     };
     const bool cu = c < UV && c < Uc, ca = c == UV;
@@ -417,8 +420,8 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
       const float beta = refl ? __fdividef(2.f, vv2) : 0.f;
       // Publish v (zero for rows <= k) as duplicated pairs.
       const float2 vc = live ? (c == k + 1 ? v1 : xc) : make_float2(0.f, 0.f);
-      xd[c] = make_float4(vc.x, vc.x, vc.y, vc.y);
-      if (c == k) db[k] = ck.x;
+      if (TASER_IN(c, VB)) xd[c] = make_float4(vc.x, vc.x, vc.y, vc.y);
+      if (c == k && TASER_IN(k, VB)) db[k] = ck.x;
       __syncwarp();
       // p_c = beta sum_j conj(M[j][c]) v_j in one pass over j:
       //   A = sum {Re M, Im M} {Re v, Re v},  Bs = sum {Re M, Im M} {Im v, Im v},
@@ -441,8 +444,8 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
       for (int o = G / 2; o > 0; o >>= 1) kk += __shfl_xor_sync(TASER_FULL_MASK, kk, o);
       kk *= 0.5f * beta;
       const float2 w = make_float2(fmaf(-kk, vc.x, p.x), fmaf(-kk, vc.y, p.y));
-      wd[c] = make_float4(w.x, w.x, w.y, w.y);
-      if (c == k + 1) eb2[k] = sig2;                               // |alpha|^2
+      if (TASER_IN(c, VB)) wd[c] = make_float4(w.x, w.x, w.y, w.y);
+      if (c == k + 1 && TASER_IN(k, VB)) eb2[k] = sig2;                               // |alpha|^2
       __syncwarp();
       // M[j][c] -= v_j conj(w_c) + w_j conj(v_c), as four pair FMAs per row:
       //   v conj(w) = {Re v, Re v}{Re w, -Im w} + {Im v, Im v}{Im w, Re w}.
@@ -502,9 +505,10 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
     }
   }
   const float nrm = 0.5f * (lo + hi) * pow2f(ex);
-  if (active && gl == 0) {
+  if (active && gl == 0 && TASER_IN(inst, batch)) {
     tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
     if (nrm_out != nullptr) nrm_out[inst] = nrm;
+    TASER_FINITE(nrm);
   }
 }
 
@@ -546,3 +550,5 @@ cudaError_t spectral(int64_t batch, int N, const float* Tt, float alpha, int hin
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(spectral)

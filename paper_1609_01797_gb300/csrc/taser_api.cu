@@ -494,3 +494,46 @@ taser_status taser_detect_uneven(int64_t n_items, const taser_item* items, const
 }
 
 }  // extern "C"
+
+#ifdef TASER_DEBUG
+namespace taser {
+namespace dbg {
+// Counter collectors of the translation units that hold kernels (TASER_DEBUG_COLLECTOR).
+cudaError_t take_build_T(unsigned long long* out);
+cudaError_t take_spectral(unsigned long long* out);
+cudaError_t take_detect_fp32(unsigned long long* out);
+cudaError_t take_detect_tc(unsigned long long* out);
+cudaError_t take_detect_tc64(unsigned long long* out);
+cudaError_t take_detect_fx14(unsigned long long* out);
+cudaError_t take_unfolded(unsigned long long* out);
+cudaError_t take_unfolded_tc(unsigned long long* out);
+cudaError_t take_uneven(unsigned long long* out);
+}  // namespace dbg
+}  // namespace taser
+#endif
+
+extern "C" {
+
+taser_status taser_debug_report(uint64_t* fails, uint64_t* first, uint64_t* nonfinite) {
+  TASER_REQUIRE(fails != nullptr && first != nullptr && nonfinite != nullptr,
+                "fails, first and nonfinite must not be NULL");
+#ifdef TASER_DEBUG
+  using namespace taser::dbg;
+  cudaError_t (*const takes[])(unsigned long long*) = {take_build_T,     take_spectral, take_detect_fp32,
+                                                        take_detect_tc,   take_detect_tc64, take_detect_fx14,
+                                                        take_unfolded,    take_unfolded_tc, take_uneven};
+  unsigned long long acc[3] = {0ull, 0ull, 0ull};
+  for (auto take : takes) {
+    const cudaError_t e = take(acc);
+    if (e != cudaSuccess) return from_cuda(e, "debug counters");
+  }
+  *fails = acc[0];
+  *first = acc[1];
+  *nonfinite = acc[2];
+  return ok();
+#else
+  return fail(TASER_ERR_UNSUPPORTED, "release build: the debug counters exist in libtaser_debug.so only");
+#endif
+}
+
+}  // extern "C"

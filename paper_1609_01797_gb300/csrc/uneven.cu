@@ -33,8 +33,11 @@ __device__ __forceinline__ int bucket_index(int N) {
 __device__ __forceinline__ int item_key(const taser_item& it) {
   return bucket_index(it.N) * kClasses + (kClasses - min(it.t_max, kClasses));
 }
+// The bounds-checked debug build also rejects (and counts) negative pool offsets; the
+// release build takes the offsets as given.
 __device__ __forceinline__ bool item_ok(const taser_item& it) {
-  return it.N >= 2 && it.N <= TASER_MAX_N && it.t_max >= 1;
+  return it.N >= 2 && it.N <= TASER_MAX_N && it.t_max >= 1 && TASER_IN(it.t_off, INT64_MAX) &&
+         TASER_IN(it.d_off, INT64_MAX) && TASER_IN(it.s_off, INT64_MAX) && TASER_IN(it.l_off + 1, INT64_MAX);
 }
 
 constexpr int kSortThreads = 256;
@@ -49,8 +52,11 @@ bucket_hist_kernel(int n, const taser_item* __restrict__ items, int* __restrict_
   const int i0 = blockIdx.x * kSortItemsPerBlock, i1 = min(n, i0 + kSortItemsPerBlock);
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const taser_item it = items[i];
-    if (item_ok(it)) atomicAdd(&hist[item_key(it)], 1);
-    else if (flags != nullptr) flags[i] |= TASER_FLAG_BAD_ITEM;
+    if (item_ok(it)) {
+      if (TASER_IN(item_key(it), kKeys)) atomicAdd(&hist[item_key(it)], 1);
+    } else if (flags != nullptr) {
+      flags[i] |= TASER_FLAG_BAD_ITEM;
+    }
   }
   __syncthreads();
   for (int k = threadIdx.x; k < kKeys; k += blockDim.x)
@@ -90,7 +96,7 @@ bucket_scatter_kernel(int n, const taser_item* __restrict__ items, int* __restri
   const int i0 = blockIdx.x * kSortItemsPerBlock, i1 = min(n, i0 + kSortItemsPerBlock);
   for (int i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
     const taser_item it = items[i];
-    if (item_ok(it)) atomicAdd(&hist[item_key(it)], 1);
+    if (item_ok(it) && TASER_IN(item_key(it), kKeys)) atomicAdd(&hist[item_key(it)], 1);
   }
   __syncthreads();
   for (int k = threadIdx.x; k < kKeys; k += blockDim.x) {
@@ -102,7 +108,9 @@ bucket_scatter_kernel(int n, const taser_item* __restrict__ items, int* __restri
     const taser_item it = items[i];
     if (item_ok(it)) {
       const int key = item_key(it);
-      list[base[key] + atomicAdd(&hist[key], 1)] = i;
+      if (!TASER_IN(key, kKeys)) continue;
+      const int at = base[key] + atomicAdd(&hist[key], 1);
+      if (TASER_IN(at, n)) list[at] = i;
     }
   }
 }
@@ -190,6 +198,7 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
     q.list = list;
     q.meta = meta;
     q.b = b;
+    q.n = n_items;
     const int bps = tuning != nullptr ? tuning->blocks_per_sm[b] : 0;
     const bool tc = precision != TASER_FP32 && precision != TASER_FIXED14 && nb >= 16;
     // Default items per pop (measured on the 200,000-item batch): the short tensor-core
@@ -218,3 +227,5 @@ cudaError_t detect_uneven(int64_t n_items, const taser_item* items, const float*
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(uneven)

@@ -100,7 +100,7 @@ __device__ __forceinline__ void load_tcol(TPairs<NB>& tcol, const float* T, int 
     for (int h = 0; h < 2; ++h) {
       const int k = 2 * p + h;
       const int kr = k <= NB ? bucket_to_real(k, N, NB) : -1;
-      v[h] = (jr >= 0 && kr >= 0) ? T[(int64_t)kr * N + jr] : 0.f;
+      v[h] = (jr >= 0 && kr >= 0 && TASER_IN(kr * N + jr, N * N)) ? T[(int64_t)kr * N + jr] : 0.f;
     }
     tcol.v[p] = f2pack(v[0], v[1]);
   }
@@ -132,7 +132,7 @@ unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, cons
   const float* T = Tt + inst * (int64_t)N * N;
   TPairs<NB> tcol;
   load_tcol<NB>(tcol, T, N, jr);
-  const float Dj = jr >= 0 ? Dg[inst * N + jr] : 0.f;
+  const float Dj = jr >= 0 && TASER_IN(inst * N + jr, batch * N) ? Dg[inst * N + jr] : 0.f;
   const float DN = Dg[inst * N + N - 1];
   const float inv = inv_norm[inst];
   const int n_ckpt = (t_max + c - 1) / c;
@@ -152,21 +152,24 @@ unfolded_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, cons
       int r = lane / N, cc = lane % N;                 // (r, cc) of element e, advanced by 32
       for (int e = lane; e < N * N; e += 32) {
         const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
-        out[e] = bc <= br ? cur[tri_off(br) + bc] : 0.f;
+        if (TASER_IN((inst * n_ckpt + t / c) * N * N + e, batch * n_ckpt * N * N) &&
+            TASER_IN(tri_off(br) + (bc <= br ? bc : 0), C::MAT))
+          out[e] = bc <= br ? cur[tri_off(br) + bc] : 0.f;
         r += dq;
         cc += dm;
         if (cc >= N) { cc -= N; ++r; }
       }
     }
-    const float tau = alpha_t[t] * inv;
+    const float tau = TASER_IN(t, t_max) ? alpha_t[t] * inv : 0.f;
     if (j < NB) forward_step<NB>(cur, nxt, l, tcol, tau, Dj, j);
     __syncwarp();
     float* tmp = cur;
     cur = nxt;
     nxt = tmp;
   }
-  if (jr >= 0) {
+  if (jr >= 0 && TASER_IN(inst * (N - 1) + jr, batch * (N - 1))) {
     soft[inst * (N - 1) + jr] = Dj > 0.f ? l[NB] / Dj : 0.f;
+    TASER_FINITE(soft[inst * (N - 1) + jr]);
     if (s_hat != nullptr) s_hat[inst * (N - 1) + jr] = l[NB] >= 0.f ? int8_t(1) : int8_t(-1);
   }
 }
@@ -190,7 +193,7 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
   const float* T = Tt + inst * (int64_t)N * N;
   TPairs<NB> tcol;
   load_tcol<NB>(tcol, T, N, jr);
-  const float Dj = jr >= 0 ? Dg[inst * N + jr] : 0.f;
+  const float Dj = jr >= 0 && TASER_IN(inst * N + jr, batch * N) ? Dg[inst * N + jr] : 0.f;
   const float inv = inv_norm[inst];
   // The rows of Vbar are written on and below the diagonal only: zero the padding once.
   for (int idx = lane; idx < C::MAT; idx += 32) vb[idx] = 0.f;
@@ -200,7 +203,8 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
   float lbar[NB + 1];
 #pragma unroll
   for (int i = 0; i <= NB; ++i) lbar[i] = 0.f;
-  if (jr >= 0 && Dj > 0.f) lbar[NB] = grad_soft[inst * (N - 1) + jr] / Dj;
+  if (jr >= 0 && Dj > 0.f && TASER_IN(inst * (N - 1) + jr, batch * (N - 1)))
+    lbar[NB] = grad_soft[inst * (N - 1) + jr] / Dj;
 
   for (int kc = n_ckpt - 1; kc >= 0; --kc) {
     const int t0 = kc * c, t1 = min(t0 + c, t_max);
@@ -214,7 +218,9 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
       int r = lane / N, cc = lane % N;                 // (r, cc) of element e, advanced by 32
       for (int e = lane; e < N * N; e += 32) {
         const int br = r == N - 1 ? NB : r, bc = cc == N - 1 ? NB : cc;
-        if (bc <= br) uf_cp_async4(seg + tri_off(br) + bc, in + e);
+        if (bc <= br && TASER_IN(tri_off(br) + bc, C::MAT) &&
+            TASER_IN((inst * n_ckpt + kc) * N * N + e, batch * n_ckpt * N * N))
+          uf_cp_async4(seg + tri_off(br) + bc, in + e);
         r += dq;
         cc += dm;
         if (cc >= N) { cc -= N; ++r; }
@@ -226,7 +232,7 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
     float l[NB + 1];
     for (int s = t0 + 1; s < t1; ++s) {
       float* Lin = seg + (s - 1 - t0) * C::MAT;
-      float* Lout = seg + (s - t0) * C::MAT;
+      float* Lout = seg + (TASER_IN(s - t0, c + 1) ? s - t0 : 0) * C::MAT;
       for (int idx = lane; idx < C::MAT; idx += 32) Lout[idx] = Lin[idx];  // zeros and L~_NN
       __syncwarp();
       if (j < NB) forward_step<NB>(Lin, Lout, l, tcol, alpha_t[s - 1] * inv, Dj, j);
@@ -259,7 +265,10 @@ unfolded_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, con
 #pragma unroll
       for (int i = 0; i <= NB; ++i) lbar[i] = (i >= j) ? f * fmaf(-v[i] * rn, proj, lbar[i]) : 0.f;
       const float tb = -warp_sum(f * fmaf(-rn * proj, gv, gl));
-      if (lane == 0) grad_tau[inst * t_max + (s - 1)] = tb;
+      if (lane == 0 && TASER_IN(inst * t_max + (s - 1), batch * t_max)) {
+        grad_tau[inst * t_max + (s - 1)] = tb;
+        TASER_FINITE(tb);
+      }
       // Lbar(s-1) = tril(Vbar - tau Vbar (2 T~)): rows of Vbar through shared memory
 #pragma unroll
       for (int i = 0; i <= NB; ++i)
@@ -364,3 +373,5 @@ cudaError_t unfolded(bool backward, int precision, int64_t batch, int N, const f
 }
 
 }  // namespace taser
+
+TASER_DEBUG_COLLECTOR(unfolded)

@@ -138,3 +138,25 @@ def test_unfolded_rejects_fixed_point_and_unknown_precision(lib):
     b = lambda prec, c: lib.taser_unfolded_backward(1, 33, P16, P16, P16, P16, 100, c, prec, P16, P16, P16, None, None)
     assert b(1, 45) == 1 and b"shared memory" in lib.taser_last_error()     # tensor cores: c <= 44
     assert b(0, 93) == 1 and b"shared memory" in lib.taser_last_error()     # FP32: c <= 92
+
+
+def test_debug_library_exports_the_same_symbols():
+    from paper_1609_01797_gb300 import build as B
+    if not os.path.exists(B.LIB_DEBUG):
+        B.build(debug=True)
+    dbg = ctypes.CDLL(B.LIB_DEBUG)
+    for name in _declared_functions():
+        assert hasattr(dbg, name), name
+    out = [ctypes.c_uint64(7) for _ in range(3)]
+    dbg.taser_debug_report.restype = ctypes.c_int
+    # NULL outputs are rejected before any CUDA call
+    assert dbg.taser_debug_report(None, ctypes.byref(out[1]), ctypes.byref(out[2])) == 1
+    assert [o.value for o in out] == [7, 7, 7]
+
+
+def test_debug_report_is_unsupported_in_the_release_library(lib):
+    out = [ctypes.c_uint64(7) for _ in range(3)]
+    assert lib.taser_debug_report(*[ctypes.byref(o) for o in out]) == 2   # TASER_ERR_UNSUPPORTED
+    assert [o.value for o in out] == [7, 7, 7]
+    assert b"libtaser_debug.so" in lib.taser_last_error()
+    assert lib.taser_debug_report(None, None, None) == 1                   # TASER_ERR_INVALID_ARG
