@@ -90,6 +90,8 @@ typedef enum {
 #define TASER_FLAG_BAD_ITEM    (1u << 4) /* uneven batch: item with N or t_max out of range */
 #define TASER_FLAG_SATURATED   (1u << 5) /* TASER_FIXED14: a value saturated to 14 bits    */
 #define TASER_FLAG_ASCENT      (1u << 6) /* taser_detect_monitored: the objective rose      */
+#define TASER_FLAG_TIMEOUT     (1u << 7) /* a bounded device wait expired: outputs of the
+                                            instance are not written                       */
 
 /* Largest N supported by the detection kernels. */
 #define TASER_MAX_N 65
@@ -390,6 +392,17 @@ taser_status taser_run_host_static(int kind, int64_t batch, int B, int U_or_K,
  * (libtaser.so) returns TASER_ERR_UNSUPPORTED and leaves the outputs unchanged.
  */
 taser_status taser_debug_report(uint64_t* fails, uint64_t* first, uint64_t* nonfinite);
+
+/*
+ * taser_debug_drop_copy -- fault injection of the bounds-checked debug build (the paper has
+ * no counterpart).  Later taser_build_T calls that stage by TMA (QPSK with 16 users, B
+ * even) withhold the staging copy of 16-antenna chunk `chunk` of instance `instance`, so
+ * the bounded wait for it (about a second of SM clock) expires.  That instance then gets
+ * TASER_FLAG_TIMEOUT and its T~ and D are left unwritten; the other instances are not
+ * affected.  Nothing faults, because the copy is never issued.  instance < 0 turns the
+ * injection off.  The release library returns TASER_ERR_UNSUPPORTED.
+ */
+taser_status taser_debug_drop_copy(int64_t instance, int chunk);
 
 #ifdef __cplusplus
 }

@@ -7,4 +7,4 @@ from .api import (BPSK, GENERIC, JED_BPSK, QPSK, PRECISIONS, FLAG_ASCENT, build_
                   problem_size,
                   step_size, host_workspace_bytes, run_host, run_host_static,
                   unfolded_forward, unfolded_backward, UnfoldedTASER, ITEM_DTYPE, make_items,
-                  uneven_workspace_bytes, tuning, detect_uneven, debug_report)
+                  uneven_workspace_bytes, tuning, detect_uneven, debug_report, debug_drop_copy)

@@ -37,6 +37,7 @@ SIGNATURES = {
     "taser_detect_uneven": (_c_i32, [_c_i64, _vp, _vp, _vp, _vp, _c_i32, _c_i32, _vp, _vp, _vp, _vp, ctypes.c_size_t,
                                      _vp, _vp]),
     "taser_debug_report": (_c_i32, [_vp, _vp, _vp]),
+    "taser_debug_drop_copy": (_c_i32, [_c_i64, _c_i32]),
 }
 
 

@@ -264,3 +264,9 @@ def debug_report():
         f = first.value
         rec = {"source": source_of(f >> 56), "line": (f >> 32) & 0xffffff, "index": f & 0xffffffff}
     return {"fails": fails.value, "nonfinite": nonfinite.value, "first": rec}
+
+
+def debug_drop_copy(instance, chunk):
+    """Debug library only: later TMA-staged build_T calls withhold the staging copy of
+    16-antenna chunk `chunk` of `instance` (instance < 0: off); see taser_debug_drop_copy."""
+    check(lib().taser_debug_drop_copy(int(instance), int(chunk)), "taser_debug_drop_copy")

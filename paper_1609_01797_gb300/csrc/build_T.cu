@@ -21,6 +21,7 @@
 //
 // Mapping: one warp per instance.  X is staged into shared memory through a cp.async ring
 // of antenna-row chunks; only the upper-triangular 16 x 8 tiles of G' are computed.
+#include <cuda.h>
 #include <cuda_fp16.h>
 
 #include "common.cuh"
@@ -114,25 +115,109 @@ struct CInt {
 // 2^e as a float for -126 <= e <= 127.
 __device__ __forceinline__ float pow2i(int e) { return __uint_as_float((uint32_t)(e + 127) << 23); }
 
+// Staging by the tensor memory accelerator (TMA).  QPSK problems that fill the column
+// bucket (16 users: 17 complex columns with y) stage their antenna rows with
+// cp.async.bulk.tensor instead of per-lane cp.async.  H is a 3-D tensor (32 floats per
+// antenna row, B rows, batch instances) read in boxes of 16 rows with the 128-byte swizzle;
+// rows past B read as zero.  y is a 2-D tensor (2B floats per instance) read in boxes of 32
+// floats.  One lane per warp arms a stage's mbarrier with the expected bytes and issues both
+// copies; every lane waits on the barrier's phase.  Each wait is bounded by a clock64
+// budget.  An expired wait marks the instance TASER_FLAG_TIMEOUT, waits (bounded again) for
+// the warp's other copies in flight and leaves that instance's T~ and D unwritten.
+struct TmaCfg {
+  static constexpr int NS = 4;                        // stages in the ring
+  static constexpr int H_FLOATS = 16 * 32;            // one H box: 16 rows of 128 bytes
+  static constexpr int Y_FLOATS = 32;                 // one y box: 16 complex values
+  static constexpr unsigned TX_BYTES = (H_FLOATS + Y_FLOATS) * 4;
+  static constexpr int WARP_FLOATS = 2304;            // NS (H + y) = 2,176 floats, in 1 KB units
+  static constexpr int WARPS = 4;
+  // Per block: the warps' rings, their mbarriers and 1 KB of slack to align the rings.
+  static constexpr int SMEM_BYTES = WARPS * WARP_FLOATS * 4 + WARPS * NS * 8 + 1024;
+};
+static_assert(TmaCfg::NS * (TmaCfg::H_FLOATS + TmaCfg::Y_FLOATS) <= TmaCfg::WARP_FLOATS, "ring must fit");
+static_assert((TmaCfg::WARP_FLOATS * 4) % 1024 == 0, "swizzled boxes need 1 KB alignment");
+static_assert(33 * 33 + 144 <= TmaCfg::WARP_FLOATS, "epilogue scratch must fit the ring");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+// Arrives once and adds `tx` bytes to the phase's expected transaction count.
+__device__ __forceinline__ void mbar_arm(uint32_t bar, unsigned tx) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(tx) : "memory");
+}
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Waits for the completion of the phase with the given parity; false once `budget` clock
+// cycles have passed without it.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (clock64() - t0 > budget) return false;
+  }
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int z,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(dst),
+      "l"(map), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+#ifdef TASER_DEBUG
+// Debug build only: the staging copy of chunk g_drop_chunk of instance g_drop_inst is
+// withheld, so that its bounded wait expires (the timeout path under test).
+static __device__ long long g_drop_inst = -1;
+static __device__ int g_drop_chunk = -1;
+#endif
+
 // KIND >= 0 compiles the epilogue for that problem kind; -1 takes it from kind_rt.
-template <int MP, int KIND>
+// TMA: staging by the tensor memory accelerator (MP = 17, QPSK only; see TmaCfg).
+template <int MP, int KIND, bool TMA = false>
 __global__ void __launch_bounds__(128, MP == 17 ? 5 : 1)
 build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __restrict__ X,
                const float2* __restrict__ yv, float* __restrict__ Tt, float* __restrict__ Dout,
-               uint32_t* __restrict__ flags) {
+               uint32_t* __restrict__ flags, const __grid_constant__ CUtensorMap tmH,
+               const __grid_constant__ CUtensorMap tmY, long long wait_budget) {
   using C = BuildCfg<MP>;
   constexpr int NT = C::NT, MT = C::MT, WS = C::WS, CH = C::CH;
+  constexpr int WFL = TMA ? TmaCfg::WARP_FLOATS : C::WARP_FLOATS;   // floats per warp
+  static_assert(!TMA || (MP == 17 && KIND == TASER_MIMO_QPSK), "TMA staging serves the 17-column QPSK Gram");
   const int kind = KIND >= 0 ? KIND : kind_rt;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
   const int64_t inst = (int64_t)blockIdx.x * C::WARPS + warp;
   if (inst >= batch) return;
-  float* Ws = smem + warp * C::WARP_FLOATS;
+  float* sbase = smem;
+  if constexpr (TMA) {   // swizzled boxes start on 1 KB boundaries
+    const uint32_t a = smem_u32(smem);
+    sbase = smem + ((((a + 1023u) & ~1023u) - a) >> 2);
+  }
+  float* Ws = sbase + warp * WFL;
 
-  // Padding columns (2P .. 2MP-3 and >= 2MP) stay zero for the whole Gram phase.
-  for (int i = lane; i < C::WARP_FLOATS / 4; i += 32) reinterpret_cast<float4*>(Ws)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  __syncwarp();
+  if constexpr (!TMA) {
+    // Padding columns (2P .. 2MP-3 and >= 2MP) stay zero for the whole Gram phase.
+    for (int i = lane; i < C::WARP_FLOATS / 4; i += 32)
+      reinterpret_cast<float4*>(Ws)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    __syncwarp();
+  }
   const bool jed = kind == TASER_SIMO_JED_BPSK || kind == TASER_SIMO_JED_QPSK;
   const int src_cols = jed ? P + 1 : P;                 // complex columns per antenna row
   const float2* Xi = X + inst * (int64_t)B * src_cols;
@@ -149,7 +234,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
     const int rows = min(CH, B - r0);
     if (crow < rows_per_iter) {
       for (int r = crow; r < rows; r += rows_per_iter) {
-        const int64_t xe = (inst * B + r0 + r) * src_cols;   // complex element of the row in X
+        [[maybe_unused]] const int64_t xe = (inst * B + r0 + r) * src_cols;   // element of the row in X
         const float2* src = Xi + (int64_t)(r0 + r) * src_cols;
         if (pairs) {
           if (TASER_IN(r * WS + 4 * cu + 3, C::BUF_FLOATS) && TASER_IN(xe + 2 * cu + 1, batch * B * src_cols))
@@ -163,7 +248,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
     }
     for (int r = lane; r < rows; r += 32) {
       const float2* src = jed ? Xi + (int64_t)(r0 + r) * src_cols : yi + (r0 + r);
-      const int64_t se = jed ? (inst * B + r0 + r) * src_cols : inst * B + r0 + r;
+      [[maybe_unused]] const int64_t se = jed ? (inst * B + r0 + r) * src_cols : inst * B + r0 + r;
       if (TASER_IN(r * WS + 2 * (MP - 1) + 1, C::BUF_FLOATS) && TASER_IN(se, batch * B * (jed ? src_cols : 1)))
         cp_async8(buf + r * WS + 2 * (MP - 1), src);
     }
@@ -176,7 +261,175 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   int exq[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) exq[j] = 0;
-  if constexpr (C::F16) {
+  if constexpr (TMA) {
+    // The FP16-split Gram of the branch below (same scales, restart and tiles), staged by
+    // TMA.  A 16-row step pairs rows (2tq, 2tq + 1) and (2tq + 8, 2tq + 9) as its k-indices;
+    // under the 128-byte swizzle, row r's float c lives at r 32 + ((c / 4) ^ (r mod 8)) 4 +
+    // c mod 4, and these rows put the 32 lanes of every fragment load in 32 banks.
+    using TC = TmaCfg;
+    float* const Hs = Ws;                          // NS boxes of 16 x 32 floats (swizzled)
+    float* const Ys = Ws + TC::NS * TC::H_FLOATS;  // NS boxes of 32 floats
+    uint64_t* const bars = reinterpret_cast<uint64_t*>(sbase + TC::WARPS * TC::WARP_FLOATS) + warp * TC::NS;
+    if (lane == 0) {
+      for (int st = 0; st < TC::NS; ++st) mbar_init(smem_u32(bars + st), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    // Chunks are numbered across restarts: chunk sequence q sits in stage q mod NS, and its
+    // barrier phase has parity (q / NS) mod 2.
+    unsigned q_issued = 0;
+    auto issue = [&](int chunk) {   // called by every lane; lane 0 arms and copies
+      const unsigned q = q_issued++;
+      if (lane != 0) return;
+#ifdef TASER_DEBUG
+      if (inst == g_drop_inst && chunk == g_drop_chunk) return;   // withheld (timeout test)
+#endif
+      const int st = (int)(q % TC::NS);
+      const uint32_t bar = smem_u32(bars + st);
+      mbar_arm(bar, TC::TX_BYTES);
+      tma_load_3d(smem_u32(Hs + st * TC::H_FLOATS), &tmH, 0, chunk * 16, (int)inst, bar);
+      tma_load_2d(smem_u32(Ys + st * TC::Y_FLOATS), &tmY, chunk * 32, (int)inst, bar);
+    };
+    auto arrived = [&](unsigned q) -> bool {
+      const bool ok = mbar_wait(smem_u32(bars + q % TC::NS), (q / TC::NS) & 1u, wait_budget);
+      return __all_sync(TASER_FULL_MASK, ok);
+    };
+    // Per-lane parts of the swizzled addresses: row 2tq (+8) and row 2tq + 1 (+9) of column
+    // 8j + g are at base0 / base1 + 8 (j ^ tq) (+ 256).
+    const int gb = g >> 2, gi = g & 3;
+    const int base0 = 64 * tq + 4 * gb + gi, base1 = 64 * tq + 32 + 4 * (gb ^ 1) + gi, t8 = 8 * tq;
+    const bool ylane = g < 2;                      // n-tile 4: column 32 + g is y (re, im) for g < 2
+    int ex[NT];
+    float sc[NT];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) ex[j] = 0;
+    bool timed_out = false;
+    unsigned q_fail = 0;
+    for (int attempt = 0; attempt < 16 && !timed_out; ++attempt) {
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+      const unsigned q0 = q_issued;
+#pragma unroll
+      for (int st = 0; st < TC::NS - 1; ++st)
+        if (st < nchunks) issue(st);
+      for (int chunk = 0; chunk < nchunks; ++chunk) {
+        const unsigned q = q0 + chunk;
+        if (!arrived(q)) {
+          timed_out = true;
+          q_fail = q;
+          break;
+        }
+        if (attempt == 0 && chunk == 0) {
+          // Column maxima over the first 32 antenna rows (chunks 0 and 1; rows past B read
+          // as zero), then over tq and over the re / im pair of a complex column.
+          if (nchunks > 1 && !arrived(q + 1)) {
+            timed_out = true;
+            q_fail = q + 1;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            float m = 0.f;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+              if (h == 1 && nchunks < 2) continue;
+              const float* hb = Hs + ((q + h) % TC::NS) * TC::H_FLOATS;
+              const float* yb = Ys + ((q + h) % TC::NS) * TC::Y_FLOATS;
+              if (j < 4) {
+                const int x = (8 * j) ^ t8;
+                m = fmaxf(m, fmaxf(fmaxf(fabsf(hb[base0 + x]), fabsf(hb[base1 + x])),
+                                   fmaxf(fabsf(hb[base0 + x + 256]), fabsf(hb[base1 + x + 256]))));
+              } else if (ylane) {
+                m = fmaxf(m, fmaxf(fmaxf(fabsf(yb[4 * tq + g]), fabsf(yb[4 * tq + 2 + g])),
+                                   fmaxf(fabsf(yb[4 * tq + 16 + g]), fabsf(yb[4 * tq + 18 + g]))));
+              }
+            }
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 2));
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 4));   // re and im of one column
+            const int e2 = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;
+            ex[j] = (m > 0.f && e2 > -127) ? min(max(6 - e2, -100), 100) : 0;
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NT; ++j) sc[j] = pow2i(ex[j]);
+        // Chunk c + NS - 1 goes into the stage of chunk c - 1, which every lane has read.
+        if (chunk + TC::NS - 1 < nchunks) issue(chunk + TC::NS - 1);
+        const float* hb = Hs + (q % TC::NS) * TC::H_FLOATS;
+        const float* yb = Ys + (q % TC::NS) * TC::Y_FLOATS;
+        uint32_t bh[NT][2], bl[NT][2];
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          const uint64_t sc2 = f2pack(sc[j], sc[j]);
+          float x0, x1, x2, x3;
+          if (j < 4) {
+            const int x = (8 * j) ^ t8;
+            x0 = hb[base0 + x];
+            x1 = hb[base1 + x];
+            x2 = hb[base0 + x + 256];
+            x3 = hb[base1 + x + 256];
+          } else {
+            x0 = ylane ? yb[4 * tq + g] : 0.f;
+            x1 = ylane ? yb[4 * tq + 2 + g] : 0.f;
+            x2 = ylane ? yb[4 * tq + 16 + g] : 0.f;
+            x3 = ylane ? yb[4 * tq + 18 + g] : 0.f;
+          }
+          split_f16(x0, x1, sc2, bh[j][0], bl[j][0]);
+          split_f16(x2, x3, sc2, bh[j][1], bl[j][1]);
+        }
+#pragma unroll
+        for (int i = 0; i < MT; ++i) {
+          // A = W^T: rows 16i + g (+8) are n-tiles 2i and 2i+1 of the same loads.
+          const int j0 = 2 * i, j1 = 2 * i + 1;
+          uint32_t ah[4], al[4];
+          ah[0] = bh[j0][0];
+          ah[2] = bh[j0][1];
+          al[0] = bl[j0][0];
+          al[2] = bl[j0][1];
+          if (j1 < NT) {
+            ah[1] = bh[j1][0];
+            ah[3] = bh[j1][1];
+            al[1] = bl[j1][0];
+            al[3] = bl[j1][1];
+          } else {
+            ah[1] = ah[3] = al[1] = al[3] = 0u;
+          }
+#pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            if (!C::tile(i, j)) continue;
+            mma_f16(acc[i][j], ah, bh[j][0], bh[j][1]);
+            mma_f16(acc[i][j], ah, bl[j][0], bl[j][1]);
+            mma_f16(acc[i][j], al, bh[j][0], bh[j][1]);
+          }
+        }
+        __syncwarp();  // every lane has read this stage before it is refilled
+      }
+      if (timed_out) break;
+      bool finite = true;
+#pragma unroll
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) finite = finite && isfinite(acc[i][j][e]);
+      if (__all_sync(TASER_FULL_MASK, finite)) break;   // no FP16 overflow (non-finite input retries)
+#pragma unroll
+      for (int j = 0; j < NT; ++j) ex[j] -= 9;
+    }
+    if (timed_out) {
+      // Wait (bounded) for every copy of this warp that may still be in flight, so that
+      // none lands in shared memory after the warp has left; then flag the instance.
+      for (unsigned q = q_fail; q < q_issued; ++q) (void)arrived(q);
+      if (lane == 0 && flags != nullptr && TASER_IN(inst, batch)) flags[inst] = TASER_FLAG_TIMEOUT;
+      return;
+    }
+#pragma unroll
+    for (int j = 0; j < NT; ++j) exq[j] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq));
+  } else if constexpr (C::F16) {
     // Per-column power-of-two scales: this lane's columns 8j + g are multiplied by 2^ex[j]
     // before the FP16 split, chosen from the first 32 antenna rows so that the largest
     // magnitude of the complex column (its real and imaginary parts share one scale) lands in
@@ -384,7 +637,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   // column last.  QPSK user p: real p and U + p; BPSK / JED data column p: real p.
   const bool qpsk = kind == TASER_MIMO_QPSK || kind == TASER_SIMO_JED_QPSK;
   const bool jq = kind == TASER_SIMO_JED_QPSK;
-  float* Dc = Ws + C::WARP_FLOATS - 2 * 72;   // D per complex column
+  float* Dc = Ws + WFL - 2 * 72;              // D per complex column
   float* rDc = Dc + 72;                       // 1 / D per complex column
   float* Ts = Ws;                             // N x N staging of T~ (reuses the buffers)
   __syncwarp();
@@ -520,10 +773,72 @@ static cudaError_t launch_build(int kind, int64_t batch, int B, int P, int N, co
     if (e != cudaSuccess) return e;
   }
   const int64_t blocks = (batch + C::WARPS - 1) / C::WARPS;
+  const CUtensorMap unused{};
   build_T_kernel<MP, KIND><<<(unsigned)blocks, 32 * C::WARPS, C::SMEM_BYTES, st>>>(kind, batch, B, P, N, X, y, Tt,
-                                                                                 D, flags);
+                                                                                 D, flags, unused, unused, 0);
   return cudaGetLastError();
 }
+
+// cuTensorMapEncodeTiled, looked up once through the runtime (no link-time dependency on
+// the driver library).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      f = nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+// Bound on one staging wait of the TMA kernel, in SM clock cycles (about a second).
+constexpr long long kTmaWaitCycles = 1ll << 31;
+
+// QPSK with 16 users through the TMA kernel.  The tensor maps need 16-byte aligned bases
+// (the ABI requires them), byte strides that are multiples of 16 (B even) and 32-bit
+// coordinates.  Returns cudaErrorNotSupported when the problem does not qualify.
+static cudaError_t launch_build_tma(int64_t batch, int B, const float2* X, const float2* y, float* Tt, float* D,
+                                    uint32_t* flags, cudaStream_t st) {
+  const EncodeTiledFn encode = encode_tiled();
+  if (encode == nullptr || B % 2 != 0 || batch > (int64_t)INT32_MAX || (int64_t)B * 16 > (int64_t)INT32_MAX ||
+      (reinterpret_cast<uintptr_t>(X) & 15u) != 0 || (reinterpret_cast<uintptr_t>(y) & 15u) != 0)
+    return cudaErrorNotSupported;
+  CUtensorMap mh, my;
+  const cuuint64_t hdim[3] = {32, (cuuint64_t)B, (cuuint64_t)batch};
+  const cuuint64_t hstride[2] = {128, (cuuint64_t)B * 128};
+  const cuuint32_t hbox[3] = {32, 16, 1}, one[3] = {1, 1, 1};
+  CUresult r = encode(&mh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float2*>(X), hdim, hstride, hbox, one,
+                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const cuuint64_t ydim[2] = {(cuuint64_t)B * 2, (cuuint64_t)batch};
+  const cuuint64_t ystride[1] = {(cuuint64_t)B * 8};
+  const cuuint32_t ybox[2] = {32, 1};
+  r = encode(&my, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2*>(y), ydim, ystride, ybox, one,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  const int64_t blocks = (batch + TmaCfg::WARPS - 1) / TmaCfg::WARPS;
+  build_T_kernel<17, TASER_MIMO_QPSK, true><<<(unsigned)blocks, 32 * TmaCfg::WARPS, TmaCfg::SMEM_BYTES, st>>>(
+      TASER_MIMO_QPSK, batch, B, 16, 33, X, y, Tt, D, flags, mh, my, kTmaWaitCycles);
+  return cudaGetLastError();
+}
+
+#ifdef TASER_DEBUG
+// Debug build: withhold the staging copy of `chunk` of instance `inst` in later TMA launches
+// (inst < 0: none).
+cudaError_t debug_drop_copy(int64_t inst, int chunk) {
+  const long long i = inst;
+  cudaError_t e = cudaMemcpyToSymbol(g_drop_inst, &i, sizeof(i));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_drop_chunk, &chunk, sizeof(chunk));
+  return e;
+}
+#endif
 
 // P = data columns (U for MIMO, K-1 for JED); the augmented column sits at MP-1.
 cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X, const void* y, float* Tt,
@@ -532,6 +847,10 @@ cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X,
   const float2* yc = static_cast<const float2*>(y);
   if (P + 1 <= 9) return launch_build<9, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
   if (P + 1 <= 17) {
+    if (kind == TASER_MIMO_QPSK && P == 16) {
+      const cudaError_t e = launch_build_tma(batch, B, Xc, yc, Tt, D, flags, st);
+      if (e != cudaErrorNotSupported) return e;
+    }
     if (kind == TASER_MIMO_QPSK)
       return launch_build<17, TASER_MIMO_QPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
     return launch_build<17, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);

@@ -509,6 +509,7 @@ cudaError_t take_unfolded(unsigned long long* out);
 cudaError_t take_unfolded_tc(unsigned long long* out);
 cudaError_t take_uneven(unsigned long long* out);
 }  // namespace dbg
+cudaError_t debug_drop_copy(int64_t inst, int chunk);
 }  // namespace taser
 #endif
 
@@ -533,6 +534,17 @@ taser_status taser_debug_report(uint64_t* fails, uint64_t* first, uint64_t* nonf
   return ok();
 #else
   return fail(TASER_ERR_UNSUPPORTED, "release build: the debug counters exist in libtaser_debug.so only");
+#endif
+}
+
+taser_status taser_debug_drop_copy(int64_t instance, int chunk) {
+#ifdef TASER_DEBUG
+  return from_cuda(taser::debug_drop_copy(instance < 0 ? -1 : instance, instance < 0 ? -1 : chunk),
+                   "debug_drop_copy");
+#else
+  (void)instance;
+  (void)chunk;
+  return fail(TASER_ERR_UNSUPPORTED, "release build: fault injection exists in libtaser_debug.so only");
 #endif
 }
 

@@ -64,3 +64,38 @@ def test_negative_item_offset_is_counted_and_skipped(T):
     assert np.array_equal(s[:N - 1], s_dense[0].cpu().numpy())   # the valid item is detected
     assert not s[N - 1:].any()                                     # the invalid one is skipped
     assert T.debug_report()["fails"] == 0                          # reading cleared the counters
+
+
+FLAG_TIMEOUT = 1 << 7
+
+
+def test_withheld_staging_copy_times_out_and_is_flagged(T):
+    """A TMA staging copy that never arrives: the bounded wait expires (about a second), the
+    instance is flagged TASER_FLAG_TIMEOUT and its T~ and D stay unwritten, while the other
+    instances are built as usual.  The copy is withheld, never issued, so nothing faults."""
+    n, B, U = 8, 128, 16
+    w = make_mimo(n, B, U, 8.0, "qpsk", seed=9)
+    H, y = torch.from_numpy(w["H"]).cuda(), torch.from_numpy(w["y"]).cuda()
+    ref = T.build_T("mimo_qpsk", H, y, 0.5)
+    torch.cuda.synchronize()
+    out = {k: torch.full_like(v, 7.0) if v.dtype == torch.float32 else torch.zeros_like(v) for k, v in ref.items()}
+    T.debug_drop_copy(3, 2)
+    try:
+        T.build_T("mimo_qpsk", H, y, 0.5, out=out, with_tau=False)
+        torch.cuda.synchronize()
+    finally:
+        T.debug_drop_copy(-1, 0)
+    fl = out["flags"].cpu().numpy().astype(np.uint32)
+    assert fl[3] == FLAG_TIMEOUT, fl
+    assert (np.delete(fl, 3) == 0).all(), fl
+    Tt, D = out["T_tilde"].cpu().numpy(), out["D"].cpu().numpy()
+    assert (Tt[3] == 7.0).all() and (D[3] == 7.0).all()
+    keep = [i for i in range(n) if i != 3]
+    assert np.array_equal(Tt[keep], ref["T_tilde"].cpu().numpy()[keep])
+    assert np.array_equal(D[keep], ref["D"].cpu().numpy()[keep])
+    # with the injection off the same call builds every instance again
+    T.build_T("mimo_qpsk", H, y, 0.5, out=out, with_tau=False)
+    torch.cuda.synchronize()
+    assert (out["flags"].cpu().numpy() == 0).all()
+    assert np.array_equal(out["T_tilde"].cpu().numpy(), ref["T_tilde"].cpu().numpy())
+    assert T.debug_report()["fails"] == 0

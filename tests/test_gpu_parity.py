@@ -148,7 +148,10 @@ BUILD_CASES = [("mimo_bpsk", 32, 8), ("mimo_bpsk", 7, 3), ("mimo_bpsk", 64, 16),
                ("jed_qpsk", 5, 2), ("jed_qpsk", 40, 9), ("jed_qpsk", 64, 17),
                # 17 complex columns stage 16-row chunks: ragged last chunks (37 = 16 + 16 + 5,
                # 33 = 16 + 16 + 1), fewer than 32 rows for the scale search (20), one partial chunk (9)
-               ("mimo_qpsk", 37, 16), ("mimo_qpsk", 20, 16), ("mimo_qpsk", 9, 10), ("jed_bpsk", 33, 16)]
+               ("mimo_qpsk", 37, 16), ("mimo_qpsk", 20, 16), ("mimo_qpsk", 9, 10), ("jed_bpsk", 33, 16),
+               # QPSK with 16 users and B even is staged by TMA: ragged last boxes (38 = 16 + 16 + 6,
+               # 10), the smallest B (2), one full box (16); odd B (37 above) takes the cp.async path
+               ("mimo_qpsk", 38, 16), ("mimo_qpsk", 10, 16), ("mimo_qpsk", 2, 16), ("mimo_qpsk", 16, 16)]
 
 
 @pytest.mark.parametrize("kind,B,M", BUILD_CASES)
