@@ -925,7 +925,7 @@ def main():
                                 "frac": n / (head["detect_ms"] * 1e-3) / composite},
             "tensor_pipe_active_ncu": pipe_util.get("detect_tc")}),
         "build": (head["build_ms"], {
-            "kernel": "build_T_kernel<17> (FP16 split mma.sync Gram)", "bound": "hbm", "achieved": build_gbs,
+            "kernel": "build_T_kernel<17> (TMA-staged, FP16 split mma.sync Gram)", "bound": "hbm", "achieved": build_gbs,
             "peak": hbm_peak, "unit": "GB/s", "frac": build_gbs / hbm_peak, "traffic": tr("build"),
             "peak_source": peak_src, "algorithmic_bytes_per_launch": n * build_bytes_per_instance(B, U, N),
             "ms_per_launch": head["build_ms"]}),
