@@ -19,8 +19,10 @@
 // on G'), taken from the first 32 antenna rows with 2^8 of headroom; an overflow restarts
 // the instance at a smaller scale.
 //
-// Mapping: one warp per instance.  X is staged into shared memory through a cp.async ring
-// of antenna-row chunks; only the upper-triangular 16 x 8 tiles of G' are computed.
+// Mapping: one warp per instance.  X is staged into shared memory in chunks of antenna rows,
+// by the tensor memory accelerator (cp.async.bulk.tensor into an mbarrier ring) for QPSK with
+// 16 users and an even B, by a per-lane cp.async ring otherwise; only the upper-triangular
+// 16 x 8 tiles of G' are computed.
 #include <cuda.h>
 #include <cuda_fp16.h>
 
