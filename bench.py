@@ -81,11 +81,23 @@ KERNEL_SOURCES = {"build": "build_T.cu", "spectral": "spectral.cu", "detect_tc":
                   "detect_fp32": "detect_fp32.cu", "detect_fx14": "detect_fx14.cu"}
 
 
+def source_sha(path):
+    """sha1 of a kernel source with its // comments and blank lines removed, so that only a
+    change of the code itself marks the counters taken on it as stale (the sources hold no
+    // inside string literals)."""
+    import hashlib
+    lines = []
+    for line in open(path, encoding="utf-8"):
+        code = line.split("//", 1)[0].rstrip()
+        if code:
+            lines.append(code)
+    return hashlib.sha1("\n".join(lines).encode()).hexdigest()
+
+
 def measured_traffic(name="dram_traffic.txt"):
     """Per-kernel figures from a committed ncu summary (DRAM bytes per instance, or the
-    tensor-pipe active fraction), kept only while the kernel's source is unchanged since
-    the counters were taken (sha1 match)."""
-    import hashlib
+    tensor-pipe active fraction), kept only while the kernel's code is unchanged since the
+    counters were taken (source_sha match)."""
     path = os.path.join(ROOT, "profiles", name)
     out = {}
     if not os.path.exists(path):
@@ -96,7 +108,7 @@ def measured_traffic(name="dram_traffic.txt"):
             continue
         key, per_inst, sha = p[0], float(p[1]), p[2]
         src = os.path.join(ROOT, "paper_1609_01797_gb300", "csrc", KERNEL_SOURCES.get(key, ""))
-        if os.path.isfile(src) and hashlib.sha1(open(src, "rb").read()).hexdigest() == sha:
+        if os.path.isfile(src) and source_sha(src) == sha:
             out[key] = per_inst
     return out
 
