@@ -2,19 +2,24 @@
 // tensor cores with BF16 or FP16 operands and FP32 accumulation; the master L~ and the
 // prox (column norms, rescaling) stay in FP32.
 //
-// One warp per instance.  L~ is kept in registers in the accumulator layout of
-// mma.m16n8k16: an accumulator pair of n-tiles (2k, 2k+1) is exactly the A operand of
-// k-tile k, so the next iteration's A operand is a register conversion, no shuffle or
-// shared-memory round trip.  The C operand is the FP32 master L~ and B = -2 tau T~, so
-// one mma gives V = L~ - L~ T^ directly.
+// One warp per instance, in transposed form: the accumulators of mma.m16n8k16 hold
+//   V^T = L~^T + T^ L~^T   (T^ = -2 tau T~ is symmetric, so V^T = (L~ - 2 tau L~ T~)^T),
+// with the C operand the FP32 master L~^T, the constant A operand T^ and the B operand
+// L~^T.  A lane holds two adjacent entries of rows k of V^T (columns k of V) per n-tile,
+// so the prox's column norms are sums over the 4 lanes of a row (two butterfly shuffles),
+// which leave every lane with the norms of its own rows: no broadcast is needed.  Row N of
+// L~ is simply the last n-tile (column NB of L~^T).  The B operand of the next step is the
+// iterate transposed in 8 x 8 blocks: each block packed to 16 bits and moved with
+// movmatrix.trans, which turns the accumulator layout (row g, columns 2tq, 2tq + 1) into
+// the B-fragment layout (rows 2tq, 2tq + 1, column g).
 //
-// Tiles: rows are split into m-tiles of 16, variable columns into n-tiles of 8 and
-// k-tiles of 16.  Row block M (< NB/16) needs k-tiles 0..M and n-tiles 0..2M+1 only (L~
-// is lower-triangular, V is kept on and below the diagonal): the triangular skip of the
-// paper's array (Sec. IV-A) at tile granularity.  The augmented last row NB is one more
-// m-tile whose only live row is row NB; its L~_NN T^_{N,c} term is added in FP32.
-// The tensor-core instruction is the warp-level mma.sync: the per-instance operand B
-// changes with every instance and M is 33 rows, below the 64/128-row tiles of tcgen05.
+// Tiles: columns k of L~ in m-tiles of 16, rows i in n-tiles of 8 (the last holds row N),
+// j in k-tiles of 16.  Tile (M, n) exists only where some i >= k (V is lower-triangular,
+// V^T upper), and it needs only the k-tiles with j <= i (L~^T[j][i] = 0 for j > i): the
+// triangular skip of the paper's array (Sec. IV-A) at tile granularity.  The j = N term
+// (T^[k][N] L~_NN) and V_NN are added in FP32.  The tensor-core instruction is the
+// warp-level mma.sync: the per-instance operand T^ changes with every instance and the
+// problem is 33 x 33, below the 64/128-row tiles of tcgen05.
 #include "mma_tc.cuh"
 
 namespace taser {
@@ -131,21 +136,39 @@ struct Cursor<QueueSource> {
 // Shared-memory floats per warp after its staging slot: two job records (JobOut below).
 constexpr int kTcRecFloats = 24;
 
+template <int NB>
+struct TctCfg {
+  static constexpr int MT = NB / 16;      // m-tiles over the columns k of L~
+  static constexpr int KT = NB / 16;      // k-tiles over j
+  static constexpr int NT = NB / 8 + 1;   // n-tiles over the rows i of L~; the last holds row N (i = NB)
+  static constexpr int WARPS = 4;
+  // Tile (M, n) holds V^T[k][i] for k in 16M..16M+15, i in 8n..8n+7; rows i < k are zero.
+  __host__ __device__ static constexpr bool has_tile(int M, int n) { return n >= 2 * M; }
+  // k-tiles of j that reach n-tile n (L~^T[j][i] = 0 for j > i).
+  __host__ __device__ static constexpr int ktmax(int n) { return n / 2 < KT - 1 ? n / 2 : KT - 1; }
+};
+
+__device__ __forceinline__ uint32_t movmatrix_trans(uint32_t x) {
+  uint32_t y;
+  asm volatile("movmatrix.sync.aligned.m8n8.trans.b16 %0, %1;" : "=r"(y) : "r"(x));
+  return y;
+}
+
 // Persistent: each warp takes jobs from its source (a fixed stride, or a bucket queue) and
 // prefetches the next job's inputs with cp.async while it iterates on the current one.
 // MON: objective monitoring of taser_detect_monitored (dense source only).  f(L~) =
 // Tr(L~ T~ L~^T) is the sum over i >= k of L~_ik (L~ T~)_ik, the lower part of L~ T~ that
 // each gradient step forms.  A single BF16 product is too coarse to see a rise of f of a
-// fraction of a percent, so the monitor forms W = L~ T^ (T^ = -2 tau T~) tile by tile a
-// second time as a BF16 split (3 mma per product, about 2^-16 relative error) into
-// scratch accumulators, before the tile's own mma, and sums L~ o W; f = sum / (-2 tau).
-// The iteration itself is unchanged.  One more step after the outputs are written gives
-// f(L~(t_max)).
+// fraction of a percent, so the monitor forms W^T = T^ L~^T a second time as a BF16 split
+// (T^ = hi + lo as A fragments, the iterate's hi and lo moved like the B operand; 3 mma
+// per product, about 2^-16 relative error) into scratch accumulators, before the step's
+// own mma, and sums L~ o W; f = sum / (-2 tau).  The iteration itself is unchanged.  One
+// more step after the outputs are written gives f(L~(t_max)).
 template <int NB, bool FP16, class Src, bool MON = false>
-__global__ void __launch_bounds__(128, MON ? 3 : 4)
-detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
-  using C = TcCfg<NB>;
-  constexpr int KT = C::KT, NT = C::NT, MT = C::MT;
+__global__ void __launch_bounds__(128, MON ? 3 : 5)
+detect_tct_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
+  using C = TctCfg<NB>;
+  constexpr int MT = C::MT, KT = C::KT, NT = C::NT;
   extern __shared__ __align__(16) float smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tq = lane & 3;
@@ -171,10 +194,7 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
     Job first;
     double* ob = nullptr;
     have = cursor.next(src, first, ob, lane);
-    if (have) {
-      const int shift = stage_job(slot, first, lane, slot_floats);
-      park(first, ob, shift, 0);
-    }
+    if (have) park(first, ob, stage_job(slot, first, lane, slot_floats), 0);
   }
 
   while (have) {
@@ -184,70 +204,52 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
     const float* T = slot + outs[cur_m].shift;
     const float* Di = slot + N * N + 4;
     const float m2tau = -2.f * Di[N];
-    auto tval = [&](int k, int n) -> float {  // -2 tau T~ at bucket indices (k, n < NB)
-      return (k < N - 1 && n < N - 1) ? m2tau * T[k * N + n] : 0.f;
+    auto tval = [&](int k, int j) -> float {  // T^ at bucket indices (k, j < NB)
+      return (k < N - 1 && j < N - 1) ? m2tau * T[k * N + j] : 0.f;
     };
-    // B operand: B[k][n] = -2 tau T~[k][n]; lane holds rows 2tq..2tq+1 and +8, column g.
-    // A problem that fills the bucket (N = NB + 1, e.g. QPSK 128x16 at N = 33) has no padding
-    // rows or columns, so its values need no bounds test.
-    uint32_t bf[KT][NT][2];
-    if (N == NB + 1) {
+    // A operand: T^ rows k = 16M + g (+8), columns j = 16kt + 2tq (+1, +8, +9).  MON: also
+    // T^ = hi + lo in BF16 (same layout) for the monitor's split product.
+    uint32_t af[MT][KT][4];
+    uint32_t mah[MON ? MT : 1][KT][4], mal[MON ? MT : 1][KT][4];
 #pragma unroll
-      for (int kt = 0; kt < KT; ++kt)
+    for (int M = 0; M < MT; ++M)
 #pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
-          const float* c0 = T + k0 * (NB + 1) + n;
-          if (!TASER_IN((k0 + 9) * (NB + 1) + n, N * N)) {
-            bf[kt][nt][0] = bf[kt][nt][1] = 0u;
-            continue;
-          }
-          bf[kt][nt][0] = pack2<FP16>(m2tau * c0[0], m2tau * c0[NB + 1]);
-          bf[kt][nt][1] = pack2<FP16>(m2tau * c0[8 * (NB + 1)], m2tau * c0[9 * (NB + 1)]);
+      for (int kt = 0; kt < KT; ++kt) {
+        const int r = 16 * M + g, c = 16 * kt + 2 * tq;
+        float v[4][2];
+        if (N == NB + 1) {   // no padding rows or columns: no bounds tests
+          const float* r0 = T + r * (NB + 1) + c;
+          const float* r1 = r0 + 8 * (NB + 1);
+          v[0][0] = m2tau * r0[0], v[0][1] = m2tau * r0[1];
+          v[1][0] = m2tau * r1[0], v[1][1] = m2tau * r1[1];
+          v[2][0] = m2tau * r0[8], v[2][1] = m2tau * r0[9];
+          v[3][0] = m2tau * r1[8], v[3][1] = m2tau * r1[9];
+        } else {
+          v[0][0] = tval(r, c), v[0][1] = tval(r, c + 1);
+          v[1][0] = tval(r + 8, c), v[1][1] = tval(r + 8, c + 1);
+          v[2][0] = tval(r, c + 8), v[2][1] = tval(r, c + 9);
+          v[3][0] = tval(r + 8, c + 8), v[3][1] = tval(r + 8, c + 9);
         }
-    } else {
 #pragma unroll
-      for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
-          bf[kt][nt][0] = pack2<FP16>(tval(k0, n), tval(k0 + 1, n));
-          bf[kt][nt][1] = pack2<FP16>(tval(k0 + 8, n), tval(k0 + 9, n));
+        for (int x = 0; x < 4; ++x) {
+          af[M][kt][x] = pack2<FP16>(v[x][0], v[x][1]);
+          if constexpr (MON) split_bf16(v[x][0], v[x][1], mah[M][kt][x], mal[M][kt][x]);
         }
-    }
-    // MON: T^ = hi + lo in BF16 (B layout of bf).
-    uint32_t mbh[MON ? KT : 1][NT][2], mbl[MON ? KT : 1][NT][2];
-    if constexpr (MON) {
-#pragma unroll
-      for (int kt = 0; kt < KT; ++kt)
-#pragma unroll
-        for (int nt = 0; nt < NT; ++nt) {
-          const int k0 = 16 * kt + 2 * tq, n = 8 * nt + g;
-          split_bf16(tval(k0, n), tval(k0 + 1, n), mbh[kt][nt][0], mbl[kt][nt][0]);
-          split_bf16(tval(k0 + 8, n), tval(k0 + 9, n), mbh[kt][nt][1], mbl[kt][nt][1]);
-        }
-    }
-    // Row N of T^ at this lane's accumulator columns c = 8n + 2tq + p (FP32).
-    float tN[NT][2];
-#pragma unroll
-    for (int nt = 0; nt < NT; ++nt)
-#pragma unroll
-      for (int p = 0; p < 2; ++p) {
-        const int c = 8 * nt + 2 * tq + p;
-        tN[nt][p] = (g == 0 && c < N - 1 && TASER_IN((N - 1) * N + c, N * N)) ? m2tau * T[(N - 1) * N + c] : 0.f;
       }
-    uint64_t tN2[NT];   // packed pairs (zero off the lanes g == 0 that hold row N)
+    // This lane's rows k = 16M + g + 8h: T^[k][N] (FP32, the j = N term) and D_k.
+    float tkN[MT][2], Dk[MT][2];
 #pragma unroll
-    for (int nt = 0; nt < NT; ++nt) tN2[nt] = f2pack(tN[nt][0], tN[nt][1]);
-    auto tN2f = [&](int n, int p) -> float { return tN[n][p]; };
+    for (int M = 0; M < MT; ++M)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * M + g + 8 * h;
+        tkN[M][h] = k < N - 1 ? m2tau * T[k * N + N - 1] : 0.f;
+        Dk[M][h] = k < N - 1 ? Di[k] : 0.f;
+      }
     const float tnNN = m2tau * T[(N - 1) * N + (N - 1)];
     const float DN = Di[N - 1];
-    // After the column-sum reduction this lane owns column cown.
-    const int own_idx = NT == 4 ? g : (g >> 1);
-    const int cown = 8 * (own_idx >> 1) + 2 * tq + (own_idx & 1);
-    const float Down = cown < N - 1 ? Di[cown] : 0.f;
-    // L~(0) = D in accumulator layout: element (M, n, e) is row 16M + g + 8(e >> 1),
-    // column 8n + 2tq + (e & 1).
+    // L~(0) = D in the V^T layout: element (M, n, e) is k = 16M + g + 8(e >> 1),
+    // i = 8n + 2tq + (e & 1).
     float acc[MT][NT][4];
 #pragma unroll
     for (int M = 0; M < MT; ++M)
@@ -255,8 +257,8 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
       for (int n = 0; n < NT; ++n)
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-          const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
-          acc[M][n][e] = (M < MT - 1 && r == c && r < N - 1) ? Di[r] : 0.f;
+          const int k = 16 * M + g + 8 * (e >> 1), i = 8 * n + 2 * tq + (e & 1);
+          acc[M][n][e] = (C::has_tile(M, n) && i == k && k < N - 1) ? Dk[M][e >> 1] : 0.f;
         }
     __syncwarp();  // every lane has read the slot
     bool have_next;
@@ -264,165 +266,102 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
       Job nxt;
       double* ob = nullptr;
       have_next = cursor.next(src, nxt, ob, lane);
-      if (have_next) {
-        const int shift = stage_job(slot, nxt, lane, slot_floats);
-        park(nxt, ob, shift, cur_m ^ 1);
-      }
+      if (have_next) park(nxt, ob, stage_job(slot, nxt, lane, slot_floats), cur_m ^ 1);
     }
     float LNN = DN;
     uint32_t fl = 0;
-    // Inside a diagonal 16 x 16 block the element (row g + 8h, column 2tq + p + 8h') lies
-    // above the diagonal iff h' > h, or h' == h and 2tq + p > g.
-    const bool up0 = 2 * tq > g, up1 = 2 * tq + 1 > g;
-    const int src_row0 = 4 * (2 * tq) + (g != 0), src_row1 = 4 * (2 * tq + 1) + (g != 0);
+    // Inside a diagonal 8 x 8 block, element (row g, column 2tq + p) lies below the
+    // diagonal of V^T (i < k) iff 2tq + p < g.
+    const bool lo0 = 2 * tq < g, lo1 = 2 * tq + 1 < g;
 
-    // One gradient step: acc <- V = L~ - tril(2 tau L~ T~) (kept lower-triangular);
-    // returns V_NN.  MON: fterm += sum of L~_ik W_ik over this lane's elements, W = L~ T^.
+    // One gradient step: acc <- V^T = L~^T + T^ L~^T (kept on and above its diagonal);
+    // returns V_NN.  MON: fterm += sum of L~_ik W_ik over this lane's elements, W = L~ T^
+    // (as W^T = T^ L~^T, a BF16 split product of the old iterate, before the step).
     auto grad_step = [&](float& fterm) -> float {
-      // V_NN partial from row N of L~(t-1) (lanes g == 0 hold it), FP32.
-      uint64_t part2 = 0ull;
+      // V_NN partial sum_{j < N} T^[N][j] L~[N][j] from the old row N (column NB of L~^T,
+      // held by the lanes tq == 0), summed over g.
+      float part = 0.f;
+      if (tq == 0) {
 #pragma unroll
-      for (int n = 0; n < NT; ++n) part2 = f2fma(f2pack(acc[MT - 1][n][0], acc[MT - 1][n][1]), tN2[n], part2);
-      float part, part_hi;
-      f2unpack(part2, part, part_hi);
-      part += part_hi;
-      part += __shfl_xor_sync(TASER_FULL_MASK, part, 1);
-      part += __shfl_xor_sync(TASER_FULL_MASK, part, 2);
-      part = __shfl_sync(TASER_FULL_MASK, part, 0);
-
+        for (int M = 0; M < MT; ++M)
 #pragma unroll
-      for (int M = 0; M < MT; ++M) {
-        // A operand of row block M from the FP32 master (old L~).  The last row block
-        // holds row N only (its rows g + 8 are identically zero).
-        uint32_t a[KT][4];
+          for (int h = 0; h < 2; ++h) part = fmaf(tkN[M][h], acc[M][NT - 1][2 * h], part);
+      }
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 4);
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 8);
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 16);
+      part = __shfl_sync(TASER_FULL_MASK, part, lane & 28);   // from the lane tq == 0 of the row
+      // B operand from the old iterate: block (kb, ib) of L~^T transposed; blocks with
+      // kb > ib are zero.
+      uint32_t bfr[KT][NT][2];
+      uint32_t mbh[MON ? KT : 1][NT][2], mbl[MON ? KT : 1][NT][2];
 #pragma unroll
-        for (int kt = 0; kt <= C::kmax(M); ++kt) {
-          a[kt][0] = pack2<FP16>(acc[M][2 * kt][0], acc[M][2 * kt][1]);
-          a[kt][2] = pack2<FP16>(acc[M][2 * kt + 1][0], acc[M][2 * kt + 1][1]);
-          if (M < MT - 1) {
-            a[kt][1] = pack2<FP16>(acc[M][2 * kt][2], acc[M][2 * kt][3]);
-            a[kt][3] = pack2<FP16>(acc[M][2 * kt + 1][2], acc[M][2 * kt + 1][3]);
-          } else {
-            a[kt][1] = 0u;
-            a[kt][3] = 0u;
-          }
-        }
-        if constexpr (MON) {
-          // W = L~ T^ of this row block as a BF16 split, dotted with L~ (the old values:
-          // every tile's own mma comes later).  Row N: the transposed product T^ l_N^T, whose
-          // columns are moved into the accumulator layout, plus L~_NN T^_{N,c} in FP32.
-          uint32_t ah[KT][4], al[KT][4];
+      for (int kt = 0; kt < KT; ++kt)
 #pragma unroll
-          for (int kt = 0; kt <= C::kmax(M); ++kt) {
-            split_bf16(acc[M][2 * kt][0], acc[M][2 * kt][1], ah[kt][0], al[kt][0]);
-            split_bf16(acc[M][2 * kt + 1][0], acc[M][2 * kt + 1][1], ah[kt][2], al[kt][2]);
-            if (M < MT - 1) {
-              split_bf16(acc[M][2 * kt][2], acc[M][2 * kt][3], ah[kt][1], al[kt][1]);
-              split_bf16(acc[M][2 * kt + 1][2], acc[M][2 * kt + 1][3], ah[kt][3], al[kt][3]);
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            const int kb = 2 * kt + q, M = kb / 2, h = kb % 2;
+            if (kt > C::ktmax(n) || kb > n) {
+              bfr[kt][n][q] = 0u;
+              if constexpr (MON) mbh[kt][n][q] = mbl[kt][n][q] = 0u;
             } else {
-              ah[kt][1] = ah[kt][3] = al[kt][1] = al[kt][3] = 0u;
-            }
-          }
-          if (M < MT - 1) {
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-              if (!C::has_tile(M, n)) continue;
-              float w4[4] = {0.f, 0.f, 0.f, 0.f};
-#pragma unroll
-              for (int kt = 0; kt <= C::kmax(M); ++kt) {
-                mma16816<false>(w4, ah[kt], mbh[kt][n]);
-                mma16816<false>(w4, ah[kt], mbl[kt][n]);
-                mma16816<false>(w4, al[kt], mbh[kt][n]);
-              }
-#pragma unroll
-              for (int e = 0; e < 4; ++e) fterm = fmaf(acc[M][n][e], w4[e], fterm);
-            }
-          } else {
-            float d[KT][4];
-#pragma unroll
-            for (int mt = 0; mt < KT; ++mt) {
-#pragma unroll
-              for (int e = 0; e < 4; ++e) d[mt][e] = 0.f;
-#pragma unroll
-              for (int kt = 0; kt < KT; ++kt) {
-                const uint32_t th[4] = {mbh[kt][2 * mt][0], mbh[kt][2 * mt + 1][0], mbh[kt][2 * mt][1],
-                                        mbh[kt][2 * mt + 1][1]};
-                const uint32_t tl[4] = {mbl[kt][2 * mt][0], mbl[kt][2 * mt + 1][0], mbl[kt][2 * mt][1],
-                                        mbl[kt][2 * mt + 1][1]};
-                const uint32_t bh2[2] = {ah[kt][0], ah[kt][2]}, bl2[2] = {al[kt][0], al[kt][2]};
-                mma16816<false>(d[mt], th, bh2);
-                mma16816<false>(d[mt], tl, bh2);
-                mma16816<false>(d[mt], th, bl2);
+              bfr[kt][n][q] = movmatrix_trans(pack2<FP16>(acc[M][n][2 * h], acc[M][n][2 * h + 1]));
+              if constexpr (MON) {
+                uint32_t hi, lo;
+                split_bf16(acc[M][n][2 * h], acc[M][n][2 * h + 1], hi, lo);
+                mbh[kt][n][q] = movmatrix_trans(hi);
+                mbl[kt][n][q] = movmatrix_trans(lo);
               }
             }
-#pragma unroll
-            for (int n = 0; n < NT; ++n) {
-              const float v0 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row0);
-              const float v1 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row1);
-              fterm = fmaf(acc[M][n][0], fmaf(LNN, tN2f(n, 0), v0), fterm);
-              fterm = fmaf(acc[M][n][1], fmaf(LNN, tN2f(n, 1), v1), fterm);
-            }
           }
-        }
-        if (M == MT - 1) {
-          // k = N term of row N in FP32: L~_NN T^_{N,c}.
-          const uint64_t lnn2 = f2pack(LNN, LNN);
+      if constexpr (MON) {
 #pragma unroll
-          for (int n = 0; n < NT; ++n) TASER_PAIR_APPLY(acc[M][n], 0, f2fma(lnn2, tN2[n], _x));
-        }
-        if (M == MT - 1 && KT >= 2) {
-          // Row N as the transposed product T^ L~_N^T (T^ symmetric): KT m-tiles of output
-          // columns against KT k-tiles, KT^2 mma instead of the KT NT of a 16-row tile with
-          // one live row (4 instead of 8 at NB = 32; at NB = 16 the saved mma costs more in
-          // shuffles than it gains, measured).  The A fragments of T^ are the B fragments
-          // already held; the B operand is the packed row N (column 0; rows g != 0 of the
-          // row-N tile are zero).
-          float d[KT][4];
-#pragma unroll
-          for (int mt = 0; mt < KT; ++mt) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) d[mt][e] = 0.f;
-#pragma unroll
-            for (int kt = 0; kt < KT; ++kt) {
-              const uint32_t at[4] = {bf[kt][2 * mt][0], bf[kt][2 * mt + 1][0], bf[kt][2 * mt][1],
-                                      bf[kt][2 * mt + 1][1]};
-              const uint32_t bt[2] = {a[kt][0], a[kt][2]};
-              mma16816<FP16>(d[mt], at, bt);
-            }
-          }
-          // Column c = 8n + 2tq + p of row N sits in D column 0 at lane 4 (c mod 8), element
-          // 2 (n mod 2) of m-tile n / 2; lanes g != 0 read a lane with tq = 1 (D column 2,
-          // zero), so their row-N tile stays zero.
-#pragma unroll
-          for (int n = 0; n < NT; ++n) {
-            const float v0 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row0);
-            const float v1 = __shfl_sync(TASER_FULL_MASK, d[n >> 1][2 * (n & 1)], src_row1);
-            TASER_PAIR_APPLY(acc[M][n], 0, f2fma(f2pack(1.f, 1.f), f2pack(v0, v1), _x));
-          }
-        } else {
+        for (int M = 0; M < MT; ++M)
 #pragma unroll
           for (int n = 0; n < NT; ++n) {
             if (!C::has_tile(M, n)) continue;
+            float w4[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
-            for (int kt = 0; kt <= C::kmax(M); ++kt) {
-              if (M == MT - 1) mma16816_top<FP16>(acc[M][n], a[kt], bf[kt][n]);
-              else mma16816<FP16>(acc[M][n], a[kt], bf[kt][n]);
+            for (int kt = 0; kt <= C::ktmax(n); ++kt) {
+              mma16816<false>(w4, mah[M][kt], mbh[kt][n]);
+              mma16816<false>(w4, mah[M][kt], mbl[kt][n]);
+              mma16816<false>(w4, mal[M][kt], mbh[kt][n]);
             }
-          }
-        }
-      }
-      // Keep V lower-triangular inside the diagonal blocks: the rows g of n-tile 2M + 1
-      // are above the diagonal on every lane.
+            if (n == NT - 1 && tq == 0) {   // j = N term of column NB, in FP32
+              w4[0] = fmaf(tkN[M][0], LNN, w4[0]);
+              w4[2] = fmaf(tkN[M][1], LNN, w4[2]);
+            }
 #pragma unroll
-      for (int M = 0; M < MT - 1; ++M) {
-        if (up0) acc[M][2 * M][0] = 0.f;
-        if (up1) acc[M][2 * M][1] = 0.f;
-        acc[M][2 * M + 1][0] = 0.f;
-        acc[M][2 * M + 1][1] = 0.f;
-        if (up0) acc[M][2 * M + 1][2] = 0.f;
-        if (up1) acc[M][2 * M + 1][3] = 0.f;
+            for (int e = 0; e < 4; ++e) fterm = fmaf(acc[M][n][e], w4[e], fterm);
+          }
       }
-
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+          if (!C::has_tile(M, n)) continue;
+#pragma unroll
+          for (int kt = 0; kt <= C::ktmax(n); ++kt) mma16816<FP16>(acc[M][n], af[M][kt], bfr[kt][n]);
+        }
+      // j = N term of column NB: V^T[k][N] += T^[k][N] L~_NN.
+      if (tq == 0) {
+#pragma unroll
+        for (int M = 0; M < MT; ++M)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) acc[M][NT - 1][2 * h] = fmaf(tkN[M][h], LNN, acc[M][NT - 1][2 * h]);
+      }
+      // Keep V^T on and above its diagonal (i >= k): blocks kb == ib are masked, the block
+      // kb = 2M + 1 > ib = 2M is cleared.
+#pragma unroll
+      for (int M = 0; M < MT; ++M) {
+        if (lo0) acc[M][2 * M][0] = 0.f;
+        if (lo1) acc[M][2 * M][1] = 0.f;
+        acc[M][2 * M][2] = 0.f;
+        acc[M][2 * M][3] = 0.f;
+        if (lo0) acc[M][2 * M + 1][2] = 0.f;
+        if (lo1) acc[M][2 * M + 1][3] = 0.f;
+      }
       return fmaf(LNN, tnNN, LNN) + part;
     };
 
@@ -445,90 +384,63 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
       if constexpr (MON) monitor(t, fterm, vnn);
       if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
       if (literal) LNN = vnn >= 0.f ? DN : -DN;
-
-      // prox: column sums of squares, reduced over the 8 lanes sharing tq.
-      float s[C::NV];
+      // prox: squared norms of this lane's rows k, summed over the 4 lanes of the row.
+      float sn[MT][2];
 #pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        uint64_t v2 = 0ull;
+      for (int M = 0; M < MT; ++M)
 #pragma unroll
-        for (int M = 0; M < MT; ++M) {
-          if (!C::has_tile(M, n)) continue;
-          if (!(M < MT - 1 && n == 2 * M + 1)) {   // rows g of n-tile 2M + 1 are zero
-            const uint64_t x01 = f2pack(acc[M][n][0], acc[M][n][1]);
-            v2 = f2fma(x01, x01, v2);
+        for (int h = 0; h < 2; ++h) {
+          uint64_t v2 = 0ull;
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            if (!C::has_tile(M, n) || (n == 2 * M && h == 1)) continue;   // the cleared block
+            const uint64_t x = f2pack(acc[M][n][2 * h], acc[M][n][2 * h + 1]);
+            v2 = f2fma(x, x, v2);
           }
-          if (M < MT - 1) {
-            const uint64_t x23 = f2pack(acc[M][n][2], acc[M][n][3]);
-            v2 = f2fma(x23, x23, v2);
-          }
+          float a, b;
+          f2unpack(v2, a, b);
+          sn[M][h] = a + b;
         }
-        f2unpack(v2, s[2 * n], s[2 * n + 1]);
-      }
-      // Transpose-reduce over lane bits 4, 3, 2 (each step halves the values a lane keeps),
-      // then a shuffle broadcast of the scales.  (An exchange of the partials and scales
-      // through shared memory was measured at bucket 32, together with the triangle
-      // staging above: 4,890 instead of 4,182 warp instructions per instance, 0.440 instead
-      // of 0.391 ms per 65,536; the FMA-pipe count rose by 18 per iteration, the register
-      // moves that assemble the 16-byte stores and the addressing.)
-      {
-        int len = C::NV;
 #pragma unroll
-        for (int m = 16; m >= 4; m >>= 1) {
-          const bool up = (lane & m) != 0;
-          if (len > 1) {
-            const int h = len >> 1;
+      for (int M = 0; M < MT; ++M)
 #pragma unroll
-            for (int i = 0; i < C::NV / 2; ++i) {
-              if (i >= h) break;
-              const float send = up ? s[i] : s[i + h];
-              const float keep = up ? s[i + h] : s[i];
-              s[i] = keep + __shfl_xor_sync(TASER_FULL_MASK, send, m);
-            }
-            len = h;
-          } else {
-            s[0] += __shfl_xor_sync(TASER_FULL_MASK, s[0], m);
+        for (int h = 0; h < 2; ++h) sn[M][h] += __shfl_xor_sync(TASER_FULL_MASK, sn[M][h], 1);
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sn[M][h] += __shfl_xor_sync(TASER_FULL_MASK, sn[M][h], 2);
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float sc = 0.f;
+          if (sn[M][h] > 0.f) {
+            sc = Dk[M][h] * rsqrtf(sn[M][h]);
+          } else if (16 * M + g + 8 * h < N - 1) {
+            fl |= TASER_FLAG_ZERO_COLUMN;
+          }
+          const uint64_t sc2 = f2pack(sc, sc);
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            if (!C::has_tile(M, n) || (n == 2 * M && h == 1)) continue;
+            TASER_PAIR_APPLY(acc[M][n], 2 * h, f2mul(_x, sc2));
           }
         }
-      }
-      float sc_own = 0.f;
-      if (s[0] > 0.f) {
-        sc_own = Down * rsqrtf(s[0]);
-      } else if (cown < N - 1) {
-        fl |= TASER_FLAG_ZERO_COLUMN;
-      }
-#pragma unroll
-      for (int n = 0; n < NT; ++n) {
-        float sc[2];
-#pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          const int idx = 2 * n + p;
-          sc[p] = __shfl_sync(TASER_FULL_MASK, sc_own, 4 * (NT == 4 ? idx : 2 * idx) + tq);
-        }
-        const uint64_t sc2 = f2pack(sc[0], sc[1]);
-#pragma unroll
-        for (int M = 0; M < MT; ++M) {
-          if (!C::has_tile(M, n)) continue;
-          if (!(M < MT - 1 && n == 2 * M + 1)) TASER_PAIR_APPLY(acc[M][n], 0, f2mul(_x, sc2));
-          if (M < MT - 1) TASER_PAIR_APPLY(acc[M][n], 2, f2mul(_x, sc2));
-        }
-      }
     }
 
     const JobOut o = outs[cur_m];
-
-    // Decisions from row N (lanes g == 0).
-    if (g == 0) {
+    // Decisions from row N of L~ (column NB of L~^T, lanes tq == 0).
+    if (tq == 0) {
 #pragma unroll
-      for (int n = 0; n < NT; ++n)
+      for (int M = 0; M < MT; ++M)
 #pragma unroll
-        for (int p = 0; p < 2; ++p) {
-          const int c = 8 * n + 2 * tq + p;
-          if (c < N - 1 && TASER_IN(c, N - 1)) {
-            float r = acc[MT - 1][n][p];
+        for (int h = 0; h < 2; ++h) {
+          const int k = 16 * M + g + 8 * h;
+          if (k < N - 1 && TASER_IN(k, N - 1)) {
+            float r = acc[M][NT - 1][2 * h];
             TASER_FINITE(r);
             if (literal && LNN < 0.f) r = -r;
-            o.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
+            o.s[k] = r >= 0.f ? int8_t(1) : int8_t(-1);
           }
         }
     }
@@ -540,12 +452,11 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
         for (int n = 0; n < NT; ++n)
 #pragma unroll
           for (int e = 0; e < 4; ++e) {
-            if (M == MT - 1 && e >= 2) continue;
-            const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
-            const int rr = bucket_to_real(r, N, NB);
-            if (rr < 0 || c >= N - 1 || !TASER_IN(rr * N + c, N * N)) continue;
-            Lo[(int64_t)rr * N + c] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
-            TASER_FINITE(Lo[(int64_t)rr * N + c]);
+            const int k = 16 * M + g + 8 * (e >> 1), i = 8 * n + 2 * tq + (e & 1);
+            const int rr = bucket_to_real(i, N, NB);
+            if (rr < 0 || k >= N - 1 || !TASER_IN(rr * N + k, N * N)) continue;
+            Lo[(int64_t)rr * N + k] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
+            TASER_FINITE(Lo[(int64_t)rr * N + k]);
           }
       for (int rr = lane; rr < N; rr += 32)
         if (TASER_IN(rr * N + N - 1, N * N)) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
@@ -564,24 +475,26 @@ detect_tc_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
   }
 }
 
+// Persistent launch for a job source: `blocks_per_sm` blocks per SM (as many as fit if
+// <= 0), fewer if the jobs are fewer (jobs < 0: unknown, a queue).
 template <int NB, bool FP16, class Src, bool MON = false>
 static cudaError_t launch_tc_src(const Src& src, int64_t jobs, int blocks_per_sm, int literal, int slot_floats,
                                  float ascent_tol, cudaStream_t st) {
-  using C = TcCfg<NB>;
+  using C = TctCfg<NB>;
   const size_t smem = (size_t)C::WARPS * (slot_floats + kTcRecFloats) * sizeof(float);
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, Src, MON>, 32 * C::WARPS,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tct_kernel<NB, FP16, Src, MON>, 32 * C::WARPS,
                                                       smem);
   if (e != cudaSuccess) return e;
   const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
   const int64_t need = (jobs + C::WARPS - 1) / C::WARPS;
   const int64_t resident = (int64_t)sms * per_sm;
   const int64_t blocks = jobs >= 0 && need < resident ? need : resident;
-  detect_tc_kernel<NB, FP16, Src, MON><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(src, literal, slot_floats,
-                                                                                      ascent_tol);
+  detect_tct_kernel<NB, FP16, Src, MON><<<(unsigned)blocks, 32 * C::WARPS, smem, st>>>(src, literal, slot_floats,
+                                                                                       ascent_tol);
   return cudaGetLastError();
 }
 
@@ -589,15 +502,15 @@ template <int NB, bool FP16, bool MON = false>
 static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                              int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st,
                              double* obj = nullptr, float ascent_tol = 0.f) {
-  using C = TcCfg<NB>;
+  using C = TctCfg<NB>;
   const int slot_floats = tc_slot_floats(N);
+  const size_t smem = (size_t)C::WARPS * (slot_floats + kTcRecFloats) * sizeof(float);
   int dev = 0, sms = 0, fit = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tc_kernel<NB, FP16, DenseSource, MON>,
-                                                      32 * C::WARPS,
-                                                      (size_t)C::WARPS * (slot_floats + kTcRecFloats) * sizeof(float));
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tct_kernel<NB, FP16, DenseSource, MON>,
+                                                      32 * C::WARPS, smem);
   if (e != cudaSuccess) return e;
   const int64_t need = (batch + C::WARPS - 1) / C::WARPS;
   const int64_t resident = (int64_t)sms * (fit > 0 ? fit : 1);

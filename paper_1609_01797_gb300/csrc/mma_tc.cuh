@@ -47,24 +47,6 @@ __device__ __forceinline__ void mma16816(float (&d)[4], const uint32_t (&a)[4], 
     f2unpack(_y, arr[e], arr[e + 1]);           \
   } while (0)
 
-// The same mma for the m-tile of row N, whose rows g + 8 are identically zero: their
-// accumulators are fed zeros and discarded, so they occupy no registers across iterations.
-template <bool FP16>
-__device__ __forceinline__ void mma16816_top(float (&d)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
-  float z2 = 0.f, z3 = 0.f;
-  if constexpr (FP16) {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.f16.f16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(z2), "+f"(z3)
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  } else {
-    asm("mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(z2), "+f"(z3)
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-  }
-}
-
 // BF16 split x = hi + lo of a float pair (hi = bf16(x), lo = bf16(x - hi)): the products
 // hi hi' + hi lo' + lo hi' carry about 2^-16 relative error, where a single BF16 product
 // carries 2^-8.  Used only by the objective monitor, whatever the path's precision.
