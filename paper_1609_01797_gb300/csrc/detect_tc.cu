@@ -336,10 +336,13 @@ detect_tct_kernel(Src src, int literal, int slot_floats, float ascent_tol) {
             for (int e = 0; e < 4; ++e) fterm = fmaf(acc[M][n][e], w4[e], fterm);
           }
       }
+      // The step's products, row N's n-tile first (measured: 0.371 -> 0.367 ms per 65,536 at
+      // N = 33 against the m-tile-major order; two partial chains in the column sums below
+      // were slower, 0.384 ms).
 #pragma unroll
-      for (int M = 0; M < MT; ++M)
+      for (int n = NT - 1; n >= 0; --n)
 #pragma unroll
-        for (int n = 0; n < NT; ++n) {
+        for (int M = 0; M < MT; ++M) {
           if (!C::has_tile(M, n)) continue;
 #pragma unroll
           for (int kt = 0; kt <= C::ktmax(n); ++kt) mma16816<FP16>(acc[M][n], af[M][kt], bfr[kt][n]);
