@@ -925,7 +925,7 @@ def main():
     spec_tf = n * spectral_flops_per_instance(U) / (head["spectral_ms"] * 1e-3) / 1e12
     roofs = {
         "detect": (head["detect_ms"], {
-            "kernel": "detect_tc_kernel<32,bf16> (mma.sync m16n8k16)", "bound": "tensor", "achieved": det_tc,
+            "kernel": "detect_tct_kernel<32,bf16> (transposed form, mma.sync m16n8k16)", "bound": "tensor", "achieved": det_tc,
             "peak": bf16_peak, "unit": "TFLOP/s", "frac": det_tc / bf16_peak, "traffic": tr("detect_tc"),
             "peak_source": peak_src, "algorithmic_flops_per_launch": fl * n, "ms_per_launch": head["detect_ms"],
             "fp32_pipe_frac": det_tc / fp32_peak,
