@@ -929,8 +929,9 @@ def main():
             "peak": bf16_peak, "unit": "TFLOP/s", "frac": det_tc / bf16_peak, "traffic": tr("detect_tc"),
             "peak_source": peak_src, "algorithmic_flops_per_launch": fl * n, "ms_per_launch": head["detect_ms"],
             "fp32_pipe_frac": det_tc / fp32_peak,
-            # the mma.sync work actually issued: 14 m16n8k16 per iteration at N = 33 (row blocks
-            # 0 and 1: 2 + 8, row N as the transposed product: 4), 4,096 flops each
+            # the mma.sync work actually issued: 14 m16n8k16 per iteration at N = 33 (m-tile 0 of
+            # the columns k: 1 + 1 + 2 + 2 + 2 over n-tiles 0..4, m-tile 1: 2 + 2 + 2 over n-tiles
+            # 2..4; n-tile 4 holds row N), 4,096 flops each
             "padded_issue": {"flops_per_instance": 14 * 4096 * T_MAX, "achieved": padded_tf, "unit": "TFLOP/s",
                              "frac": padded_tf / bf16_peak},
             # min(tensor pipe at the algorithmic flops, FP32 pipe at the prox's flops, HBM at the
