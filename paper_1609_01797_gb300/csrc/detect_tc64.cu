@@ -66,9 +66,15 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
   const int N = jb.N;
   const float* T = jb.T;
   const float m2tau = -2.f * (*jb.tau);
+#ifdef TASER_DEBUG
   auto tval = [&](int k, int n) -> float {
     return (k < N - 1 && n < N - 1 && TASER_IN(k * N + n, N * N)) ? m2tau * T[(int64_t)k * N + n] : 0.f;
   };
+#else
+  // (The release code keeps this kernel's original shape: folding in the debug build's
+  // checks, even as constants, was measured 8.5% slower at N = 65.)
+  auto tval = [&](int k, int n) -> float { return (k < N - 1 && n < N - 1) ? m2tau * T[(int64_t)k * N + n] : 0.f; };
+#endif
   auto needB = [](int kt, int n) -> bool {
     return (kt <= MLO && n < NLO) || (kt <= MHI && n < NHI) || (n >= RN0 && n < RN0 + 4);
   };
@@ -270,9 +276,13 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int c = 8 * (RN0 + n) + 2 * tq + p;
+#ifdef TASER_DEBUG
         if (c < N - 1 && TASER_IN(c, N - 1)) {
+          TASER_FINITE(rw[n][p]);
+#else
+        if (c < N - 1) {
+#endif
           float r = rw[n][p];
-          TASER_FINITE(r);
           if (literal && LNN < 0.f) r = -r;
           jb.s[c] = r >= 0.f ? int8_t(1) : int8_t(-1);
         }
@@ -287,9 +297,14 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const int r = 16 * M + g + 8 * (e >> 1), c = 8 * n + 2 * tq + (e & 1);
+#ifdef TASER_DEBUG
           if (r >= N - 1 || c >= N - 1 || !TASER_IN(r * N + c, N * N)) continue;
           Lo[(int64_t)r * N + c] = n < nmax ? acc[n < nmax ? n : 0][e] : 0.f;
           TASER_FINITE(Lo[(int64_t)r * N + c]);
+#else
+          if (r >= N - 1 || c >= N - 1) continue;
+          Lo[(int64_t)r * N + c] = n < nmax ? acc[n < nmax ? n : 0][e] : 0.f;
+#endif
         }
     };
     put(lo, std::integral_constant<int, MLO>{}, NLO);
@@ -300,12 +315,20 @@ __device__ __forceinline__ void tc64_run(const Job& jb, float* X, int lane, int 
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
           const int c = 8 * (RN0 + n) + 2 * tq + p;
+#ifdef TASER_DEBUG
           if (c < N - 1 && TASER_IN((N - 1) * N + c, N * N)) Lo[(int64_t)(N - 1) * N + c] = rw[n][p];
+#else
+          if (c < N - 1) Lo[(int64_t)(N - 1) * N + c] = rw[n][p];
+#endif
         }
     }
     if (ROLE == 0)
+#ifdef TASER_DEBUG
       for (int rr = lane; rr < N; rr += 32)
         if (TASER_IN(rr * N + N - 1, N * N)) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+#else
+      for (int rr = lane; rr < N; rr += 32) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+#endif
   }
 }
 
@@ -366,13 +389,21 @@ detect_tc64_kernel(bool from_list, int64_t batch, int N, const float* __restrict
   int64_t k = 0;                                        // jobs acquired so far
 
   auto valid = [&](int64_t kk) { return gp + kk * stride < count; };
+#ifdef TASER_DEBUG
   auto list_at = [&](int64_t kk) {
     const int64_t at = lbase + (gp + kk * stride);
     return q.list + (TASER_IN(at, q.n) ? at : 0);
   };
+#else
+  auto list_at = [&](int64_t kk) { return q.list + lbase + (gp + kk * stride); };
+#endif
   // Thread 0: item record of job kk (its list entry is already in the ring), 8 bytes at a time.
   auto fetch_item = [&](int64_t kk) {
+#ifdef TASER_DEBUG
     const float* src = reinterpret_cast<const float*>(q.items + (TASER_IN(lidx[kk & 7], q.n) ? lidx[kk & 7] : 0));
+#else
+    const float* src = reinterpret_cast<const float*>(q.items + lidx[kk & 7]);
+#endif
     float* dst = reinterpret_cast<float*>(litem + (kk & 3));
 #pragma unroll
     for (int h = 0; h < (int)(sizeof(taser_item) / 8); ++h) {
@@ -402,12 +433,19 @@ detect_tc64_kernel(bool from_list, int64_t batch, int N, const float* __restrict
   auto stage = [&](const Job& jb, int w) {
     float* S = slots + w * SLOT64;
     const int nn = jb.N * jb.N;
+#ifdef TASER_DEBUG
     for (int i = tid; i < nn; i += 64)
       if (TASER_IN(i, SLOT64)) cp_async4_64(S + i, jb.T + i);
     for (int i = tid; i < jb.N; i += 64)
       if (TASER_IN(nn + i, SLOT64)) cp_async4_64(S + nn + i, jb.D + i);
     if (tid == 0) {
       if (TASER_IN(nn + jb.N, SLOT64)) cp_async4_64(S + nn + jb.N, jb.tau);
+#else
+    for (int i = tid; i < nn; i += 64) cp_async4_64(S + i, jb.T + i);
+    for (int i = tid; i < jb.N; i += 64) cp_async4_64(S + nn + i, jb.D + i);
+    if (tid == 0) {
+      cp_async4_64(S + nn + jb.N, jb.tau);
+#endif
       recs[w] = JobRec64{jb.L, jb.s, jb.flag, jb.N, jb.t_max};
     }
     asm volatile("cp.async.commit_group;" ::: "memory");
