@@ -67,6 +67,18 @@ static __device__ __forceinline__ void finite(float v) {
 #define TASER_FINITE(v) ((void)0)
 #define TASER_DEBUG_COLLECTOR(name)
 #endif
+// Guards that vanish from release builds token for token, so that a kernel's release code
+// keeps its exact shape: TASER_CHECKED(c) stmt is `if (c) stmt` in the debug build and
+// `stmt` otherwise; `cond TASER_AND(c)` is `cond && (c)` in the debug build and `cond`
+// otherwise.  (Checks folded in as constants changed the release code generation of two
+// kernels measurably, 8-9%.)
+#ifdef TASER_DEBUG
+#define TASER_CHECKED(c) if (c)
+#define TASER_AND(c) &&(c)
+#else
+#define TASER_CHECKED(c)
+#define TASER_AND(c)
+#endif
 
 namespace taser {
 

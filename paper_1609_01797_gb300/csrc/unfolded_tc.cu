@@ -66,8 +66,8 @@ __device__ __forceinline__ void stage_T(float* slot, const float* T, const float
   }
   for (int e = lane; e < ntri; e += 32) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(slot + i * N + j);
-    if (TASER_IN(i * N + j, N * N) && TASER_IN(j, i + 1))
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(T + i * N + j) : "memory");
+    TASER_CHECKED(TASER_IN(i * N + j, N * N) && TASER_IN(j, i + 1))
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(T + i * N + j) : "memory");
     j += 32;
     while (j > i) {
       j -= i + 1;
@@ -76,8 +76,8 @@ __device__ __forceinline__ void stage_T(float* slot, const float* T, const float
   }
   for (int k = lane; k < N; k += 32) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(slot + N * N + k);
-    if (TASER_IN(N * N + k, kSlotFloats))
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(D + k) : "memory");
+    TASER_CHECKED(TASER_IN(N * N + k, kSlotFloats))
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(D + k) : "memory");
   }
   asm volatile("cp.async.commit_group;" ::: "memory");
   asm volatile("cp.async.wait_all;" ::: "memory");
@@ -279,10 +279,9 @@ __device__ __forceinline__ void store_full(float* out, const Acc& acc, int N, fl
         const int rr = bucket_to_real(r, N, kNB);
         if (rr < 0 || c >= N - 1) continue;
         const bool zero = !UTC::has_tile(M, n) || (M < kMT - 1 && n == 2 * M + 1 && e < 2);
-        if (TASER_IN(rr * N + c, N * N)) out[(int64_t)rr * N + c] = zero ? 0.f : acc[M][n][e];
+        TASER_CHECKED(TASER_IN(rr * N + c, N * N)) out[(int64_t)rr * N + c] = zero ? 0.f : acc[M][n][e];
       }
-  for (int rr = L.lane; rr < N; rr += 32)
-    if (TASER_IN(rr * N + N - 1, N * N)) out[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+  for (int rr = L.lane; rr < N; rr += 32) TASER_CHECKED(TASER_IN(rr * N + N - 1, N * N)) out[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
 }
 
 __device__ __forceinline__ void load_full(const float* in, Acc& acc, int N, const LaneGeom& L) {
@@ -296,7 +295,7 @@ __device__ __forceinline__ void load_full(const float* in, Acc& acc, int N, cons
         const int rr = bucket_to_real(r, N, kNB);
         const bool live = UTC::has_tile(M, n) && !(M == kMT - 1 && e >= 2) &&
                           !(M < kMT - 1 && n == 2 * M + 1 && e < 2);
-        acc[M][n][e] = (live && rr >= 0 && c < N - 1 && TASER_IN(rr * N + c, N * N)) ? in[(int64_t)rr * N + c] : 0.f;
+        acc[M][n][e] = (live && rr >= 0 && c < N - 1 TASER_AND(TASER_IN(rr * N + c, N * N))) ? in[(int64_t)rr * N + c] : 0.f;
       }
 }
 
@@ -368,9 +367,8 @@ unfolded_tc_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, c
   const float inv = inv_norm[inst];
   const int n_ckpt = (t_max + c - 1) / c;
   for (int t = 0; t < t_max; ++t) {
-    if (t % c == 0 && ckpt != nullptr && TASER_IN(inst * n_ckpt + t / c, batch * n_ckpt))
-      store_full(ckpt + (inst * n_ckpt + t / c) * (int64_t)N * N, acc, N, DN, L);
-    tc_step<FP16>(acc, bf, tN2, TASER_IN(t, t_max) ? -2.f * alpha_t[t] * inv : 0.f, DN, L);
+    if (t % c == 0 && ckpt != nullptr TASER_AND(TASER_IN(inst * n_ckpt + t / c, batch * n_ckpt))) store_full(ckpt + (inst * n_ckpt + t / c) * (int64_t)N * N, acc, N, DN, L);
+    tc_step<FP16>(acc, bf, tN2, -2.f * alpha_t[t] * inv, DN, L);
     tc_prox(acc, red, Down, L);
   }
   if (L.g == 0) {
@@ -379,9 +377,8 @@ unfolded_tc_forward_kernel(int64_t batch, int N, const float* __restrict__ Tt, c
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
         const int cc = 8 * n + 2 * L.tq + p;
-        if (cc < N - 1 && TASER_IN(inst * (N - 1) + cc, batch * (N - 1))) {
+        if (cc < N - 1 TASER_AND(TASER_IN(inst * (N - 1) + cc, batch * (N - 1)))) {
           const float x = acc[kMT - 1][n][p];
-          TASER_FINITE(x);
           soft[inst * (N - 1) + cc] = Drow[n][p] > 0.f ? x / Drow[n][p] : 0.f;
           if (s_hat != nullptr) s_hat[inst * (N - 1) + cc] = x >= 0.f ? int8_t(1) : int8_t(-1);
         }
@@ -422,8 +419,7 @@ unfolded_tc_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, 
       for (int p = 0; p < 2; ++p) {
         const int cc = 8 * n + 2 * L.tq + p;
         const float Dc = cc < N - 1 ? its[N * N + cc] : 0.f;
-        lbar[kMT - 1][n][p] =
-            Dc > 0.f && TASER_IN(inst * (N - 1) + cc, batch * (N - 1)) ? grad_soft[inst * (N - 1) + cc] / Dc : 0.f;
+        lbar[kMT - 1][n][p] = Dc > 0.f TASER_AND(TASER_IN(inst * (N - 1) + cc, batch * (N - 1))) ? grad_soft[inst * (N - 1) + cc] / Dc : 0.f;
       }
   }
   // The adjoint is linear in Lbar, so it runs on Lbar 2^-e with e the exponent of the
@@ -450,17 +446,17 @@ unfolded_tc_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, 
   for (int kc = n_ckpt - 1; kc >= 0; --kc) {
     const int t0 = kc * c, t1 = min(t0 + c, t_max);
     Acc acc;
-    if (TASER_IN(inst * n_ckpt + kc, batch * n_ckpt)) load_full(ckpt + (inst * n_ckpt + kc) * (int64_t)N * N, acc, N, L);
+    TASER_CHECKED(TASER_IN(inst * n_ckpt + kc, batch * n_ckpt)) load_full(ckpt + (inst * n_ckpt + kc) * (int64_t)N * N, acc, N, L);
     put_iter(its, acc, L.lane);
     for (int s = t0 + 1; s < t1; ++s) {   // recompute L~(t0+1) .. L~(t1-1)
       tc_step<FP16>(acc, bf, tN2, -2.f * alpha_t[s - 1] * inv, DN, L);
       tc_prox(acc, red, Down, L);
-      if (TASER_IN(s - t0, c)) put_iter(its + (size_t)(s - t0) * kNE * 32, acc, L.lane);
+      TASER_CHECKED(TASER_IN(s - t0, c)) put_iter(its + (size_t)(s - t0) * kNE * 32, acc, L.lane);
     }
     for (int s = t1; s > t0; --s) {       // step s maps L~(s-1) -> L~(s) with tau_s
       const float tau = alpha_t[s - 1] * inv;
       Acc lp, v;
-      get_iter(its + (size_t)(TASER_IN(s - 1 - t0, c) ? s - 1 - t0 : 0) * kNE * 32, lp, L.lane);
+      TASER_CHECKED(TASER_IN(s - 1 - t0, c)) get_iter(its + (size_t)(s - 1 - t0) * kNE * 32, lp, L.lane);
 #pragma unroll
       for (int M = 0; M < kMT; ++M)
 #pragma unroll
@@ -491,10 +487,7 @@ unfolded_tc_backward_kernel(int64_t batch, int N, const float* __restrict__ Tt, 
       const float fb = fa * rn * proj;
       const float tb = (fa * (tot[2] - tot[1]) - fb * (tot[3] - tot[0])) / tau;   // <Vbar, G>
       const float taubar = -warp_sum(tb) * gup;
-      if (L.lane == 0 && TASER_IN(inst * t_max + (s - 1), batch * t_max)) {
-        grad_tau[inst * t_max + (s - 1)] = taubar;
-        TASER_FINITE(taubar);
-      }
+      if (L.lane == 0 TASER_AND(TASER_IN(inst * t_max + (s - 1), batch * t_max))) grad_tau[inst * t_max + (s - 1)] = taubar;
       float own[2] = {fa, fb};
       float ab[2][2 * kNT];
       col_bcast<2>(red + 8 * kRedRows(4), own, ab, L);
