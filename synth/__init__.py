@@ -126,21 +126,26 @@ def make_uneven(n, seed=0, shapes=UNEVEN_SHAPES, snr_range=(4.0, 16.0), t_max_ch
             "shapes": tuple(shapes)}
 
 
-def make_mimo_device(n, B, U, snr_db, constellation="qpsk", seed=0, device="cuda"):
+def make_mimo_device(n, B, U, snr_db, constellation="qpsk", seed=0, device="cuda", generator=None):
     """make_mimo's recipe drawn on a CUDA device with a seeded torch generator, for
     workloads that need fresh instances at every step (a different random stream from
     make_mimo's PCG64, same distributions).
 
-    snr_db: a scalar, or a (lo, hi) pair for SNRs drawn uniformly per instance.  Returns
-    H complex64 [n, B, U], y complex64 [n, B] and the transmitted signs int8 [n, M] in
-    decision order (BPSK: M = U; QPSK: real parts then imaginary parts, M = 2U), all on
-    the device.
+    snr_db: a scalar, or a (lo, hi) pair for SNRs drawn uniformly per instance.  generator:
+    a torch CUDA generator to draw from (then `seed` is unused; its state advances, which
+    also keeps the draw capturable in a CUDA graph with the default generator), or None for
+    a fresh generator seeded with `seed`.  Returns H complex64 [n, B, U], y complex64 [n, B]
+    and the transmitted signs int8 [n, M] in decision order (BPSK: M = U; QPSK: real parts
+    then imaginary parts, M = 2U), all on the device.
     """
     import torch
     if constellation not in ("bpsk", "qpsk"):
         raise ValueError("constellation must be 'bpsk' or 'qpsk'")
-    gen = torch.Generator(device=device)
-    gen.manual_seed(int(seed))
+    if generator is not None:
+        gen = generator
+    else:
+        gen = torch.Generator(device=device)
+        gen.manual_seed(int(seed))
     half = 0.5 ** 0.5
 
     def cn(shape):
