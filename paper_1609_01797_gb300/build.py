@@ -17,7 +17,7 @@ LIBDIR = os.path.join(PKG, "lib")
 LIB = os.path.join(LIBDIR, "libtaser.so")
 LIB_DEBUG = os.path.join(LIBDIR, "libtaser_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["taser_api.cu", "build_T.cu", "spectral.cu", "detect_fp32.cu", "detect_tc.cu", "detect_tc64.cu", "detect_fx14.cu", "static_scratch.cu", "unfolded.cu", "unfolded_tc.cu", "uneven.cu"]
+SOURCES = ["taser_api.cu", "build_T.cu", "spectral.cu", "detect_fp32.cu", "detect_tc.cu", "detect_fx14.cu", "static_scratch.cu", "unfolded.cu", "unfolded_tc.cu", "uneven.cu"]
 
 
 def _nvcc():

@@ -532,18 +532,305 @@ static cudaError_t launch_tc(int64_t batch, int N, const float* Tt, const float*
   return launch_tc_src<NB, FP16, DenseSource, MON>(src, batch, fit, literal, slot_floats, ascent_tol, st);
 }
 
-cudaError_t detect_tc64(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
-                        int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st);
-cudaError_t detect_tc64_queue(bool fp16, const Queue& q, int blocks_per_sm, const float* T_pool, const float* D_pool,
-                              const float* tau, int literal, float* L_pool, int8_t* s_pool, uint32_t* flags,
-                              cudaStream_t st);
+// ---------------------------------------------------------------------------------
+// The transposed form at 34 <= N <= 65 (bucket 64), one warp per instance.  The 24 tiles of
+// V^T (96 accumulators a lane) and the 16 A fragments of T^ (64 registers) stay in
+// registers.  The B operand goes through shared memory: every step the lane packs and
+// transposes the 44 nonzero 8 x 8 blocks of L~^T it holds (movmatrix.trans) into the warp's
+// block grid, and each group of mma loads its two B registers from there just before use.
+// T^, D and tau are read from global memory once per job (no staging slot, so the block
+// grid is the only shared memory).  No step needs another warp: the column norms are sums
+// over the 4 lanes of a row, as in the bucket-32 kernel.
+// ---------------------------------------------------------------------------------
+constexpr int kBlk64Words = 8 * 9 * 32;   // block grid [kb][ib][lane] of one warp (kb <= ib used)
+
+template <bool FP16, class Src>
+__global__ void __launch_bounds__(128, 2)
+detect_tct64_kernel(Src src, int literal, int slot_floats) {
+  using C = TctCfg<64>;
+  constexpr int MT = C::MT, KT = C::KT, NT = C::NT, NB = 64;
+  extern __shared__ __align__(16) float smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tq = lane & 3;
+  // Per warp: the block grid, then the staging slot of the next job and two job records.
+  uint32_t* const blk = reinterpret_cast<uint32_t*>(smem) + warp * (kBlk64Words + slot_floats + kTcRecFloats);
+  float* const slot = reinterpret_cast<float*>(blk + kBlk64Words);
+  auto bw = [&](int kb, int ib) -> uint32_t& { return blk[(kb * 9 + ib) * 32 + lane]; };
+  struct JobOut {
+    float* L;
+    int8_t* s;
+    uint32_t* flag;
+    double* obj;
+    int N, t_max, shift;
+  };
+  static_assert(2 * sizeof(JobOut) <= kTcRecFloats * sizeof(float), "job records must fit");
+  JobOut* outs = reinterpret_cast<JobOut*>(slot + slot_floats);
+  auto park = [&](const Job& jb, int shift, int which) {
+    if (lane == 0) outs[which] = JobOut{jb.L, jb.s, jb.flag, nullptr, jb.N, jb.t_max, shift};
+  };
+  // Inside a diagonal 8 x 8 block, element (row g, column 2tq + p) lies below the
+  // diagonal of V^T (i < k) iff 2tq + p < g.
+  const bool lo0 = 2 * tq < g, lo1 = 2 * tq + 1 < g;
+  Cursor<Src> cursor;
+  int cur_m = 0;
+  bool have;
+  {
+    Job first;
+    double* ob = nullptr;
+    have = cursor.next(src, first, ob, lane);
+    if (have) park(first, stage_job(slot, first, lane, slot_floats), 0);
+  }
+  while (have) {
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    const int N = outs[cur_m].N, t_max = outs[cur_m].t_max;
+    const float* T = slot + outs[cur_m].shift;
+    const float* Di = slot + N * N + 4;
+    const float m2tau = -2.f * Di[N];
+    auto tval = [&](int k, int j) -> float {  // T^ at bucket indices (k, j < NB)
+      return (k < N - 1 && j < N - 1) ? m2tau * T[k * N + j] : 0.f;
+    };
+    // A operand: T^ rows k = 16M + g (+8), columns j = 16kt + 2tq (+1, +8, +9).
+    uint32_t af[MT][KT][4];
+#pragma unroll
+    for (int M = 0; M < MT; ++M)
+#pragma unroll
+      for (int kt = 0; kt < KT; ++kt) {
+        const int r = 16 * M + g, c = 16 * kt + 2 * tq;
+        af[M][kt][0] = pack2<FP16>(tval(r, c), tval(r, c + 1));
+        af[M][kt][1] = pack2<FP16>(tval(r + 8, c), tval(r + 8, c + 1));
+        af[M][kt][2] = pack2<FP16>(tval(r, c + 8), tval(r, c + 9));
+        af[M][kt][3] = pack2<FP16>(tval(r + 8, c + 8), tval(r + 8, c + 9));
+      }
+    // This lane's rows k = 16M + g + 8h: T^[k][N] (FP32, the j = N term) and D_k.
+    float tkN[MT][2], Dk[MT][2];
+#pragma unroll
+    for (int M = 0; M < MT; ++M)
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * M + g + 8 * h;
+        tkN[M][h] = k < N - 1 ? m2tau * T[k * N + N - 1] : 0.f;
+        Dk[M][h] = k < N - 1 ? Di[k] : 0.f;
+      }
+    const float tnNN = m2tau * T[(N - 1) * N + (N - 1)];
+    const float DN = Di[N - 1];
+    // L~(0) = D in the V^T layout: element (M, n, e) is k = 16M + g + 8(e >> 1),
+    // i = 8n + 2tq + (e & 1).
+    float acc[MT][NT][4];
+#pragma unroll
+    for (int M = 0; M < MT; ++M)
+#pragma unroll
+      for (int n = 0; n < NT; ++n)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int k = 16 * M + g + 8 * (e >> 1), i = 8 * n + 2 * tq + (e & 1);
+          acc[M][n][e] = (C::has_tile(M, n) && i == k && k < N - 1) ? Dk[M][e >> 1] : 0.f;
+        }
+    __syncwarp();  // every lane has read the slot
+    bool have_next;
+    {
+      Job nxt;
+      double* ob = nullptr;
+      have_next = cursor.next(src, nxt, ob, lane);
+      if (have_next) park(nxt, stage_job(slot, nxt, lane, slot_floats), cur_m ^ 1);
+    }
+    float LNN = DN;
+    uint32_t fl = 0;
+
+    for (int t = 0; t < t_max; ++t) {
+      // V_NN partial sum_{j < N} T^[N][j] L~[N][j] from the old row N (lanes tq == 0).
+      float part = 0.f;
+      if (tq == 0) {
+#pragma unroll
+        for (int M = 0; M < MT; ++M)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) part = fmaf(tkN[M][h], acc[M][NT - 1][2 * h], part);
+      }
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 4);
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 8);
+      part += __shfl_xor_sync(TASER_FULL_MASK, part, 16);
+      part = __shfl_sync(TASER_FULL_MASK, part, lane & 28);
+      // The old iterate as B blocks: block (kb, ib) of L~^T transposed, for kb <= ib.
+      __syncwarp();   // the previous step's B loads are done before the grid is rewritten
+#pragma unroll
+      for (int kb = 0; kb < 2 * MT; ++kb)
+#pragma unroll
+        for (int ib = kb; ib < NT; ++ib)
+          bw(kb, ib) = movmatrix_trans(pack2<FP16>(acc[kb / 2][ib][2 * (kb % 2)], acc[kb / 2][ib][2 * (kb % 2) + 1]));
+      __syncwarp();
+      // Products, row N's n-tile first; each (kt, n) B fragment serves every m-tile.
+#pragma unroll
+      for (int n = NT - 1; n >= 0; --n)
+#pragma unroll
+        for (int kt = 0; kt <= C::ktmax(n); ++kt) {
+          const uint32_t b[2] = {bw(2 * kt, n), 2 * kt + 1 <= n ? bw(2 * kt + 1, n) : 0u};
+#pragma unroll
+          for (int M = 0; M < MT; ++M) {
+            if (!C::has_tile(M, n)) continue;
+            mma16816<FP16>(acc[M][n], af[M][kt], b);
+          }
+        }
+      // j = N term of column NB: V^T[k][N] += T^[k][N] L~_NN.
+      if (tq == 0) {
+#pragma unroll
+        for (int M = 0; M < MT; ++M)
+#pragma unroll
+          for (int h = 0; h < 2; ++h) acc[M][NT - 1][2 * h] = fmaf(tkN[M][h], LNN, acc[M][NT - 1][2 * h]);
+      }
+      const float vnn = fmaf(LNN, tnNN, LNN) + part;
+      // Keep V^T on and above its diagonal.
+#pragma unroll
+      for (int M = 0; M < MT; ++M) {
+        if (lo0) acc[M][2 * M][0] = 0.f;
+        if (lo1) acc[M][2 * M][1] = 0.f;
+        acc[M][2 * M][2] = 0.f;
+        acc[M][2 * M][3] = 0.f;
+        if (lo0) acc[M][2 * M + 1][2] = 0.f;
+        if (lo1) acc[M][2 * M + 1][3] = 0.f;
+      }
+      if (vnn <= 0.f) fl |= TASER_FLAG_LNN_SIGN;
+      if (literal) LNN = vnn >= 0.f ? DN : -DN;
+      // prox: squared norms of this lane's 8 rows k, summed over the 4 lanes of a row.
+      float sn[MT][2];
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          uint64_t v2 = 0ull;
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            if (!C::has_tile(M, n) || (n == 2 * M && h == 1)) continue;   // the cleared block
+            const uint64_t x = f2pack(acc[M][n][2 * h], acc[M][n][2 * h + 1]);
+            v2 = f2fma(x, x, v2);
+          }
+          float a, b;
+          f2unpack(v2, a, b);
+          sn[M][h] = a + b;
+        }
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sn[M][h] += __shfl_xor_sync(TASER_FULL_MASK, sn[M][h], 1);
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) sn[M][h] += __shfl_xor_sync(TASER_FULL_MASK, sn[M][h], 2);
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          float sc = 0.f;
+          if (sn[M][h] > 0.f) {
+            sc = Dk[M][h] * rsqrtf(sn[M][h]);
+          } else if (16 * M + g + 8 * h < N - 1) {
+            fl |= TASER_FLAG_ZERO_COLUMN;
+          }
+          const uint64_t sc2 = f2pack(sc, sc);
+#pragma unroll
+          for (int n = 0; n < NT; ++n) {
+            if (!C::has_tile(M, n) || (n == 2 * M && h == 1)) continue;
+            TASER_PAIR_APPLY(acc[M][n], 2 * h, f2mul(_x, sc2));
+          }
+        }
+    }
+
+    const JobOut o = outs[cur_m];
+    // Decisions from row N of L~ (column NB of L~^T, lanes tq == 0).
+    if (tq == 0) {
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = 16 * M + g + 8 * h;
+          if (k < N - 1 TASER_AND(TASER_IN(k, N - 1))) {
+            float r = acc[M][NT - 1][2 * h];
+            if (literal && LNN < 0.f) r = -r;
+            o.s[k] = r >= 0.f ? int8_t(1) : int8_t(-1);
+          }
+        }
+    }
+    if (o.L != nullptr) {
+      float* Lo = o.L;
+#pragma unroll
+      for (int M = 0; M < MT; ++M)
+#pragma unroll
+        for (int n = 0; n < NT; ++n)
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int k = 16 * M + g + 8 * (e >> 1), i = 8 * n + 2 * tq + (e & 1);
+            const int rr = bucket_to_real(i, N, NB);
+            if (rr < 0 || k >= N - 1) continue;
+            TASER_CHECKED(TASER_IN(rr * N + k, N * N)) Lo[(int64_t)rr * N + k] = C::has_tile(M, n) ? acc[M][n][e] : 0.f;
+          }
+      for (int rr = lane; rr < N; rr += 32)
+        TASER_CHECKED(TASER_IN(rr * N + N - 1, N * N)) Lo[(int64_t)rr * N + (N - 1)] = rr == N - 1 ? LNN : 0.f;
+    }
+#pragma unroll
+    for (int ofs = 16; ofs > 0; ofs >>= 1) fl |= __shfl_xor_sync(TASER_FULL_MASK, fl, ofs);
+    if (lane == 0 && o.flag != nullptr && fl) *o.flag |= fl;
+    __syncwarp();  // the record of this job is consumed before it is reused
+    cur_m ^= 1;
+    have = have_next;
+  }
+}
+
+template <bool FP16, class Src>
+static cudaError_t launch_tct64_src(const Src& src, int64_t jobs, int blocks_per_sm, int literal, cudaStream_t st) {
+  const int slot_floats = tc_slot_floats(65);
+  const size_t smem = (size_t)4 * (kBlk64Words + slot_floats + kTcRecFloats) * sizeof(uint32_t);
+  int dev = 0, sms = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(detect_tct64_kernel<FP16, Src>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tct64_kernel<FP16, Src>, 128, smem);
+  if (e != cudaSuccess) return e;
+  const int per_sm = blocks_per_sm > 0 && blocks_per_sm < fit ? blocks_per_sm : (fit > 0 ? fit : 1);
+  const int64_t need = (jobs + 3) / 4;
+  const int64_t resident = (int64_t)sms * per_sm;
+  const int64_t blocks = jobs >= 0 && need < resident ? need : resident;
+  detect_tct64_kernel<FP16, Src><<<(unsigned)blocks, 128, smem, st>>>(src, literal, slot_floats);
+  return cudaGetLastError();
+}
+
+template <bool FP16>
+static cudaError_t launch_tct64(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
+                                int literal, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
+  const size_t smem = (size_t)4 * (kBlk64Words + tc_slot_floats(65) + kTcRecFloats) * sizeof(uint32_t);
+  int dev = 0, sms = 0, fit = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(detect_tct64_kernel<FP16, DenseSource>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&fit, detect_tct64_kernel<FP16, DenseSource>, 128, smem);
+  if (e != cudaSuccess) return e;
+  const int64_t need = (batch + 3) / 4;
+  const int64_t resident = (int64_t)sms * (fit > 0 ? fit : 1);
+  DenseSource src;
+  src.batch = batch;
+  src.stride = (need < resident ? need : resident) * 4;
+  src.N = N;
+  src.t_max = t_max;
+  src.Tt = Tt;
+  src.Dg = D;
+  src.tau = tau;
+  src.L = L;
+  src.s = s;
+  src.flags = flags;
+  src.obj = nullptr;
+  return launch_tct64_src<FP16, DenseSource>(src, batch, fit, literal, st);
+}
+
 
 // Returns cudaErrorNotSupported when the bucket has no tensor-core kernel.
 cudaError_t detect_tc(int64_t batch, int N, const float* Tt, const float* D, const float* tau, int t_max,
                       int literal, bool fp16, float* L, int8_t* s, uint32_t* flags, cudaStream_t st) {
   switch (bucket_of(N)) {
     case 64:
-      return detect_tc64(batch, N, Tt, D, tau, t_max, literal, fp16, L, s, flags, st);
+      return fp16 ? launch_tct64<true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st)
+                  : launch_tct64<false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
     case 16:
       return fp16 ? launch_tc<16, true>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st)
                   : launch_tc<16, false>(batch, N, Tt, D, tau, t_max, literal, L, s, flags, st);
@@ -588,7 +875,8 @@ cudaError_t detect_tc_queue(int nb, bool fp16, const Queue& q, int blocks_per_sm
   const int slot_floats = tc_slot_floats(nb + 1);
   switch (nb) {
     case 64:
-      return detect_tc64_queue(fp16, q, blocks_per_sm, T_pool, D_pool, tau, literal, L_pool, s_pool, flags, st);
+      return fp16 ? launch_tct64_src<true>(src, -1, blocks_per_sm, literal, st)
+                  : launch_tct64_src<false>(src, -1, blocks_per_sm, literal, st);
     case 16:
       return fp16 ? launch_tc_src<16, true>(src, -1, blocks_per_sm, literal, slot_floats, 0.f, st)
                   : launch_tc_src<16, false>(src, -1, blocks_per_sm, literal, slot_floats, 0.f, st);

@@ -503,7 +503,6 @@ cudaError_t take_build_T(unsigned long long* out);
 cudaError_t take_spectral(unsigned long long* out);
 cudaError_t take_detect_fp32(unsigned long long* out);
 cudaError_t take_detect_tc(unsigned long long* out);
-cudaError_t take_detect_tc64(unsigned long long* out);
 cudaError_t take_detect_fx14(unsigned long long* out);
 cudaError_t take_unfolded(unsigned long long* out);
 cudaError_t take_unfolded_tc(unsigned long long* out);
@@ -521,7 +520,7 @@ taser_status taser_debug_report(uint64_t* fails, uint64_t* first, uint64_t* nonf
 #ifdef TASER_DEBUG
   using namespace taser::dbg;
   cudaError_t (*const takes[])(unsigned long long*) = {take_build_T,     take_spectral, take_detect_fp32,
-                                                        take_detect_tc,   take_detect_tc64, take_detect_fx14,
+                                                        take_detect_tc,   take_detect_fx14,
                                                         take_unfolded,    take_unfolded_tc, take_uneven};
   unsigned long long acc[3] = {0ull, 0ull, 0ull};
   for (auto take : takes) {
