@@ -124,7 +124,14 @@ const char* taser_last_error(void);
  *   tau       out, float [batch]; NULL skips the step size (then call
  *             taser_step_size with structure = kind).
  *   spec_norm out, float [batch] = ||T~||_2, or NULL.
- *   flags     out, uint32 [batch] (overwritten with ZERO_DIAG / NONFINITE bits), or NULL.
+ *   flags     out, uint32 [batch] (overwritten with ZERO_DIAG / NONFINITE bits, or with
+ *             TIMEOUT alone, see below), or NULL.
+ *
+ * QPSK with 16 users and an even B stages its antenna rows with the tensor memory
+ * accelerator.  Each wait for a staged chunk is bounded (about a second of SM clock).  An
+ * instance whose wait expires gets TASER_FLAG_TIMEOUT, and its T~, D, tau and spec_norm are
+ * left unwritten.  This cannot happen on a healthy device; the debug library's
+ * taser_debug_drop_copy provokes it for tests.
  *
  * QPSK symbols are taken as (+-1 +-j)/sqrt2: T is built from the effective channel
  * H/sqrt2 (or Y_r/sqrt2) so that the relaxed vector lies in {+-1}^N.  For JED the pilot
