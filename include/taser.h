@@ -129,9 +129,10 @@ const char* taser_last_error(void);
  *
  * QPSK with 16 users and an even B stages its antenna rows with the tensor memory
  * accelerator.  Each wait for a staged chunk is bounded (about a second of SM clock).  An
- * instance whose wait expires gets TASER_FLAG_TIMEOUT, and its T~, D, tau and spec_norm are
- * left unwritten.  This cannot happen on a healthy device; the debug library's
- * taser_debug_drop_copy provokes it for tests.
+ * instance whose wait expires gets TASER_FLAG_TIMEOUT and its T~ and D are left unwritten
+ * (tau and spec_norm, computed from them afterwards, are then meaningless for it).  This
+ * cannot happen on a healthy device; the debug library's taser_debug_drop_copy provokes it
+ * for tests.
  *
  * QPSK symbols are taken as (+-1 +-j)/sqrt2: T is built from the effective channel
  * H/sqrt2 (or Y_r/sqrt2) so that the relaxed vector lies in {+-1}^N.  For JED the pilot
