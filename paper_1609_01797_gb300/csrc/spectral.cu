@@ -64,17 +64,21 @@ struct SpecInt {
 // column is already eliminated: the rest is rounding residue far under FP32's resolution.
 constexpr float kTinyNorm2 = 0x1p-100f;
 
-// Sturm count: number of eigenvalues of the tridiagonal (sg*d, e) below sigma.
+// Sturm count: number of eigenvalues of the tridiagonal (sg*d, e) below sigma, as the
+// number of negative pivots q_j of the LDL^T factorisation of (sg*T - sigma I).  No pivot
+// guard sits in the recurrence: IEEE infinities carry a zero pivot through (Demmel, Dhillon
+// and Ren, 1995).  A pivot +0 yields -inf next (counted), -0 yields +inf, and the pivot
+// after an infinite one is finite again.  This needs e2 > 0 throughout (0 * inf would be a
+// NaN), so callers floor the squared off-diagonals at kTinyNorm2.  The count reads the sign
+// bit, so -0 counts as negative and +0 does not, matching the infinities they produce.
 template <int NP>
 __device__ __forceinline__ int sturm_count(const float (&d)[NP], const float (&e2)[NP], float sg, float sigma) {
-  const float pivmin = 1e-30f;
   float q = sg * d[0] - sigma;
-  int cnt = q < 0.f;
+  int cnt = (int)(__float_as_uint(q) >> 31);
 #pragma unroll
   for (int j = 1; j < NP; ++j) {
-    if (fabsf(q) < pivmin) q = -pivmin;
     q = (sg * d[j] - sigma) - __fdividef(e2[j - 1], q);
-    cnt += q < 0.f;
+    cnt += (int)(__float_as_uint(q) >> 31);
   }
   return cnt;
 }
@@ -255,6 +259,10 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
     lo = fmaxf(lo, dj);
     hi = fmaxf(hi, dj + r);
   }
+  // The Sturm count needs e2 > 0; the floor comes after the bracket, which it must not
+  // widen (the zero matrix keeps the norm 0).
+#pragma unroll
+  for (int j = 0; j < NP; ++j) e2[j] = fmaxf(e2[j], kTinyNorm2);
   const float inv_parts = 1.f / (float)parts;
 #pragma unroll 1
   for (int round = 0; round < rounds; ++round) {
@@ -485,6 +493,10 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
     lo = fmaxf(lo, d[j]);
     hi = fmaxf(hi, d[j] + r);
   }
+  // The Sturm count needs e2 > 0; the floor comes after the bracket, which it must not
+  // widen (the zero matrix keeps the norm 0).
+#pragma unroll
+  for (int j = 0; j < NP; ++j) e2[j] = fmaxf(e2[j], kTinyNorm2);
   const float inv_parts = 1.f / (float)(G + 1);
   const unsigned gmask = G == 32 ? 0xffffffffu : ((1u << G) - 1u);
 #pragma unroll 1
