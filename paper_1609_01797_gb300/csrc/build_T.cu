@@ -158,8 +158,10 @@ __device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
   return done != 0;
 }
 // Waits for the completion of the phase with the given parity; false once `budget` clock
-// cycles have passed without it.
+// cycles have passed without it.  A phase that has already completed costs one test and
+// no clock read.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget) {
+  if (mbar_test(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(bar, parity)) {
     if (clock64() - t0 > budget) return false;
