@@ -301,8 +301,9 @@ spectral_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha,
 // and smallest eigenvalues of T~ are those of M~, and ||T~||_2 = ||M~||_2.  M~ is read
 // from T~:  M~_ab = T~_ab + i T~_{U+a,b},  M~_{a,N} = T~_{a,2U} + i T~_{U+a,2U}.
 // Tridiagonalising the (U+1) complex matrix costs about 2.5x fewer flops and half the
-// sequential steps of the real (2U+1) one, and its UV = 16 trailing columns let two
-// instances share a warp.
+// sequential steps of the real (2U+1) one.  The one-column layout below (one lane per
+// trailing column) serves UV = 32; UV = 8 and 16 use the folded layout further down (two
+// columns per lane).
 // ---------------------------------------------------------------------------------
 template <int UV>
 struct HermCfg {
@@ -524,12 +525,275 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
   }
 }
 
+// Folded layout of the complex Householder for UV = 8 and 16: G = UV / 2 lanes per
+// instance (four instances per warp at UV = 16, eight at UV = 8).  Lane gl holds two
+// columns, ca = gl + 1 (1..UV/2) and cb = UV - gl (UV/2 + 1..UV).  The per-step scalar work
+// (reductions, reflector scalars, selects) is then shared by twice as many instances as in
+// the one-column layout, and one shared-memory read of v and w serves both columns.  From
+// step UV/2 on every ca column is finished, and those blocks drop it at compile time.  The
+// multisection evaluates two points per lane: the same UV points per round as the
+// one-column layout, so both layouts take the same bracket decisions on the same
+// tridiagonal.  Measured at QPSK 128x16: 0.183 -> 0.138 ms per 65,536 matrices (128
+// registers, 4 blocks per SM; at 3 blocks and 138 registers 0.150 ms).
+template <int UV>
+struct HermFoldCfg {
+  static constexpr int HALF = UV / 2;
+  static constexpr int G = HALF;               // lanes per instance
+  static constexpr int IPW = 32 / G;           // instances per warp
+  static constexpr int NP = UV + 1;
+  static constexpr int VB = (NP + 1) & ~1;
+  static constexpr int WARPS = 4;
+  static constexpr int IPC = WARPS * IPW;
+  static constexpr int INST_FLOATS = 8 * VB + 2 * VB;  // xd, wd ({re, re, im, im}), db, eb2
+  static constexpr int ROUNDS = UV == 16 ? 5 : 8;       // UV + 1 parts per round (as HermCfg)
+};
+
+template <int UV, bool NEG>
+__global__ void __launch_bounds__(128, 4)
+spectral_herm_fold_kernel(int64_t batch, int U, const float* __restrict__ Tt, float alpha, float* __restrict__ tau,
+                          float* __restrict__ nrm_out) {
+  using C = HermFoldCfg<UV>;
+  constexpr int NP = C::NP, VB = C::VB, G = C::G, HALF = C::HALF;
+  static_assert(HALF % KBLK_HERM == 0, "a Householder block must not straddle step UV / 2");
+  static_assert(HALF >= 2, "the trailing 2 x 2 block sits in the cb columns");
+  __shared__ __align__(16) float sm[C::IPC * C::INST_FLOATS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane % G;
+  const int local = warp * C::IPW + grp;
+  const int64_t inst = (int64_t)blockIdx.x * C::IPC + local;
+  const bool active = inst < batch;
+  float4* xd = reinterpret_cast<float4*>(sm + local * C::INST_FLOATS);
+  float4* wd = xd + VB;
+  float* db = reinterpret_cast<float*>(wd + VB);
+  float* eb2 = db + VB;
+  const int ca = gl + 1, cb = UV - gl;
+  float2 colA[NP], colB[NP];
+  float m00 = 0.f;
+  auto load = [&](auto u_c) {
+    const int Uc = u_c, N = 2 * Uc + 1;
+    const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
+    auto t = [&](int a, int b) -> float {
+      const float v = active && TASER_IN(inst * N * N + a * N + b, batch * N * N) ? T[a * N + b] : 0.f;
+      return NEG ? -v : v;
+    };
+    // M~[j][c] as in the one-column layout: users below min(UV, Uc), the augmented
+    // coordinate at index UV.
+    auto entry = [&](int j, int c) -> float2 {
+      const bool ju = j < UV && j < Uc, ja = j == UV;
+      const bool cu = c < UV && c < Uc, cx = c == UV;
+      if (ju && cu) return make_float2(t(j, c), t(Uc + j, c));
+      if (ju && cx) return make_float2(t(j, 2 * Uc), t(Uc + j, 2 * Uc));
+      if (ja && cu) return make_float2(t(c, 2 * Uc), -t(Uc + c, 2 * Uc));
+      if (ja && cx) return make_float2(t(2 * Uc, 2 * Uc), 0.f);
+      return make_float2(0.f, 0.f);
+    };
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      colA[j] = entry(j, ca);
+      colB[j] = entry(j, cb);
+    }
+    m00 = Uc >= 1 ? t(0, 0) : 0.f;
+  };
+  if (U == UV) load(SpecInt<UV>{});
+  else load(U);
+  float amax = fabsf(m00);
+#pragma unroll
+  for (int j = 0; j < NP; ++j)
+    amax = fmaxf(fmaxf(amax, fmaxf(fabsf(colA[j].x), fabsf(colA[j].y))),
+                 fmaxf(fabsf(colB[j].x), fabsf(colB[j].y)));
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(TASER_FULL_MASK, amax, o));
+  const int ex = scale_exponent(amax);
+  {
+    const float sc = pow2f(-ex);
+    m00 *= sc;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) {
+      colA[j] = make_float2(colA[j].x * sc, colA[j].y * sc);
+      colB[j] = make_float2(colB[j].x * sc, colB[j].y * sc);
+    }
+  }
+  for (int i = gl; i < VB; i += G) {
+    xd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+    wd[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  if (gl == 0) db[0] = m00;
+  __syncwarp();
+
+  static_for_blocks<UV, KBLK_HERM>([&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    constexpr int KE = (KB + KBLK_HERM < UV - 1) ? KB + KBLK_HERM : UV - 1;   // k in [KB, KE)
+    constexpr bool LIVE_A = KB < HALF;   // k < UV / 2 throughout the block: some ca > k
+#pragma unroll 1
+    for (int k = KB; k < KE; ++k) {
+      // Row k of both columns: x_c = conj(M[k][c]) for c > k.  ckA also gives the diagonal
+      // M[k][k] when ca == k (k <= UV / 2).
+      float2 ckA = make_float2(0.f, 0.f), ckB = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = KB; r < KE; ++r) {
+        ckA = (r == k) ? colA[r] : ckA;
+        ckB = (r == k) ? colB[r] : ckB;
+      }
+      const bool liveA = LIVE_A && ca > k, liveB = cb > k;
+      const float2 xcA = make_float2(ckA.x, -ckA.y), xcB = make_float2(ckB.x, -ckB.y);
+      float sig2 = (liveA ? fmaf(ckA.x, ckA.x, ckA.y * ckA.y) : 0.f) + (liveB ? fmaf(ckB.x, ckB.x, ckB.y * ckB.y) : 0.f);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) sig2 += __shfl_xor_sync(TASER_FULL_MASK, sig2, o);
+      // x_{k+1}: column k + 1 is ca of lane k (k + 1 <= UV / 2) or cb of lane UV - 1 - k.
+      const bool x1_in_a = k + 1 <= HALF;
+      const int src = grp * G + (x1_in_a ? k : UV - 1 - k);
+      const float sx = x1_in_a ? xcA.x : xcB.x, sy = x1_in_a ? xcA.y : xcB.y;
+      const float2 x1 = make_float2(__shfl_sync(TASER_FULL_MASK, sx, src), __shfl_sync(TASER_FULL_MASK, sy, src));
+      const bool refl = sig2 >= kTinyNorm2;
+      const float sig = refl ? sig2 * rsqrtf(sig2) : 0.f;
+      const float n1 = fmaf(x1.x, x1.x, x1.y * x1.y);
+      const bool big1 = n1 >= kTinyNorm2;
+      const float r1 = big1 ? rsqrtf(n1) : 0.f;
+      const float2 ph = big1 ? make_float2(x1.x * r1, x1.y * r1) : make_float2(1.f, 0.f);
+      const float ax1 = big1 ? n1 * r1 : x1.x;
+      const float2 v1 = make_float2(fmaf(ph.x, sig, x1.x), fmaf(ph.y, sig, x1.y));
+      const float vv2 = 2.f * sig * (sig + ax1);
+      const float beta = refl ? __fdividef(2.f, vv2) : 0.f;
+      const float2 vcA = liveA ? (ca == k + 1 ? v1 : xcA) : make_float2(0.f, 0.f);
+      const float2 vcB = liveB ? (cb == k + 1 ? v1 : xcB) : make_float2(0.f, 0.f);
+      if (LIVE_A && TASER_IN(ca, VB)) xd[ca] = make_float4(vcA.x, vcA.x, vcA.y, vcA.y);
+      if (TASER_IN(cb, VB)) xd[cb] = make_float4(vcB.x, vcB.x, vcB.y, vcB.y);
+      if (ca == k && TASER_IN(k, VB)) db[k] = ckA.x;
+      if (cb == k && TASER_IN(k, VB)) db[k] = ckB.x;
+      __syncwarp();
+      uint64_t AA = 0ull, AB = 0ull, BA = 0ull, BB = 0ull;
+#pragma unroll
+      for (int j = KB + 1; j < NP; ++j) {
+        const float4 q = xd[j];
+        const uint64_t X1 = f2pack(q.x, q.y), X2 = f2pack(q.z, q.w);
+        if constexpr (LIVE_A) {
+          const uint64_t Ma = f2pack(colA[j].x, colA[j].y);
+          AA = f2fma(Ma, X1, AA);
+          AB = f2fma(Ma, X2, AB);
+        }
+        const uint64_t Mb = f2pack(colB[j].x, colB[j].y);
+        BA = f2fma(Mb, X1, BA);
+        BB = f2fma(Mb, X2, BB);
+      }
+      float2 pA = make_float2(0.f, 0.f), pB;
+      if constexpr (LIVE_A) {
+        float ax, ay, bx, by;
+        f2unpack(AA, ax, ay);
+        f2unpack(AB, bx, by);
+        pA = liveA ? make_float2(beta * (ax + by), beta * (bx - ay)) : make_float2(0.f, 0.f);
+      }
+      {
+        float ax, ay, bx, by;
+        f2unpack(BA, ax, ay);
+        f2unpack(BB, bx, by);
+        pB = liveB ? make_float2(beta * (ax + by), beta * (bx - ay)) : make_float2(0.f, 0.f);
+      }
+      float kk = fmaf(vcA.x, pA.x, vcA.y * pA.y) + fmaf(vcB.x, pB.x, vcB.y * pB.y);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) kk += __shfl_xor_sync(TASER_FULL_MASK, kk, o);
+      kk *= 0.5f * beta;
+      const float2 wA = make_float2(fmaf(-kk, vcA.x, pA.x), fmaf(-kk, vcA.y, pA.y));
+      const float2 wB = make_float2(fmaf(-kk, vcB.x, pB.x), fmaf(-kk, vcB.y, pB.y));
+      if (LIVE_A && TASER_IN(ca, VB)) wd[ca] = make_float4(wA.x, wA.x, wA.y, wA.y);
+      if (TASER_IN(cb, VB)) wd[cb] = make_float4(wB.x, wB.x, wB.y, wB.y);
+      if (gl == 0 && TASER_IN(k, VB)) eb2[k] = sig2;                                  // |alpha|^2
+      __syncwarp();
+      const uint64_t nWaA = f2pack(-wA.x, wA.y), nWbA = f2pack(-wA.y, -wA.x);
+      const uint64_t nVaA = f2pack(-vcA.x, vcA.y), nVbA = f2pack(-vcA.y, -vcA.x);
+      const uint64_t nWaB = f2pack(-wB.x, wB.y), nWbB = f2pack(-wB.y, -wB.x);
+      const uint64_t nVaB = f2pack(-vcB.x, vcB.y), nVbB = f2pack(-vcB.y, -vcB.x);
+#pragma unroll
+      for (int j = KB + 1; j < NP; ++j) {
+        const float4 q = xd[j], u = wd[j];
+        const uint64_t Q1 = f2pack(q.x, q.y), Q2 = f2pack(q.z, q.w), U1 = f2pack(u.x, u.y), U2 = f2pack(u.z, u.w);
+        if constexpr (LIVE_A) {
+          uint64_t Ma = f2pack(colA[j].x, colA[j].y);
+          Ma = f2fma(Q1, nWaA, Ma);
+          Ma = f2fma(Q2, nWbA, Ma);
+          Ma = f2fma(U1, nVaA, Ma);
+          Ma = f2fma(U2, nVbA, Ma);
+          f2unpack(Ma, colA[j].x, colA[j].y);
+        }
+        uint64_t Mb = f2pack(colB[j].x, colB[j].y);
+        Mb = f2fma(Q1, nWaB, Mb);
+        Mb = f2fma(Q2, nWbB, Mb);
+        Mb = f2fma(U1, nVaB, Mb);
+        Mb = f2fma(U2, nVbB, Mb);
+        f2unpack(Mb, colB[j].x, colB[j].y);
+      }
+      __syncwarp();
+    }
+  });
+  // Trailing 2 x 2 block: columns UV - 1 and UV are cb of lanes 1 and 0.
+  if (cb == UV - 1) {
+    db[UV - 1] = colB[UV - 1].x;
+    eb2[UV - 1] = fmaf(colB[UV].x, colB[UV].x, colB[UV].y * colB[UV].y);
+  }
+  if (cb == UV) db[UV] = colB[UV].x;
+  __syncwarp();
+  float d[NP], e2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    d[j] = db[j];
+    e2[j] = j < UV ? eb2[j] : 0.f;
+  }
+  float lo = -3.0e38f, hi = -3.0e38f;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const float r = (j > 0 ? sqrtf(e2[j - 1]) : 0.f) + sqrtf(e2[j]);
+    lo = fmaxf(lo, d[j]);
+    hi = fmaxf(hi, d[j] + r);
+  }
+  // The Sturm count needs e2 > 0; the floor comes after the bracket, which it must not
+  // widen (the zero matrix keeps the norm 0).
+#pragma unroll
+  for (int j = 0; j < NP; ++j) e2[j] = fmaxf(e2[j], kTinyNorm2);
+  // One-sided multisection, UV + 1 parts: lane gl evaluates points 2 gl and 2 gl + 1
+  // (sigma_p = lo + (p + 1) step), the same 16 points as the one-column layout.
+  const float inv_parts = 1.f / (float)(UV + 1);
+  const unsigned gmask = (1u << G) - 1u;
+#pragma unroll 1
+  for (int round = 0; round < C::ROUNDS; ++round) {
+    const float step = (hi - lo) * inv_parts;
+    const float s0 = fmaf(step, (float)(2 * gl + 1), lo);
+    const float s1 = fmaf(step, (float)(2 * gl + 2), lo);
+    const int c0 = sturm_count<NP>(d, e2, 1.f, s0);
+    const int c1 = sturm_count<NP>(d, e2, 1.f, s1);
+    const unsigned m0 = (__ballot_sync(TASER_FULL_MASK, c0 == NP) >> (grp * G)) & gmask;
+    const unsigned m1 = (__ballot_sync(TASER_FULL_MASK, c1 == NP) >> (grp * G)) & gmask;
+    const int f0 = m0 ? 2 * (__ffs(m0) - 1) : 2 * G;
+    const int f1 = m1 ? 2 * (__ffs(m1) - 1) + 1 : 2 * G;
+    const int f = min(f0, f1);   // first point at or above lambda_max
+    if (f == 2 * G) {
+      lo = fmaf(step, (float)(2 * G), lo);
+    } else {
+      const float nhi = fmaf(step, (float)(f + 1), lo);
+      const float nlo = f == 0 ? lo : fmaf(step, (float)f, lo);
+      lo = nlo;
+      hi = nhi;
+    }
+  }
+  const float nrm = 0.5f * (lo + hi) * pow2f(ex);
+  if (active && gl == 0 && TASER_IN(inst, batch)) {
+    tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
+    if (nrm_out != nullptr) nrm_out[inst] = nrm;
+    TASER_FINITE(nrm);
+  }
+}
+
 template <int UV>
 static cudaError_t launch_herm(int64_t batch, int U, const float* Tt, bool neg, float alpha, float* tau,
                                float* nrm, cudaStream_t st) {
-  const int64_t blocks = (batch + HermCfg<UV>::IPC - 1) / HermCfg<UV>::IPC;
-  if (neg) spectral_herm_kernel<UV, true><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
-  else spectral_herm_kernel<UV, false><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+  if constexpr (UV <= 16) {
+    const int64_t blocks = (batch + HermFoldCfg<UV>::IPC - 1) / HermFoldCfg<UV>::IPC;
+    if (neg) spectral_herm_fold_kernel<UV, true><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+    else spectral_herm_fold_kernel<UV, false><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+  } else {
+    // UV = 32: two columns a lane would need about 130 registers for the matrix alone.
+    const int64_t blocks = (batch + HermCfg<UV>::IPC - 1) / HermCfg<UV>::IPC;
+    if (neg) spectral_herm_kernel<UV, true><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+    else spectral_herm_kernel<UV, false><<<(unsigned)blocks, 128, 0, st>>>(batch, U, Tt, alpha, tau, nrm);
+  }
   return cudaGetLastError();
 }
 
