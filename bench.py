@@ -994,7 +994,7 @@ def main():
             "peak_source": peak_src, "algorithmic_bytes_per_launch": n * build_bytes_per_instance(B, U, N),
             "ms_per_launch": head["build_ms"]}),
         "spectral": (head["spectral_ms"], {
-            "kernel": "spectral_herm_kernel<16> (Householder + Sturm)", "bound": "alu", "achieved": spec_tf,
+            "kernel": "spectral_herm_fold_kernel<16> (Householder, two columns a lane, + Sturm)", "bound": "alu", "achieved": spec_tf,
             "peak": fp32_peak, "unit": "TFLOP/s", "frac": spec_tf / fp32_peak, "traffic": tr("spectral"),
             "peak_source": "derived FP32 pipe", "algorithmic_flops_per_launch": n * spectral_flops_per_instance(U),
             "ms_per_launch": head["spectral_ms"]}),
