@@ -138,7 +138,7 @@ struct TmaCfg {
 };
 static_assert(TmaCfg::NS * (TmaCfg::H_FLOATS + TmaCfg::Y_FLOATS) <= TmaCfg::WARP_FLOATS, "ring must fit");
 static_assert((TmaCfg::WARP_FLOATS * 4) % 1024 == 0, "swizzled boxes need 1 KB alignment");
-static_assert(33 * 33 + 144 <= TmaCfg::WARP_FLOATS, "epilogue scratch must fit the ring");
+static_assert(33 * 33 + 3 + 144 <= TmaCfg::WARP_FLOATS, "epilogue scratch (tile, its offset, D) must fit the ring");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint32_t bar, unsigned count) {
@@ -684,9 +684,15 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   const float dsg = jed ? -1.f : 1.f;   // sign of T_aa
   auto scatter_and_store = [&](auto nu_c, auto nr_c) {
     const int NU = nu_c, Nr = nr_c;
-    // Ts[a] = v (a debug build checks a against the N x N tile).
+    // The tile starts `mis` floats into the staging area, mis = (address of the instance's
+    // T~ / 4) mod 4, so that its 16-byte groups coincide in shared and global memory and
+    // the copy-out runs as 16-byte loads and stores between a scalar head and tail.
+    float* To = Tt + inst * (int64_t)Nr * Nr;
+    const int mis = (int)((reinterpret_cast<uintptr_t>(To) >> 2) & 3u);
+    float* Tsm = Ts + mis;
+    // Tsm[a] = v (a debug build checks a against the N x N tile).
     auto put = [&](int a, float v) {
-      if (TASER_IN(a, Nr * Nr)) Ts[a] = v;
+      if (TASER_IN(a, Nr * Nr)) Tsm[a] = v;
     };
 #pragma unroll
     for (int i = 0; i < MT; ++i)
@@ -746,10 +752,23 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
         }
       }
     __syncwarp();
-    float* To = Tt + inst * (int64_t)Nr * Nr;
-    for (int e = lane; e < Nr * Nr; e += 32) {
-      if (TASER_IN(inst * Nr * Nr + e, batch * Nr * Nr)) To[e] = Ts[e];
-      TASER_FINITE(Ts[e]);
+    const int e0 = (4 - mis) & 3;                 // first entry on a 16-byte boundary
+    const int nvec = (Nr * Nr - e0) >> 2;
+    const int e1 = e0 + 4 * nvec;                 // first entry of the scalar tail
+    if (lane < e0 || (lane >= 4 && lane - 4 < Nr * Nr - e1)) {
+      const int e = lane < e0 ? lane : e1 + lane - 4;
+      if (TASER_IN(inst * Nr * Nr + e, batch * Nr * Nr)) To[e] = Tsm[e];
+      TASER_FINITE(Tsm[e]);
+    }
+    const float4* src4 = reinterpret_cast<const float4*>(Tsm + e0);
+    float4* dst4 = reinterpret_cast<float4*>(To + e0);
+    for (int v = lane; v < nvec; v += 32) {
+      const float4 x = src4[v];
+      if (TASER_IN(inst * Nr * Nr + e0 + 4 * v + 3, batch * Nr * Nr)) dst4[v] = x;
+      TASER_FINITE(x.x);
+      TASER_FINITE(x.y);
+      TASER_FINITE(x.z);
+      TASER_FINITE(x.w);
     }
     for (int a = lane; a < Nr; a += 32) {
       const int p = a == Nr - 1 ? MP - 1 : (qpsk && a >= NU ? a - NU : a);
@@ -770,7 +789,8 @@ template <int MP, int KIND>
 static cudaError_t launch_build(int kind, int64_t batch, int B, int P, int N, const float2* X, const float2* y,
                                 float* Tt, float* D, uint32_t* flags, cudaStream_t st) {
   using C = BuildCfg<MP>;
-  static_assert((2 * MP - 1) * (2 * MP - 1) + 144 <= C::WARP_FLOATS, "epilogue scratch must fit the staging buffers");
+  static_assert((2 * MP - 1) * (2 * MP - 1) + 3 + 144 <= C::WARP_FLOATS,
+                "epilogue scratch (tile, its offset, D) must fit the staging buffers");
   if (C::SMEM_BYTES > 48 * 1024) {
     cudaError_t e = cudaFuncSetAttribute(build_T_kernel<MP, KIND>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          C::SMEM_BYTES);
