@@ -47,12 +47,13 @@ def parse_args():
                                                                  "(--workload unfolded)")
     ap.add_argument("--unfolded-precision", choices=["fp32", "bf16_tc", "fp16_tc"], default="fp32",
                     help="arithmetic of the unfolded forward and adjoint products (--workload unfolded)")
-    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff", "unfolded", "ber"],
+    ap.add_argument("--workload", choices=["qpsk128x16", "uneven", "tradeoff", "unfolded", "ber", "jed"],
                     default="qpsk128x16",
                     help="uneven: 200,000 QPSK items with N in {9,17,33,65}, t_max in {10,20}; tradeoff: SNR "
                          "for 1%% VER vs throughput over t_max = 1..20 for 32x32 BPSK/QPSK; unfolded: training "
                          "steps of unfolded TASER on batches of 8,192; ber: BER per SNR point of the GPU paths "
-                         "against the FP64 oracle (none of these is the headline)")
+                         "against the FP64 oracle; jed: throughput of the JED BPSK path, B = 16, K = 16 and 32 "
+                         "(none of these is the headline)")
     return ap.parse_args()
 
 
@@ -557,6 +558,76 @@ def run_uneven(args):
     return 0
 
 
+def run_jed(args):
+    """Throughput of the whole SIMO JED BPSK path (Sec. II-B and III-C: build T~ = -D^-1 A^T A
+    D^-1 and D from Y, step size, Algorithm 1) at B = 16 receive antennas, K = 16 and 32
+    slots, t_max = 20, 131,072 device-resident instances per step, SNR cycling over 0..12 dB
+    in 2 dB steps: detections/s per path, the per-kernel split and the BER against the
+    transmitted symbols."""
+    import torch
+    import paper_1609_01797_gb300 as taser
+    from synth import make_jed
+    dev = torch.device("cuda", 0)
+    n = args.jed_instances
+    steps, warmup = args.steps, max(args.warmup, 3)
+    snr = np.tile(np.arange(0.0, 13.0, 2.0), n // 7 + 1)[:n]
+    result = {}
+    for K in (16, 32):
+        w = make_jed(n, 16, K, snr, seed=31_000 + K)
+        Y = torch.from_numpy(w["Y"]).to(dev)
+        truth = torch.from_numpy(w["s"][:, 1:].astype(np.int8)).to(dev)
+        N = taser.problem_size("jed_bpsk", K)
+        bufs = {"T_tilde": torch.empty((n, N, N), device=dev), "D": torch.empty((n, N), device=dev),
+                "tau": torch.empty((n,), device=dev), "flags": torch.zeros((n,), device=dev, dtype=torch.int32)}
+        s_hat = torch.empty((n, N - 1), device=dev, dtype=torch.int8)
+        stream = torch.cuda.current_stream(dev)
+        paths = {}
+        for precision in ("bf16_tc", "fp32"):
+            def one(ev=None):
+                if ev is not None:
+                    ev[0].record(stream)
+                taser.build_T("jed_bpsk", Y, None, ALPHA, out=bufs, with_tau=False)
+                if ev is not None:
+                    ev[1].record(stream)
+                taser.step_size(bufs["T_tilde"], ALPHA, structure="jed_bpsk", tau=bufs["tau"])
+                if ev is not None:
+                    ev[2].record(stream)
+                taser.detect(bufs["T_tilde"], bufs["D"], bufs["tau"], T_MAX, precision, want_L=False,
+                             flags=bufs["flags"], out_s=s_hat)
+                if ev is not None:
+                    ev[3].record(stream)
+            for _ in range(warmup):
+                one()
+            ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(steps)]
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize(dev)
+            a.record(stream)
+            for i in range(steps):
+                one(ev[i])
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ms = a.elapsed_time(b) / steps
+            split = [sum(e[k].elapsed_time(e[k + 1]) for e in ev) / steps for k in range(3)]
+            errs = int((s_hat != truth).sum().item())
+            nbits = n * (N - 1)
+            paths[precision] = {"det_per_s": n / (ms * 1e-3), "ms_per_step": ms, "build_ms": split[0],
+                                "spectral_ms": split[1], "detect_ms": split[2],
+                                "detect_only_det_per_s": n / (split[2] * 1e-3),
+                                "bit_errors": errs, "ber": errs / nbits,
+                                "ber_ci95": list(clopper_pearson(errs, nbits))}
+        result["K%d" % K] = {"N": N, "instances": n, "paths": paths}
+        del Y, truth, bufs, s_hat
+    head = result["K32"]["paths"]["bf16_tc"]
+    print(json.dumps({"metric": "TASER JED BPSK detections/s (whole path: build T~ and D from Y, step size, "
+                      "Algorithm 1), BF16 tensor-core path", "value": head["det_per_s"], "unit": "detections/s",
+                      "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": head["ms_per_step"],
+                      "higher_is_better": True, "dtype": "bf16", "data": "synthetic",
+                      "config": {"workload": "jed_bpsk_B16_K16_K32_tmax20_snr0-12dB", "instances": n, "t_max": T_MAX,
+                                 "alpha": ALPHA, "inputs": "device-resident, larger than L2"},
+                      "results": result}))
+    return 0
+
+
 def run_tradeoff(args):
     """Throughput vs the SNR needed for 1% VER as t_max goes from 1 to 20, for 32-user
     systems (B = 32, U = 32, BPSK N = 33 and QPSK N = 65): the GPU counterpart of the
@@ -819,6 +890,8 @@ def main():
         return run_unfolded(args)
     if args.workload == "ber":
         return run_ber(args)
+    if args.workload == "jed":
+        return run_jed(args)
 
     import torch
     import torch.distributed as dist

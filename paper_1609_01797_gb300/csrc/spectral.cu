@@ -807,11 +807,257 @@ cudaError_t spectral_qpsk(int64_t batch, int U, const float* Tt, int sign, float
   return launch_herm<32>(batch, U, Tt, neg, alpha, tau, nrm, st);
 }
 
+// Folded layout of the real Householder for NV = 8, 16 and 32: G = NV / 2 lanes per
+// instance (two instances per warp at NV = 32, four at 16, eight at 8).  Lane gl holds
+// columns ca = gl + 1 and cb = NV - gl as one packed pair (A[j][ca], A[j][cb]); v and w are
+// published as duplicated pairs (x_j, x_j), so one packed multiply-add per row serves both
+// columns of the reduction p = beta A v and two serve their rank-2 update.  A finished
+// column (c <= k) has v_c = w_c = 0 and its updates add zero.
+// The multisection keeps the one-column kernel's structure: one-sided, each lane evaluates
+// two of NV points (NV + 1 parts); two-sided, one point on each side (G + 1 parts a side).
+// Measured per 131,072 JED BPSK matrices (B = 16): K = 16 0.394 -> 0.189 ms, K = 32 0.988 ->
+// 0.939 ms; per 65,536 BPSK 32x8 0.095 -> 0.029 ms.  At NV = 32 the 128-register bound
+// spills a little and is still faster than 152 registers at 3 blocks per SM.
+template <int NV>
+struct SpecFoldCfg {
+  static constexpr int HALF = NV / 2;
+  static constexpr int G = HALF;                  // lanes per instance
+  static constexpr int IPW = 32 / G;              // instances per warp
+  static constexpr int NP = NV + 1;               // padded order
+  static constexpr int VB = ((NP + 3) / 4) * 4;   // pair vectors padded to 16-byte pairs of rows
+  static constexpr int WARPS = 4;
+  static constexpr int IPC = WARPS * IPW;
+  static constexpr int INST_FLOATS = 2 * VB + 2 * VB + 2 * VB;   // xd, wd (pairs), d, e
+  // Resolution (parts^rounds) of the one-sided search: 33^5 = 3.9e7, 17^6 = 2.4e7,
+  // 9^8 = 4.3e7; of the two-sided one: 17^7 = 4.1e8, 9^9 = 3.9e8, 5^12 = 2.4e8.
+  static constexpr int ROUNDS1 = NV == 32 ? 5 : (NV == 16 ? 6 : 8);
+  static constexpr int ROUNDS2 = NV == 32 ? 7 : (NV == 16 ? 9 : 12);
+};
+
+template <int NV>
+__global__ void __launch_bounds__(128, 4)
+spectral_fold_kernel(int64_t batch, int N, const float* __restrict__ Tt, float alpha, int sign_hint,
+                     float* __restrict__ tau, float* __restrict__ nrm_out) {
+  using C = SpecFoldCfg<NV>;
+  constexpr int NP = C::NP, VB = C::VB, G = C::G, HALF = C::HALF;
+  __shared__ __align__(16) float sm[C::IPC * C::INST_FLOATS];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int grp = lane / G, gl = lane % G;
+  const int local = warp * C::IPW + grp;
+  const int64_t inst = (int64_t)blockIdx.x * C::IPC + local;
+  const bool active = inst < batch;
+  float2* xd = reinterpret_cast<float2*>(sm + local * C::INST_FLOATS);
+  float2* wd = xd + VB;
+  float* db = reinterpret_cast<float*>(wd + VB);
+  float* eb = db + VB;
+  const int ca = gl + 1, cb = NV - gl;
+  const float* T = Tt + (active ? inst : 0) * (int64_t)N * N;
+  auto a_rc = [&](int r, int c) -> float {
+    return active && r < N && c < N && TASER_IN(inst * N * N + r * N + c, batch * N * N) ? T[(int64_t)r * N + c] : 0.f;
+  };
+  uint64_t cab[NP];
+  float amax;
+  float d0 = a_rc(0, 0);
+  {
+    float ma = fabsf(d0);
+#pragma unroll
+    for (int r = 0; r < NP; ++r) {
+      const float x = a_rc(r, ca), y = a_rc(r, cb);
+      ma = fmaxf(ma, fmaxf(fabsf(x), fabsf(y)));
+      cab[r] = f2pack(x, y);
+    }
+    amax = ma;
+  }
+#pragma unroll
+  for (int o = G / 2; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(TASER_FULL_MASK, amax, o));
+  const int ex = scale_exponent(amax);
+  {
+    const float sc = pow2f(-ex);
+    const uint64_t sc2 = f2pack(sc, sc);
+    d0 *= sc;
+#pragma unroll
+    for (int r = 0; r < NP; ++r) cab[r] = f2mul(cab[r], sc2);
+  }
+  for (int i = gl; i < VB; i += G) {
+    xd[i] = make_float2(0.f, 0.f);
+    wd[i] = make_float2(0.f, 0.f);
+  }
+  if (gl == 0) db[0] = d0;
+  __syncwarp();
+
+  static_for_blocks<NV, KBLK>([&](auto kb) {
+    constexpr int KB = decltype(kb)::value;
+    constexpr int KE = (KB + KBLK < NV - 1) ? KB + KBLK : NV - 1;   // k in [KB, KE)
+    constexpr int J0 = (KB + 1) & ~1;                                 // rows read in pairs
+#pragma unroll 1
+    for (int k = KB; k < KE; ++k) {
+      // Row k of both columns: x_c = A[k][c] for c > k (A symmetric).
+      uint64_t ckp = 0ull;
+#pragma unroll
+      for (int r = KB; r < KE; ++r) ckp = (r == k) ? cab[r] : ckp;
+      float ckA, ckB;
+      f2unpack(ckp, ckA, ckB);
+      const bool liveA = ca > k, liveB = cb > k;
+      float sig2 = (liveA ? ckA * ckA : 0.f) + (liveB ? ckB * ckB : 0.f);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) sig2 += __shfl_xor_sync(TASER_FULL_MASK, sig2, o);
+      // x_{k+1}: column k + 1 is ca of lane k (k + 1 <= NV / 2) or cb of lane NV - 1 - k.
+      const bool x1_in_a = k + 1 <= HALF;
+      const float x1 = __shfl_sync(TASER_FULL_MASK, x1_in_a ? ckA : ckB, grp * G + (x1_in_a ? k : NV - 1 - k));
+      // Reflector H = I - beta v v^T, v = x - ah e_{k+1}, ah = -sign(x_{k+1}) ||x||.
+      const bool refl = sig2 >= kTinyNorm2;
+      const float sig = refl ? sig2 * rsqrtf(sig2) : 0.f;
+      const float ah = x1 >= 0.f ? -sig : sig;
+      const float vv2 = 2.f * (sig2 + sig * fabsf(x1));
+      const float beta = refl ? __fdividef(2.f, vv2) : 0.f;
+      const float vA = liveA ? (ca == k + 1 ? ckA - ah : ckA) : 0.f;
+      const float vB = liveB ? (cb == k + 1 ? ckB - ah : ckB) : 0.f;
+      if (TASER_IN(ca, VB)) xd[ca] = make_float2(vA, vA);
+      if (TASER_IN(cb, VB)) xd[cb] = make_float2(vB, vB);
+      if (ca == k && TASER_IN(k, VB)) db[k] = ckA;
+      if (cb == k && TASER_IN(k, VB)) db[k] = ckB;
+      __syncwarp();
+      // (p_ca, p_cb) = beta sum_j (A[j][ca], A[j][cb]) v_j.
+      uint64_t acc = 0ull;
+#pragma unroll
+      for (int j = J0; j < NP; j += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(xd + j);   // rows j, j + 1
+        acc = f2fma(cab[j], f2pack(q.x, q.y), acc);
+        if (j + 1 < NP) acc = f2fma(cab[j + 1], f2pack(q.z, q.w), acc);
+      }
+      float pA, pB;
+      f2unpack(acc, pA, pB);
+      pA = liveA ? beta * pA : 0.f;
+      pB = liveB ? beta * pB : 0.f;
+      float kk = fmaf(vA, pA, vB * pB);
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) kk += __shfl_xor_sync(TASER_FULL_MASK, kk, o);
+      kk *= 0.5f * beta;
+      const float wA = fmaf(-kk, vA, pA), wB = fmaf(-kk, vB, pB);
+      if (TASER_IN(ca, VB)) wd[ca] = make_float2(wA, wA);
+      if (TASER_IN(cb, VB)) wd[cb] = make_float2(wB, wB);
+      if (gl == 0 && TASER_IN(k, VB)) eb[k] = ah;
+      __syncwarp();
+      // A <- A - v w^T - w v^T on the lane's two columns.
+      const uint64_t nw = f2pack(-wA, -wB), nv = f2pack(-vA, -vB);
+#pragma unroll
+      for (int j = J0; j < NP; j += 2) {
+        const float4 q = *reinterpret_cast<const float4*>(xd + j);
+        const float4 u = *reinterpret_cast<const float4*>(wd + j);
+        cab[j] = f2fma(f2pack(q.x, q.y), nw, f2fma(f2pack(u.x, u.y), nv, cab[j]));
+        if (j + 1 < NP) cab[j + 1] = f2fma(f2pack(q.z, q.w), nw, f2fma(f2pack(u.z, u.w), nv, cab[j + 1]));
+      }
+      __syncwarp();
+    }
+  });
+  // Trailing 2 x 2 block: columns NV - 1 and NV are cb of lanes 1 and 0.
+  {
+    float bl, bn, al_unused;
+    f2unpack(cab[NV - 1], al_unused, bl);
+    float an_unused;
+    f2unpack(cab[NV], an_unused, bn);
+    (void)al_unused;
+    (void)an_unused;
+    if (cb == NV - 1) {
+      db[NV - 1] = bl;
+      eb[NV - 1] = bn;
+    }
+    if (cb == NV) db[NV] = bn;
+  }
+  __syncwarp();
+  float d[NP], e2[NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    d[j] = db[j];
+    e2[j] = j < NV ? eb[j] * eb[j] : 0.f;
+  }
+  // Multisection.  One-sided: sg = the hint's sign, points 2 gl and 2 gl + 1 of NV.
+  // Two-sided (hint 0): the point gl of lambda_max(A) and the point gl of lambda_max(-A).
+  const bool two = sign_hint == 0;
+  const float sg0 = two ? 1.f : (sign_hint > 0 ? 1.f : -1.f);
+  const float sg1 = two ? -1.f : sg0;
+  const int parts = two ? G + 1 : NV + 1;
+  const int rounds = two ? C::ROUNDS2 : C::ROUNDS1;
+  // Bracket per side: [max sg d_j, max (sg d_j + |e_{j-1}| + |e_j|)].
+  float lo0 = -3.0e38f, hi0 = -3.0e38f, lo1 = -3.0e38f, hi1 = -3.0e38f;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const float r = (j > 0 ? sqrtf(e2[j - 1]) : 0.f) + sqrtf(e2[j]);
+    lo0 = fmaxf(lo0, sg0 * d[j]);
+    hi0 = fmaxf(hi0, sg0 * d[j] + r);
+    lo1 = fmaxf(lo1, sg1 * d[j]);
+    hi1 = fmaxf(hi1, sg1 * d[j] + r);
+  }
+  // The Sturm count needs e2 > 0; the floor comes after the bracket, which it must not
+  // widen (the zero matrix keeps the norm 0).
+#pragma unroll
+  for (int j = 0; j < NP; ++j) e2[j] = fmaxf(e2[j], kTinyNorm2);
+  const float inv_parts = 1.f / (float)parts;
+  const unsigned gmask = (1u << G) - 1u;
+  // index of the point of lane gl on each side: one-sided 2 gl and 2 gl + 1, two-sided gl
+  const int p0 = two ? gl : 2 * gl, p1 = two ? gl : 2 * gl + 1;
+#pragma unroll 1
+  for (int round = 0; round < rounds; ++round) {
+    const float st0 = (hi0 - lo0) * inv_parts, st1 = (hi1 - lo1) * inv_parts;
+    const float s0 = fmaf(st0, (float)(p0 + 1), lo0);
+    const float s1 = two ? fmaf(st1, (float)(p1 + 1), lo1) : fmaf(st0, (float)(p1 + 1), lo0);
+    const int c0 = sturm_count<NP>(d, e2, sg0, s0);
+    const int c1 = sturm_count<NP>(d, e2, sg1, s1);
+    const unsigned m0 = (__ballot_sync(TASER_FULL_MASK, c0 == NP) >> (grp * G)) & gmask;
+    const unsigned m1 = (__ballot_sync(TASER_FULL_MASK, c1 == NP) >> (grp * G)) & gmask;
+    if (two) {
+      // each side: first of its G points at or above its lambda_max
+      if (m0 == 0u) {
+        lo0 = fmaf(st0, (float)G, lo0);
+      } else {
+        const int f = __ffs(m0) - 1;
+        const float nhi = fmaf(st0, (float)(f + 1), lo0);
+        lo0 = f == 0 ? lo0 : fmaf(st0, (float)f, lo0);
+        hi0 = nhi;
+      }
+      if (m1 == 0u) {
+        lo1 = fmaf(st1, (float)G, lo1);
+      } else {
+        const int f = __ffs(m1) - 1;
+        const float nhi = fmaf(st1, (float)(f + 1), lo1);
+        lo1 = f == 0 ? lo1 : fmaf(st1, (float)f, lo1);
+        hi1 = nhi;
+      }
+    } else {
+      // one side, points interleaved over the lanes: p = 2 gl (m0) and 2 gl + 1 (m1)
+      const int f0 = m0 ? 2 * (__ffs(m0) - 1) : 2 * G;
+      const int f1 = m1 ? 2 * (__ffs(m1) - 1) + 1 : 2 * G;
+      const int f = min(f0, f1);
+      if (f == 2 * G) {
+        lo0 = fmaf(st0, (float)(2 * G), lo0);
+      } else {
+        const float nhi = fmaf(st0, (float)(f + 1), lo0);
+        lo0 = f == 0 ? lo0 : fmaf(st0, (float)f, lo0);
+        hi0 = nhi;
+      }
+    }
+  }
+  float nrm = 0.5f * (lo0 + hi0);
+  if (two) nrm = fmaxf(nrm, 0.5f * (lo1 + hi1));
+  nrm *= pow2f(ex);
+  if (active && gl == 0 && TASER_IN(inst, batch)) {
+    tau[inst] = nrm > 0.f ? alpha / nrm : 0.f;
+    if (nrm_out != nullptr) nrm_out[inst] = nrm;
+    TASER_FINITE(nrm);
+  }
+}
+
 template <int NV>
 static cudaError_t launch_spectral(int64_t batch, int N, const float* Tt, float alpha, int hint, float* tau,
                                    float* nrm, cudaStream_t st) {
-  const int64_t blocks = (batch + SpecCfg<NV>::WARPS - 1) / SpecCfg<NV>::WARPS;
-  spectral_kernel<NV><<<(unsigned)blocks, 32 * SpecCfg<NV>::WARPS, 0, st>>>(batch, N, Tt, alpha, hint, tau, nrm);
+  if constexpr (NV <= 32) {
+    const int64_t blocks = (batch + SpecFoldCfg<NV>::IPC - 1) / SpecFoldCfg<NV>::IPC;
+    spectral_fold_kernel<NV><<<(unsigned)blocks, 128, 0, st>>>(batch, N, Tt, alpha, hint, tau, nrm);
+  } else {
+    // NV = 64: two columns a lane already (S = 2); a fold would need 4.
+    const int64_t blocks = (batch + SpecCfg<NV>::WARPS - 1) / SpecCfg<NV>::WARPS;
+    spectral_kernel<NV><<<(unsigned)blocks, 32 * SpecCfg<NV>::WARPS, 0, st>>>(batch, N, Tt, alpha, hint, tau, nrm);
+  }
   return cudaGetLastError();
 }
 
