@@ -531,10 +531,10 @@ spectral_herm_kernel(int64_t batch, int U, const float* __restrict__ Tt, float a
 // (reductions, reflector scalars, selects) is then shared by twice as many instances as in
 // the one-column layout, and one shared-memory read of v and w serves both columns.  From
 // step UV/2 on every ca column is finished, and those blocks drop it at compile time.  The
-// multisection evaluates two points per lane: the same UV points per round as the
-// one-column layout, so both layouts take the same bracket decisions on the same
-// tridiagonal.  Measured at QPSK 128x16: 0.183 -> 0.138 ms per 65,536 matrices (128
-// registers, 4 blocks per SM; at 3 blocks and 138 registers 0.150 ms).
+// multisection evaluates one point per lane, G + 1 parts per round.  Measured at QPSK
+// 128x16: 0.183 -> 0.135 ms per 65,536 matrices (128 registers, 4 blocks per SM; at 3
+// blocks and 138 registers 0.150 ms; with 5 blocks and spills 0.155 ms; Householder blocks
+// of 1 or 4 steps 0.158 and 0.144 ms).
 template <int UV>
 struct HermFoldCfg {
   static constexpr int HALF = UV / 2;
@@ -545,7 +545,8 @@ struct HermFoldCfg {
   static constexpr int WARPS = 4;
   static constexpr int IPC = WARPS * IPW;
   static constexpr int INST_FLOATS = 8 * VB + 2 * VB;  // xd, wd ({re, re, im, im}), db, eb2
-  static constexpr int ROUNDS = UV == 16 ? 5 : 8;       // UV + 1 parts per round (as HermCfg)
+  // One point a lane, G + 1 parts per round: 9^7 = 4.8e6 at UV = 16, 5^12 = 2.4e8 at UV = 8.
+  static constexpr int ROUNDS = UV == 16 ? 7 : 12;
 };
 
 template <int UV, bool NEG>
@@ -748,24 +749,19 @@ spectral_herm_fold_kernel(int64_t batch, int U, const float* __restrict__ Tt, fl
   // widen (the zero matrix keeps the norm 0).
 #pragma unroll
   for (int j = 0; j < NP; ++j) e2[j] = fmaxf(e2[j], kTinyNorm2);
-  // One-sided multisection, UV + 1 parts: lane gl evaluates points 2 gl and 2 gl + 1
-  // (sigma_p = lo + (p + 1) step), the same 16 points as the one-column layout.
-  const float inv_parts = 1.f / (float)(UV + 1);
+  // One-sided multisection, G + 1 parts: lane gl evaluates the point sigma = lo + (gl + 1) step.
+  // (Two points a lane over UV + 1 parts, 5 rounds, were 1.5% slower at UV = 16.)
+  const float inv_parts = 1.f / (float)(G + 1);
   const unsigned gmask = (1u << G) - 1u;
 #pragma unroll 1
   for (int round = 0; round < C::ROUNDS; ++round) {
     const float step = (hi - lo) * inv_parts;
-    const float s0 = fmaf(step, (float)(2 * gl + 1), lo);
-    const float s1 = fmaf(step, (float)(2 * gl + 2), lo);
-    const int c0 = sturm_count<NP>(d, e2, 1.f, s0);
-    const int c1 = sturm_count<NP>(d, e2, 1.f, s1);
-    const unsigned m0 = (__ballot_sync(TASER_FULL_MASK, c0 == NP) >> (grp * G)) & gmask;
-    const unsigned m1 = (__ballot_sync(TASER_FULL_MASK, c1 == NP) >> (grp * G)) & gmask;
-    const int f0 = m0 ? 2 * (__ffs(m0) - 1) : 2 * G;
-    const int f1 = m1 ? 2 * (__ffs(m1) - 1) + 1 : 2 * G;
-    const int f = min(f0, f1);   // first point at or above lambda_max
-    if (f == 2 * G) {
-      lo = fmaf(step, (float)(2 * G), lo);
+    const float sigma = fmaf(step, (float)(gl + 1), lo);
+    const int cnt = sturm_count<NP>(d, e2, 1.f, sigma);
+    const unsigned mine = (__ballot_sync(TASER_FULL_MASK, cnt == NP) >> (grp * G)) & gmask;
+    const int f = mine ? __ffs(mine) - 1 : G;   // first point at or above lambda_max
+    if (f == G) {
+      lo = fmaf(step, (float)G, lo);
     } else {
       const float nhi = fmaf(step, (float)(f + 1), lo);
       const float nlo = f == 0 ? lo : fmaf(step, (float)f, lo);
