@@ -256,7 +256,8 @@ def test_step_size_nearly_singular_qpsk(T, B, U):
     """QPSK T~ of rank at most 2B + 1 < N = 2U + 1 (fewer antennas than users; B = U is the
     borderline square case) through the complex Hermitian form with U + 1 <= 17: the one-sided search
     relies on T~ being positive semidefinite, which the FP32 reduction only keeps to
-    rounding on such matrices.  Five multisection rounds leave at most 7e-7 relative."""
+    rounding on such matrices.  The multisection (9 parts, 7 rounds for U + 1 <= 17) leaves
+    at most 2.1e-7 relative of its own."""
     n = 64
     X, y, _ = problem("mimo_qpsk", n, B, U, 10.0, 400 + B)
     Tt = O.detect("mimo_qpsk", X, y, ALPHA, 1)["T_tilde"].astype(np.float32)
