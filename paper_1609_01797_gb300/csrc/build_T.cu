@@ -26,6 +26,8 @@
 #include <cuda.h>
 #include <cuda_fp16.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace taser {
@@ -58,6 +60,24 @@ static_assert((BuildCfg<9>::CH - 1) * BuildCfg<9>::WS + 8 * BuildCfg<9>::NT <= B
 static_assert((BuildCfg<17>::CH - 1) * BuildCfg<17>::WS + 8 * BuildCfg<17>::NT <= BuildCfg<17>::BUF_FLOATS, "");
 static_assert((BuildCfg<33>::CH - 1) * BuildCfg<33>::WS + 8 * BuildCfg<33>::NT <= BuildCfg<33>::BUF_FLOATS, "");
 static_assert(31 * BuildCfg<17>::WS + 8 * BuildCfg<17>::NT <= 2 * BuildCfg<17>::BUF_FLOATS, "");
+
+// The BPSK kinds need only Re Gamma' (T = +-A^T A with A = [Re; Im] stacked), which is the
+// Gram of the real rows: each antenna row contributes its real and its imaginary part as two
+// k-rows, and the columns are the complex columns themselves.  Against the interleaved
+// complex Gram that is half the columns, a quarter of the tiles and half the MMAs, and a
+// k-row pair (Re, Im) is one 8-byte shared-memory read.  Used with the FP16 split (MP >= 17).
+template <int MP>
+struct RealGramCfg {
+  static constexpr int NT = (MP + 7) / 8;             // n-tiles of 8 columns
+  static constexpr int MT = (MP + 15) / 16;           // m-tiles of 16 columns
+  __host__ __device__ static constexpr bool tile(int i, int j) { return j >= 2 * i && j < NT; }
+};
+// The real-row reads stay inside a staged row: column c < MP is floats 2c, 2c + 1.
+static_assert(2 * 17 <= BuildCfg<17>::WS && 2 * 33 <= BuildCfg<33>::WS, "");
+template <int MP, int KIND>
+__host__ __device__ constexpr bool real_gram() {
+  return MP >= 17 && (KIND == TASER_MIMO_BPSK || KIND == TASER_SIMO_JED_BPSK);
+}
 static_assert(31 * BuildCfg<33>::WS + 8 * BuildCfg<33>::NT <= BuildCfg<33>::BUF_FLOATS, "");
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gsrc) {
@@ -194,13 +214,15 @@ static __device__ int g_drop_chunk = -1;
 // KIND >= 0 compiles the epilogue for that problem kind; -1 takes it from kind_rt.
 // TMA: staging by the tensor memory accelerator (MP = 17, QPSK only; see TmaCfg).
 template <int MP, int KIND, bool TMA = false>
-__global__ void __launch_bounds__(128, MP == 17 ? 5 : 1)
+__global__ void __launch_bounds__(128, MP == 17 ? 5 : (real_gram<MP, KIND>() ? 3 : 1))
 build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __restrict__ X,
                const float2* __restrict__ yv, float* __restrict__ Tt, float* __restrict__ Dout,
                uint32_t* __restrict__ flags, const __grid_constant__ CUtensorMap tmH,
                const __grid_constant__ CUtensorMap tmY, long long wait_budget) {
-  using C = BuildCfg<MP>;
-  constexpr int NT = C::NT, MT = C::MT, WS = C::WS, CH = C::CH;
+  using C = BuildCfg<MP>;                      // staging (and the interleaved complex Gram)
+  constexpr bool REAL = real_gram<MP, KIND>();
+  using GT = std::conditional_t<REAL, RealGramCfg<MP>, BuildCfg<MP>>;   // Gram tiles
+  constexpr int NT = GT::NT, MT = GT::MT, WS = C::WS, CH = C::CH;
   constexpr int WFL = TMA ? TmaCfg::WARP_FLOATS : C::WARP_FLOATS;   // floats per warp
   static_assert(!TMA || (MP == 17 && KIND == TASER_MIMO_QPSK), "TMA staging serves the 17-column QPSK Gram");
   const int kind = KIND >= 0 ? KIND : kind_rt;
@@ -265,6 +287,8 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   int exq[NT];
 #pragma unroll
   for (int j = 0; j < NT; ++j) exq[j] = 0;
+  // Real-row Gram: exponent of column q = 8j + 2tq + e of this lane's accumulators.
+  [[maybe_unused]] int exr[NT][2];
   if constexpr (TMA) {
     // The FP16-split Gram of the branch below (same scales, restart and tiles), staged by
     // TMA.  A 16-row step pairs rows (2tq, 2tq + 1) and (2tq + 8, 2tq + 9) as its k-indices;
@@ -404,7 +428,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
           }
 #pragma unroll
           for (int j = 0; j < NT; ++j) {
-            if (!C::tile(i, j)) continue;
+            if (!GT::tile(i, j)) continue;
             mma_f16(acc[i][j], ah, bh[j][0], bh[j][1]);
             mma_f16(acc[i][j], ah, bl[j][0], bl[j][1]);
             mma_f16(acc[i][j], al, bh[j][0], bh[j][1]);
@@ -433,6 +457,128 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
     }
 #pragma unroll
     for (int j = 0; j < NT; ++j) exq[j] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq));
+  } else if constexpr (REAL) {
+    // The FP16-split Gram of the real rows (BPSK kinds): same per-column power-of-two scales,
+    // restart and tiles as the complex branch below.  A 16-row k-step takes 8 antenna rows:
+    // k-rows 2tq and 2tq + 1 are the real and imaginary parts of staged row tq, k-rows
+    // 2tq + 8 and 2tq + 9 those of row tq + 4, so each B register is one (Re, Im) pair of
+    // column 8j + g.  Columns >= MP read as zero.
+    int ex[NT];
+    float sc[NT];
+  #pragma unroll
+    for (int j = 0; j < NT; ++j) ex[j] = 0;
+    for (int attempt = 0; attempt < 16; ++attempt) {
+  #pragma unroll
+      for (int i = 0; i < MT; ++i)
+  #pragma unroll
+        for (int j = 0; j < NT; ++j)
+  #pragma unroll
+          for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+  #pragma unroll
+      for (int s = 0; s < C::NS - 1; ++s) {
+        if (s < nchunks) stage(s); else cp_async_commit();
+      }
+      for (int chunk = 0; chunk < nchunks; ++chunk) {
+        cp_async_wait<C::NS - 2>();
+        __syncwarp();
+        float* buf = Ws + (chunk % C::NS) * C::BUF_FLOATS;
+        const int rows = min(CH, B - chunk * CH);
+        if (rows < CH) {  // zero the unused tail rows of the last chunk
+          for (int i = rows * WS + lane; i < CH * WS; i += 32) buf[i] = 0.f;
+          __syncwarp();
+        }
+        if (attempt == 0 && chunk == 0) {
+          // Column maxima over the first 32 antenna rows (rows past B read as zero): the real
+          // and imaginary parts of rows tq + 4r of column 8j + g, then over tq.
+          if constexpr (CH < 32) {
+            static_assert(CH == 16 && C::NS >= 3, "the first 32 rows must be chunks 0 and 1");
+            cp_async_wait<C::NS - 3>();
+            __syncwarp();
+            if (nchunks > 1 && B - CH < CH) {
+              float* b1 = Ws + C::BUF_FLOATS;
+              for (int i = (B - CH) * WS + lane; i < CH * WS; i += 32) b1[i] = 0.f;
+              __syncwarp();
+            }
+          }
+  #pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            float m = 0.f;
+            if (8 * j + g < MP) {
+  #pragma unroll
+              for (int r = 0; r < 32 / 4; ++r) {
+                const float2 v = *reinterpret_cast<const float2*>(Ws + (tq + 4 * r) * WS + 2 * (8 * j + g));
+                m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+              }
+            }
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 1));
+            m = fmaxf(m, __shfl_xor_sync(TASER_FULL_MASK, m, 2));
+            const int e2 = (int)((__float_as_uint(m) >> 23) & 0xffu) - 127;   // floor(log2 m), m normal
+            ex[j] = (m > 0.f && e2 > -127) ? min(max(6 - e2, -100), 100) : 0;
+          }
+        }
+  #pragma unroll
+        for (int j = 0; j < NT; ++j) sc[j] = pow2i(ex[j]);
+        if (chunk + C::NS - 1 < nchunks) stage(chunk + C::NS - 1); else cp_async_commit();
+  #pragma unroll
+        for (int ks = 0; ks < CH / 8; ++ks) {
+          uint32_t bh[NT][2], bl[NT][2];
+          const float* rp = buf + (8 * ks + tq) * WS + 2 * g;
+  #pragma unroll
+          for (int j = 0; j < NT; ++j) {
+            const uint64_t sc2 = f2pack(sc[j], sc[j]);
+            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
+            if (8 * j + g < MP) {
+              v0 = *reinterpret_cast<const float2*>(rp + 16 * j);
+              v1 = *reinterpret_cast<const float2*>(rp + 4 * WS + 16 * j);
+            }
+            split_f16(v0.x, v0.y, sc2, bh[j][0], bl[j][0]);
+            split_f16(v1.x, v1.y, sc2, bh[j][1], bl[j][1]);
+          }
+  #pragma unroll
+          for (int i = 0; i < MT; ++i) {
+            // A = W^T: rows 16i + g (+8) are n-tiles 2i and 2i+1 of the same loads.
+            const int j0 = 2 * i, j1 = 2 * i + 1;
+            uint32_t ah[4], al[4];
+            ah[0] = bh[j0][0];
+            ah[2] = bh[j0][1];
+            al[0] = bl[j0][0];
+            al[2] = bl[j0][1];
+            if (j1 < NT) {
+              ah[1] = bh[j1][0];
+              ah[3] = bh[j1][1];
+              al[1] = bl[j1][0];
+              al[3] = bl[j1][1];
+            } else {
+              ah[1] = ah[3] = al[1] = al[3] = 0u;
+            }
+  #pragma unroll
+            for (int j = 0; j < NT; ++j) {
+              if (!GT::tile(i, j)) continue;
+              mma_f16(acc[i][j], ah, bh[j][0], bh[j][1]);
+              mma_f16(acc[i][j], ah, bl[j][0], bl[j][1]);
+              mma_f16(acc[i][j], al, bh[j][0], bh[j][1]);
+            }
+          }
+        }
+        __syncwarp();  // every lane has read this buffer before it is refilled
+      }
+      bool finite = true;
+  #pragma unroll
+      for (int i = 0; i < MT; ++i)
+  #pragma unroll
+        for (int j = 0; j < NT; ++j)
+  #pragma unroll
+          for (int e = 0; e < 4; ++e) finite = finite && isfinite(acc[i][j][e]);
+      if (__all_sync(TASER_FULL_MASK, finite)) break;   // no FP16 overflow (non-finite input retries)
+  #pragma unroll
+      for (int j = 0; j < NT; ++j) ex[j] -= 9;
+    }
+    // Column q = 8j + 2tq + e of the accumulators is column 8j + g of lane g = 2tq + e.
+  #pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      exr[j][0] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq));
+      exr[j][1] = __shfl_sync(TASER_FULL_MASK, ex[j], 4 * (2 * tq + 1));
+    }
   } else if constexpr (C::F16) {
     // Per-column power-of-two scales: this lane's columns 8j + g are multiplied by 2^ex[j]
     // before the FP16 split, chosen from the first 32 antenna rows so that the largest
@@ -530,7 +676,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
             }
   #pragma unroll
             for (int j = 0; j < NT; ++j) {
-              if (!C::tile(i, j)) continue;
+              if (!GT::tile(i, j)) continue;
               mma_f16(acc[i][j], ah, bh[j][0], bh[j][1]);
               mma_f16(acc[i][j], ah, bl[j][0], bl[j][1]);
               mma_f16(acc[i][j], al, bh[j][0], bh[j][1]);
@@ -605,7 +751,7 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
           }
   #pragma unroll
           for (int j = 0; j < NT; ++j) {
-            if (!C::tile(i, j)) continue;
+            if (!GT::tile(i, j)) continue;
             mma_tf32(acc[i][j], ah, bh[j][0], bh[j][1]);
             mma_tf32(acc[i][j], ah, bl[j][0], bl[j][1]);
             mma_tf32(acc[i][j], al, bh[j][0], bh[j][1]);
@@ -621,21 +767,25 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   // columns 8j + 2tq, +1 of G', i.e. complex column q = 4j + tq; rows 2p and 2p+1 of
   // complex row p sit in lanes g and g + 1 (even g combines).  Each (p, q) with p <= q
   // lies in exactly one computed tile.
-  float gre[MT][NT][2], gim[MT][NT][2];
+  // (The real-row Gram holds Re Gamma'_pq directly: row p = 16i + g (+8), column
+  // q = 8j + 2tq (+1) of each tile.)
+  [[maybe_unused]] float gre[MT][NT][2], gim[MT][NT][2];
+  if constexpr (!REAL) {
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+    for (int i = 0; i < MT; ++i)
 #pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      if (!C::tile(i, j)) continue;
-      float o[4];
+      for (int j = 0; j < NT; ++j) {
+        if (!GT::tile(i, j)) continue;
+        float o[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) o[e] = __shfl_xor_sync(TASER_FULL_MASK, acc[i][j][e], 4);
+        for (int e = 0; e < 4; ++e) o[e] = __shfl_xor_sync(TASER_FULL_MASK, acc[i][j][e], 4);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        gre[i][j][h] = acc[i][j][2 * h] + o[2 * h + 1];
-        gim[i][j][h] = acc[i][j][2 * h + 1] - o[2 * h];
+        for (int h = 0; h < 2; ++h) {
+          gre[i][j][h] = acc[i][j][2 * h] + o[2 * h + 1];
+          gim[i][j][h] = acc[i][j][2 * h + 1] - o[2 * h];
+        }
       }
-    }
+  }
   const bool holder = (g & 1) == 0;
   // Complex column p -> real indices of T: (ire, iim, kind of column) with the augmented
   // column last.  QPSK user p: real p and U + p; BPSK / JED data column p: real p.
@@ -647,11 +797,41 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
   __syncwarp();
   // Diagonal: D and the flags.
   uint32_t fl = 0;
+  if constexpr (REAL) {
 #pragma unroll
-  for (int i = 0; i < MT; ++i)
+    for (int i = 0; i < MT; ++i)
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        if (!GT::tile(i, j)) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int p = 16 * i + g + 8 * h, q = 8 * j + 2 * tq + e;
+            if (p == q && (p < P || p == MP - 1)) {
+              const float v = acc[i][j][2 * h + e];
+              const float taa = fabsf(v);                 // 2^(2 e_p) |T_pp|
+              if (!isfinite(v)) fl |= TASER_FLAG_NONFINITE;
+              float da = sqrtf(taa);                      // D'_p = 2^e_p D_p
+              float dtrue = ldexpf(da, -exr[j][e]);
+              if (taa == 0.f) {
+                da = 1.f;
+                dtrue = 1.f;
+                fl |= TASER_FLAG_ZERO_DIAG;
+              }
+              if (TASER_IN(p, 72)) {
+                Dc[p] = dtrue;
+                rDc[p] = 1.f / da;
+              }
+            }
+          }
+      }
+  }
+#pragma unroll
+  for (int i = 0; i < MT && !REAL; ++i)
 #pragma unroll
     for (int j = 0; j < NT; ++j) {
-      if (!C::tile(i, j)) continue;
+      if (!GT::tile(i, j)) continue;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
@@ -694,11 +874,40 @@ build_T_kernel(int kind_rt, int64_t batch, int B, int P, int N, const float2* __
     auto put = [&](int a, float v) {
       if (TASER_IN(a, Nr * Nr)) Tsm[a] = v;
     };
+    if constexpr (REAL) {
+      // BPSK kinds: T~_pq = T~_qp = +-Re Gamma'_pq / (D'_p D'_q), the augmented column last.
 #pragma unroll
-    for (int i = 0; i < MT; ++i)
+      for (int i = 0; i < MT; ++i)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) {
+          if (!GT::tile(i, j)) continue;
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              const int p = 16 * i + g + 8 * h, q = 8 * j + 2 * tq + e;
+              const bool pv = p < NU, qv = q < NU, qa = q == MP - 1, pa = p == MP - 1;
+              if (p > q || !(pv || pa) || !(qv || qa)) continue;
+              const float re = acc[i][j][2 * h + e];
+              const float sc = (TASER_IN(p, 72) && TASER_IN(q, 72)) ? rDc[p] * rDc[q] : 0.f;
+              const int ap = pa ? Nr - 1 : p, aq = qa ? Nr - 1 : q;
+              if (p == q) {
+                put(ap * Nr + ap, re == 0.f ? 0.f : dsg);
+                continue;
+              }
+              // MIMO BPSK: A = [H, -y] flips the sign of the augmented column's entries;
+              // JED BPSK: T = -A^T A.
+              const float v = (kind == TASER_SIMO_JED_BPSK ? -re : (qa ? -re : re)) * sc;
+              put(ap * Nr + aq, v);
+              put(aq * Nr + ap, v);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < MT && !REAL; ++i)
 #pragma unroll
       for (int j = 0; j < NT; ++j) {
-        if (!C::tile(i, j)) continue;
+        if (!GT::tile(i, j)) continue;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
           const int p = 8 * i + 4 * h + (g >> 1), q = 4 * j + tq;
@@ -877,9 +1086,19 @@ cudaError_t build_T(int kind, int64_t batch, int B, int P, int N, const void* X,
     }
     if (kind == TASER_MIMO_QPSK)
       return launch_build<17, TASER_MIMO_QPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+    if (kind == TASER_MIMO_BPSK)   // the BPSK kinds: Gram of the real rows
+      return launch_build<17, TASER_MIMO_BPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+    if (kind == TASER_SIMO_JED_BPSK)
+      return launch_build<17, TASER_SIMO_JED_BPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
     return launch_build<17, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
   }
-  if (P + 1 <= 33) return launch_build<33, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+  if (P + 1 <= 33) {
+    if (kind == TASER_MIMO_BPSK)
+      return launch_build<33, TASER_MIMO_BPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+    if (kind == TASER_SIMO_JED_BPSK)
+      return launch_build<33, TASER_SIMO_JED_BPSK>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+    return launch_build<33, -1>(kind, batch, B, P, N, Xc, yc, Tt, D, flags, st);
+  }
   return cudaErrorNotSupported;
 }
 

@@ -151,7 +151,12 @@ BUILD_CASES = [("mimo_bpsk", 32, 8), ("mimo_bpsk", 7, 3), ("mimo_bpsk", 64, 16),
                ("mimo_qpsk", 37, 16), ("mimo_qpsk", 20, 16), ("mimo_qpsk", 9, 10), ("jed_bpsk", 33, 16),
                # QPSK with 16 users and B even is staged by TMA: ragged last boxes (38 = 16 + 16 + 6,
                # 10), the smallest B (2), one full box (16); odd B (37 above) takes the cp.async path
-               ("mimo_qpsk", 38, 16), ("mimo_qpsk", 10, 16), ("mimo_qpsk", 2, 16), ("mimo_qpsk", 16, 16)]
+               ("mimo_qpsk", 38, 16), ("mimo_qpsk", 10, 16), ("mimo_qpsk", 2, 16), ("mimo_qpsk", 16, 16),
+               # the BPSK kinds with 10..33 columns take the Gram of the real rows: ragged
+               # 16-row chunks (37), fewer than 32 rows for the scale search (7, 20), a ragged
+               # 32-row chunk (45), padding columns inside the bucket (12, 17, 20, 24)
+               ("mimo_bpsk", 37, 12), ("mimo_bpsk", 20, 16), ("mimo_bpsk", 45, 20), ("jed_bpsk", 7, 17),
+               ("jed_bpsk", 50, 24), ("jed_bpsk", 33, 32)]
 
 
 @pytest.mark.parametrize("kind,B,M", BUILD_CASES)
@@ -169,19 +174,25 @@ def test_build_T_matches_oracle(T, kind, B, M):
     assert (out["flags"].cpu().numpy() == 0).all()
 
 
-@pytest.mark.parametrize("case", ["near_far", "huge", "tiny", "late_loud_rows", "jed_late_loud"])
+RANGE_SHAPES = {"jed_late_loud": ("jed_qpsk", 96, 17), "jed_bpsk_late_loud": ("jed_bpsk", 96, 32),
+                "bpsk_late_loud": ("mimo_bpsk", 80, 16), "bpsk_near_far": ("mimo_bpsk", 64, 24)}
+
+
+@pytest.mark.parametrize("case", ["near_far", "huge", "tiny", "late_loud_rows", "jed_late_loud",
+                                  "jed_bpsk_late_loud", "bpsk_late_loud", "bpsk_near_far"])
 def test_build_T_range_handling(T, case):
     """The FP16 split Gram scales each column by a power of two chosen on the first 32
     antenna rows and restarts at a smaller scale if a later value overflows FP16.  Inputs
     that stress this: users 80 dB apart, overall scales of 1e6 and 1e-8, and rows after the
-    first 32 that are 1e4 times louder (forcing the restart).  T~, D and tau must still
-    match the oracle to the usual tolerances."""
+    first 32 that are 1e4 times louder (forcing the restart).  The BPSK kinds take the Gram
+    of the real rows (JED BPSK K = 32 and MIMO BPSK U = 16, 24), the others the interleaved
+    complex Gram.  T~, D and tau must still match the oracle to the usual tolerances."""
     n = 29
-    kind, B, M = ("jed_qpsk", 96, 17) if case == "jed_late_loud" else ("mimo_qpsk", 128, 16)
+    kind, B, M = RANGE_SHAPES.get(case, ("mimo_qpsk", 128, 16))
     X, y, _ = problem(kind, n, B, M, 8.0, 77)
     X = X.astype(np.complex128)
     y = None if y is None else y.astype(np.complex128)
-    if case == "near_far":
+    if case in ("near_far", "bpsk_near_far"):
         X = X * (10.0 ** np.linspace(-2.0, 2.0, M))[None, None, :]
         y = X.sum(axis=2) * 0.3 + 0.01 * y
     elif case == "huge":
