@@ -73,9 +73,10 @@ def build_bytes_per_instance(b, u, n):
 
 def spectral_flops_per_instance(u):
     """Complex Hermitian tridiagonalisation of order n = U + 1 (16/3 n^3 real flops) plus
-    the Sturm multisection (5 rounds x 17 points x n steps x 4 flops)."""
+    the Sturm multisection of the folded kernel (U <= 16: 7 rounds x 8 points x n steps x 4
+    flops)."""
     n = u + 1
-    return 16 * n ** 3 // 3 + 5 * 17 * n * 4
+    return 16 * n ** 3 // 3 + 7 * 8 * n * 4
 
 
 KERNEL_SOURCES = {"build": "build_T.cu", "spectral": "spectral.cu", "detect_tc": "detect_tc.cu",
