@@ -2,17 +2,21 @@
 //
 // ||T~||_2 of a symmetric matrix is its largest |eigenvalue|.  A power iteration is not
 // used: on MU-MIMO matrices the two largest eigenvalues are often close and hundreds of
-// steps still leave errors of 1e-3.  Instead each warp reduces one T~ to tridiagonal form
-// with Householder reflections (FP32, backward stable) and then finds the extreme
-// eigenvalues of the tridiagonal matrix by Sturm-count multisection.  When T~ is known
-// to be semidefinite (MU-MIMO: T = A^T A; JED: T = -A^T A) only that end is searched by
-// all 32 lanes (33 parts per round); otherwise lanes 0..15 bracket lambda_max(T~) and
-// lanes 16..31 lambda_max(-T~) (17 parts per round).
+// steps still leave errors of 1e-3.  Instead each T~ is reduced to tridiagonal form with
+// Householder reflections (FP32, backward stable), and the extreme eigenvalues of the
+// tridiagonal matrix are found by Sturm-count multisection.  When T~ is known to be
+// semidefinite (MU-MIMO: T = A^T A; JED: T = -A^T A) only that end is searched; otherwise
+// lambda_max(T~) and lambda_max(-T~) are bracketed side by side.
 //
 // Layout: T~ is embedded in an (NV+1) x (NV+1) matrix with zero padding (zero rows and
 // columns add zero eigenvalues, which do not change ||T~||_2 since ||T~||_2 >= 0).  The
-// first reflection eliminates column 0, leaving an NV x NV trailing matrix whose column
-// c (1..NV) lives in the registers of lane (c-1) mod 32.
+// first reflection eliminates column 0, leaving an NV x NV trailing matrix whose columns
+// 1..NV live in lane registers:
+//  - spectral_fold_kernel (real, NV <= 32) and spectral_herm_fold_kernel (QPSK complex
+//    form, NV <= 16): NV / 2 lanes per instance, two columns per lane (c and NV + 1 - c),
+//    several instances per warp;
+//  - spectral_kernel (real, NV = 64) and spectral_herm_kernel (complex, NV = 32): one warp
+//    per instance, column c in lane (c - 1) mod 32.
 #include <type_traits>
 
 #include "common.cuh"
