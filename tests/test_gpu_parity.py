@@ -328,6 +328,27 @@ def test_end_to_end_matches_oracle(T, kind, B, M, t_max, precision):
     assert abs(int((s != truth).sum()) - int((r["s_hat"] != truth).sum())) <= int((~m).sum())
 
 
+@pytest.mark.parametrize("N,precision", [(17, "fp32"), (17, "bf16_tc"), (33, "bf16_tc"), (33, "fp16_tc"),
+                                         (65, "bf16_tc")])
+def test_zero_column_is_flagged(T, N, precision):
+    """A column of V with zero norm in the prox (row and column 2 of T~ zero and D_2 = 0: the
+    column starts and stays at zero) sets TASER_FLAG_ZERO_COLUMN on that instance only, as in
+    the oracle, and the column of L~ stays zero."""
+    n = 40
+    Tt, D, tau = oracle_inputs(N, n, seed=5500 + N)
+    Tt, D = Tt.copy(), D.copy()
+    Tt[5, 2, :] = 0.0
+    Tt[5, :, 2] = 0.0
+    D[5, 2] = 0.0
+    Lo, fo = O.taser(Tt.astype(np.float64), D.astype(np.float64), tau.astype(np.float64), 5)
+    assert fo[5] & O.FLAG_ZERO_COLUMN and not (np.delete(fo, 5) & O.FLAG_ZERO_COLUMN).any()
+    s, L, flags = T.detect(*to_dev(Tt, D, tau), 5, precision)
+    torch.cuda.synchronize()
+    got = flags.cpu().numpy().astype(np.uint32)
+    np.testing.assert_array_equal(got & O.FLAG_ZERO_COLUMN, fo & O.FLAG_ZERO_COLUMN)
+    assert (L.cpu().numpy()[5][:, 2] == 0).all()
+
+
 def test_zero_channel_column_is_flagged(T):
     w = make_mimo(9, 16, 4, 10.0, "qpsk", seed=3)
     H = w["H"].copy()
