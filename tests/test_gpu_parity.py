@@ -349,6 +349,38 @@ def test_zero_column_is_flagged(T, N, precision):
     assert (L.cpu().numpy()[5][:, 2] == 0).all()
 
 
+@pytest.mark.parametrize("N,precision", [(9, "fp32"), (17, "fp32"), (17, "bf16_tc"), (33, "bf16_tc"),
+                                         (33, "fp16_tc"), (65, "bf16_tc")])
+@pytest.mark.parametrize("mode", ["fixed", "literal"])
+def test_lnn_sign_flag_matches_oracle(T, N, precision, mode):
+    """TASER_FLAG_LNN_SIGN (V_NN <= 0 in some iteration) against the oracle.  From L~(0) = D
+    the first step gives V_NN = D_N (1 - 2 tau T~_NN); with T~ close to the identity, a step
+    size tau > 1/2 (alpha = 0.9) makes V_NN negative by a wide margin and alpha = 0.2 keeps it
+    positive.  Only instances whose V_NN stays 2e-2 D_N away from zero in every iteration of
+    the FP64 oracle are compared (all of them here)."""
+    rng = np.random.default_rng(6000 + N)
+    n = 96
+    E = rng.uniform(-0.05, 0.05, size=(n, N, N))
+    E = (E + np.transpose(E, (0, 2, 1))) / 2
+    E[:, np.arange(N), np.arange(N)] = 0.0
+    Tt = (np.eye(N)[None] + E).astype(np.float32)
+    D = rng.uniform(0.5, 2.0, size=(n, N)).astype(np.float32)
+    alpha = np.where(np.arange(n) % 2 == 0, 0.2, 0.9)
+    tau = (alpha / O.spectral_norm(Tt.astype(np.float64))).astype(np.float32)
+    T64, D64, tau64 = Tt.astype(np.float64), D.astype(np.float64), tau.astype(np.float64)
+    Lo, fo, Ls = O.taser(T64, D64, tau64, 10, lnn_mode=mode, history=True)
+    vnn = np.array([(Lt - tau64[:, None, None] * O.gradient(Lt, T64))[:, -1, -1] for Lt in Ls[:-1]])
+    robust = np.abs(vnn).min(axis=0) > 2e-2 * D64[:, -1]
+    want = (fo & O.FLAG_LNN_SIGN) != 0
+    assert robust.sum() >= 80 and want[robust].sum() >= 30 and (~want[robust]).sum() >= 30
+    s, L, flags = T.detect(*to_dev(Tt, D, tau), 10, precision, mode)
+    torch.cuda.synchronize()
+    got = (flags.cpu().numpy().astype(np.uint32) & O.FLAG_LNN_SIGN) != 0
+    np.testing.assert_array_equal(got[robust], want[robust])
+    err = rel_frob(L.cpu().numpy().astype(np.float64), Lo)
+    assert err[robust].max() <= (1e-5 if precision == "fp32" else 3e-2), err.max()
+
+
 def test_zero_channel_column_is_flagged(T):
     w = make_mimo(9, 16, 4, 10.0, "qpsk", seed=3)
     H = w["H"].copy()
